@@ -1,0 +1,322 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the spectral SOG evaluation (energy + forces).
+
+One step = one sog_eval call over the whole hot path (binning, near field,
+mid range, long range and its k = 0 mode, assembly) on the workload below,
+with inputs resident on the device.  Prints one JSON line.
+
+Workload (default "c2"): N = 1e5 neutral +-1 charges, uniform positions in a
+100 x 100 x 100 box, periodic in x and y and free in z, relative tolerance
+1e-6, mixed precision (FP32 bulk, FP64 tables / k = 0 mode / reductions).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torch.distributed.run) every rank evaluates
+its own replica of the workload; there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s (energy+forces) at rel. error 1e-6 vs FP64 oracle; % HBM roofline"
+WORKLOADS = {
+    "c2": dict(N=100000, L=(100.0, 100.0, 100.0), tol=1e-6, seed=1,
+               desc="uniform neutral +-1 charges, N=1e5, box 100x100x100 (periodic x,y, free z), tol 1e-6"),
+    "c2_1e4": dict(N=100000, L=(100.0, 100.0, 100.0), tol=1e-4, seed=1,
+                   desc="uniform neutral +-1 charges, N=1e5, box 100x100x100, tol 1e-4"),
+    "c1": dict(N=1000, L=(10.0, 10.0, 10.0), tol=1e-6, seed=1,
+               desc="uniform neutral +-1 charges, N=1e3, box 10x10x10, tol 1e-6"),
+}
+FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2, written between steps
+PAIR_FLOP = 50                   # FP32 operations per near-field pair
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = sorted(float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit())
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def stage_units(prm, N, stage):
+    """Algorithmic work of one stage launch and its bound."""
+    Ix, Iy, Iz = prm["I"]
+    P = prm["P_win"]
+    rho = N / (prm["L"][0] * prm["L"][1] * prm["L"][2])
+    pairs = N * 4.0 / 3.0 * math.pi * prm["rc"] ** 3 * rho
+    if stage == "near":
+        return "alu", pairs * PAIR_FLOP, "FP32 flop: %.3g pairs x %d" % (pairs, PAIR_FLOP)
+    if stage == "mid_spread":
+        return "alu", N * P ** 3 * 2.0, "FP32 flop: N x P^3 x 2"
+    if stage == "mid_gather":
+        return "alu", N * P ** 3 * 4.0, "FP32 flop: N x P^3 x 4"
+    if stage == "mid_fft":
+        cplx = Iz * Iy * (Ix // 2 + 1) * 8
+        return "hbm", 5 * 2 * cplx, "bytes: 5 passes x (read + write) of the half spectrum"
+    return None, None, None
+
+
+def run_ours(args, wl, rank, world):
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    from paper_2412_04595_gb300 import binding as B, workloads
+
+    g.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    N, L, tol = wl["N"], wl["L"], wl["tol"]
+    prec = B.SOG_PREC_FP64 if args.precision == "fp64" else B.SOG_PREC_MIXED
+    np_dt = np.float64 if prec == B.SOG_PREC_FP64 else np.float32
+    q, r = workloads.uniform_neutral(N, L, wl["seed"], dtype=np_dt)
+    plan = B.Plan(N, L, tol, precision=prec, n_nb=args.n_nb)
+    dt = plan.dtype
+    qt = torch.tensor(q, device=dev)
+    rt = torch.tensor(r, device=dev)
+    phi = torch.empty(N, dtype=dt, device=dev)
+    F = torch.empty(N, 3, dtype=dt, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    plan.set_timing(True)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        plan.eval(qt, rt, phi, E, F, stream=stream)
+    torch.cuda.synchronize()
+    if plan.check() != 0:
+        raise RuntimeError("evaluation reported a data error")
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    times = []
+    stages = {}
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval(qt, rt, phi, E, F, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        for k, v in plan.timing().items():
+            stages.setdefault(k, []).append(v)
+    torch.cuda.synchronize()
+    launches = plan.launches() * args.steps
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+    torch.cuda.synchronize()
+    value = world * N * args.steps / (total_ms * 1e-3)
+    stage_ms = {k: sum(v) / len(v) for k, v in stages.items()}
+
+    # end to end through the host entry point (pinned buffers, H2D + D2H inside)
+    qh = torch.tensor(q).pin_memory()
+    rh = torch.tensor(r).pin_memory()
+    phih = torch.empty(N, dtype=dt).pin_memory()
+    Fh = torch.empty(N, 3, dtype=dt).pin_memory()
+    Eh = torch.empty(1, dtype=torch.float64).pin_memory()
+    plan.set_timing(False)
+    for _ in range(2):
+        plan.eval_host(qh, rh, phih, Eh, Fh)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = plan.eval_host(qh, rh, phih, Eh, Fh)
+        if st != 0:
+            raise RuntimeError("sog_eval_host status %d" % st)
+    e2e_s = time.perf_counter() - t0
+    es = q.dtype.itemsize
+    e2e = {"value": N * args.steps / e2e_s, "unit": "particles/s",
+           "h2d_bytes_per_step": int(N * 4 * es), "d2h_bytes_per_step": int(N * 4 * es + 8)}
+
+    out = dict(plan=plan, stage_ms=stage_ms, value=value, total_ms=total_ms, times=times,
+               launches=launches, clocks=clk, e2e=e2e, E=float(Eh[0]), F=Fh.numpy().astype(np.float64),
+               q=q, r=r)
+    return out
+
+
+def oracle_run(prm, q, r):
+    import oracle
+    from oracle import sog as osog
+    oracle.build_oracle()
+    t0 = time.perf_counter()
+    ref = osog.sog_eval(prm, q.astype("float64"), r.astype("float64"))
+    return ref, time.perf_counter() - t0, oracle.num_threads()
+
+
+def emit(d):
+    print(json.dumps(d), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--n-nb", dest="n_nb", type=float, default=120.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    config = {"workload": wl["desc"], "N": wl["N"], "L": list(wl["L"]), "tol": wl["tol"],
+              "precision": args.precision, "n_nb": args.n_nb,
+              "l2": "flushed between steps (%d MiB write)" % (FLUSH_BYTES >> 20),
+              "parallelism": "replicas x%d" % world}
+
+    if args.impl == "reference":
+        # the oracle on the host cores, same workload, rank 0 only
+        if rank != 0:
+            return
+        import numpy as np
+        from oracle import sog as osog
+        from paper_2412_04595_gb300 import workloads
+        np_dt = np.float64 if args.precision == "fp64" else np.float32
+        q, r = workloads.uniform_neutral(wl["N"], wl["L"], wl["seed"], dtype=np_dt)
+        prm = osog.select_params(wl["N"], *wl["L"], wl["tol"], n_nb=args.n_nb)
+        for _ in range(args.warmup):
+            oracle_run(prm, q, r)
+        t = 0.0
+        cores = 1
+        for _ in range(args.steps):
+            _, dt, cores = oracle_run(prm, q, r)
+            t += dt
+        value = wl["N"] * args.steps / t
+        emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s",
+              "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+              "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                               "sample": "full workload, one FP64 oracle evaluation per step"},
+              "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": 0}})
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_ours(args, wl, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    import numpy as np
+    plan = res["plan"]
+    prm = plan.params
+    N = wl["N"]
+    hbm, smax, src = peaks()
+    fp32_peak = 152 * 128 * 2 * smax * 1e6 / 1e12          # TFLOP/s at the max SM clock
+    dom = max(res["stage_ms"], key=res["stage_ms"].get)
+    bound, work, work_desc = stage_units(prm, N, dom)
+    t_dom = res["stage_ms"][dom] * 1e-3
+    roof = None
+    if bound == "alu":
+        ach = work / t_dom / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None, "work_per_launch": work_desc,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
+    elif bound == "hbm":
+        ach = work / t_dom / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "work_per_launch": work_desc,
+                "peak_source": src}
+    line = {"metric": METRIC, "value": res["value"], "unit": "particles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "mixed" else "f64",
+            "data": "synthetic", "config": config, "e2e": res["e2e"],
+            "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": roof,
+            "stage_ms": {k: round(v, 5) for k, v in res["stage_ms"].items()},
+            "params": {k: prm[k] for k in ("rc", "M", "m", "I", "P_win", "I_long", "P_cheb")}}
+    if not args.no_cpu_baseline:
+        from oracle import sog as osog
+        oprm = osog.select_params(N, *wl["L"], wl["tol"], n_nb=args.n_nb)
+        ref, t_or, cores = oracle_run(oprm, res["q"], res["r"])
+        line["cpu_baseline"] = {"value": N / t_or, "unit": "particles/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "the full workload once (FP64 oracle, same inputs and parameters)"}
+        Fr = ref["F"]
+        line["accuracy_vs_oracle"] = {
+            "rel_energy": abs(res["E"] - ref["E"]) / abs(ref["E"]),
+            "rms_force": float(math.sqrt(np.mean(np.sum((res["F"] - Fr) ** 2, 1)) /
+                                         np.mean(np.sum(Fr ** 2, 1))))}
+    emit(line)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * sog.h -- C ABI of the GB300 spectral sum-of-Gaussians (SOG) library.
+ *
+ * Computes, for N point charges q_i at r_i in a box that is periodic in x and
+ * y and free in z, the potential of Eq. (2.6),
+ *     Phi_i = sum_j sum'_{n in Z^2 x {0}} q_j / |r_i - r_j + n o L|,
+ * the energy U = 1/2 sum_i q_i Phi_i and the forces F_i = -q_i grad Phi(r_i)
+ * (Sec. 2.3), by the spectral SOG method: the kernel split of Eq. (1.1) into
+ * a near field (direct sum over cell lists, Eq. 2.28), a mid range (3D
+ * spectral solver, Algorithm 1) and a long range (2D spectral solver with
+ * Chebyshev proxy points in z, Algorithm 2), minus the self term (Eq. 2.28).
+ * Gaussian units: no 1/(4 pi eps0) factor.
+ *
+ * Conventions shared by every entry point
+ *   - Box: the centred box of Sec. 2.1, x in [-Lx/2, Lx/2), y in
+ *     [-Ly/2, Ly/2), z in [-Lz/2, Lz/2].  x and y outside their interval
+ *     are wrapped by one period; z must lie inside its interval.
+ *   - The system must be neutral (Eq. 2.4): |sum q| <= 1e-10 sum |q|.
+ *   - Precision: the plan fixes the element type of q, r, phi and F:
+ *     double for SOG_PREC_FP64, float for SOG_PREC_MIXED.  E is always a
+ *     double.  r is N x 3 row-major (x0 y0 z0 x1 ...), F likewise.
+ *   - Memory: unless an entry point says "host", every array argument is a
+ *     device pointer on the plan's device, owned by the caller, and must stay
+ *     valid until the work enqueued on `stream` has finished.  The plan owns
+ *     all workspace memory, allocated once by sog_plan_create.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL: the legacy
+ *     default stream).  Device entry points only enqueue work and return; a
+ *     plan must not be used by two streams at the same time.
+ *   - Errors: argument errors are returned at once.  Data errors found on
+ *     the device (non-neutral charges, z outside the box, non-finite
+ *     coordinates) are latched in the plan and returned by sog_plan_check;
+ *     the outputs of such a call are unspecified but finite memory accesses
+ *     are guaranteed (coordinates are clamped into the grid).
+ */
+#ifndef SOG_H
+#define SOG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sog_plan sog_plan;
+
+typedef enum {
+  SOG_OK = 0,
+  SOG_ERR_ARG = 1,          /* invalid argument: NULL pointer, N < 2, L <= 0, tol not in (0, 0.1] */
+  SOG_ERR_NONNEUTRAL = 2,   /* |sum q| > 1e-10 sum |q| (Eq. 2.4); from sog_plan_check */
+  SOG_ERR_OUT_OF_BOX = 3,   /* a z outside [-Lz/2, Lz/2] or a non-finite coordinate; from sog_plan_check */
+  SOG_ERR_NOMEM = 4,        /* device or host allocation failed */
+  SOG_ERR_CUDA = 5,         /* a CUDA call or kernel launch failed */
+  SOG_ERR_PARAMS = 6        /* no feasible or an inconsistent parameter set */
+} sog_status;
+
+enum { SOG_PREC_FP64 = 0, SOG_PREC_MIXED = 1 };
+enum { SOG_WIN_ES = 0, SOG_WIN_GAUSS = 1 };
+
+/*
+ * Method parameters (Sec. 4.4 names).  Filled by sog_select_params or by the
+ * caller (sog_opts.manual).
+ *   L        box lengths (Lx, Ly, Lz)
+ *   b, r0, omega   SOG row (Table 1): bandwidth ratio, scaled cutoff, w_0 factor
+ *   sigma    = rc / r0; w_l, s_l of Eq. (2.22), (2.25), l = 0..M
+ *   rc       near-field cutoff, rc <= min(Lx, Ly)/2 (minimum image)
+ *   M        last Gaussian; m last mid-range Gaussian (Def. 3.2), -1: none;
+ *            Gaussians m+1..M are long range
+ *   I        mid grid Ix, Iy, Iz* (Iz* spans the padded box, Eq. 3.20)
+ *   hz       mid grid spacing in z; Lz* = Iz* hz
+ *   P_win    window support in grid points (Sec. 3.4), 2..16
+ *   shape    window shape: ES beta, or Gaussian S (Eq. 4.7)
+ *   I_long   long-range grid Ix_long, Iy_long (Sec. 3.4)
+ *   P_long, shape_long   long-range window support and shape
+ *   P_cheb   number of Chebyshev proxy points in z (Eq. A.6), 2..64
+ *   window   SOG_WIN_ES or SOG_WIN_GAUSS (Remark 3.4)
+ * Grid sizes must be even; Ix, Iy, Iz*, Ix_long, Iy_long factor into 2,3,5,7.
+ */
+typedef struct sog_params {
+  double L[3];
+  double b, r0, omega, sigma, rc;
+  int32_t M, m;
+  int32_t I[3];
+  double hz;
+  int32_t P_win;
+  double shape;
+  int32_t I_long[2];
+  int32_t P_long;
+  double shape_long;
+  int32_t P_cheb;
+  int32_t window;
+} sog_params;
+
+/*
+ * Plan options.  precision: SOG_PREC_*.  window: window of the analytic
+ * selection.  n_nb: neighbours per particle the cutoff is sized for
+ * ((4/3) pi rc^3 rho = n_nb); <= 0 selects 120.  manual: when non-NULL the
+ * parameters are used verbatim (N, L and tol arguments still checked).
+ */
+typedef struct sog_opts {
+  int32_t precision;
+  int32_t window;
+  double n_nb;
+  const sog_params* manual;
+} sog_opts;
+
+/*
+ * Analytic parameter selection of Sec. 4.4 (host only, no device work):
+ * Table 1 row, cutoff from the density, M, mid grid from K_max (Theorem 4.2),
+ * window support, then the split index m, padding Lz* and Chebyshev order P
+ * chosen by minimising an operation count (the role of Eq. 4.49) under the
+ * error constraints of Theorems 3.1, 4.4 and 4.7.  opts may be NULL.
+ * Returns SOG_ERR_ARG or SOG_ERR_PARAMS on failure; `out` is host memory.
+ */
+sog_status sog_select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
+                             const sog_opts* opts, sog_params* out);
+
+/*
+ * Create a plan for N charges in the box (Lx, Ly, Lz) at relative tolerance
+ * tol on the current CUDA device: selects (or takes) the parameters, builds
+ * the FP64 tables (SOG weights, window transforms, spectral scaling factors,
+ * Chebyshev z-kernels, near-field kernel table) and allocates every
+ * workspace.  *plan is owned by the caller and released by sog_plan_destroy.
+ * opts may be NULL (mixed precision, ES window, n_nb = 120).
+ */
+sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, double Lz,
+                           double tol, const sog_opts* opts);
+
+/* Copy the plan's parameters to host memory `out`. */
+sog_status sog_plan_get_params(const sog_plan* plan, sog_params* out);
+
+/* Element type of the plan's q, r, phi, F: SOG_PREC_FP64 or SOG_PREC_MIXED. */
+int32_t sog_plan_precision(const sog_plan* plan);
+
+/* Bytes of device memory the plan holds. */
+int64_t sog_plan_device_bytes(const sog_plan* plan);
+
+/*
+ * Evaluate potentials, energy and forces (Eq. 3.22 with the self term
+ * subtracted; U and F as in Sec. 2.3).
+ *   q    [N]      charges                         (device, plan type)
+ *   r    [N x 3]  positions                       (device, plan type)
+ *   phi  [N]      potentials Phi_i, or NULL       (device, plan type)
+ *   E    [1]      energy U, or NULL               (device, double)
+ *   F    [N x 3]  forces, or NULL                 (device, plan type)
+ * Enqueued on `stream`; returns without waiting.
+ */
+sog_status sog_eval(sog_plan* plan, const void* q, const void* r, void* phi, double* E,
+                    void* F, void* stream);
+
+/*
+ * Same work as sog_eval, but also (or only) returns the four parts of the
+ * potential before the self term, in double: part 0 near field (Eq. 2.28),
+ * 1 mid range (Algorithm 1), 2 long range without its k = 0 mode
+ * (Algorithm 2), 3 the k = 0 mode of the long range.
+ *   phi_parts  [4 x N]      device, double (NULL to skip)
+ *   grad_parts [4 x N x 3]  gradients of the parts, device, double (NULL to skip)
+ */
+sog_status sog_eval_components(sog_plan* plan, const void* q, const void* r,
+                               double* phi_parts, double* grad_parts, void* stream);
+
+/*
+ * sog_eval on host buffers: copies q and r to the device, evaluates, copies
+ * phi, E and F back (any of them may be NULL) and waits for completion.
+ * All pointers are host pointers of the plan's element type (E: double).
+ * Returns the data status of the call as sog_plan_check would.
+ */
+sog_status sog_eval_host(sog_plan* plan, const void* q, const void* r, void* phi, double* E,
+                         void* F);
+
+/*
+ * Wait for the plan's last stream, then return and clear the data status
+ * latched by the device since the previous check (SOG_ERR_NONNEUTRAL,
+ * SOG_ERR_OUT_OF_BOX), or SOG_ERR_CUDA if a launch failed.
+ */
+sog_status sog_plan_check(sog_plan* plan);
+
+/*
+ * Stage timers.  With timing enabled, every evaluation records CUDA events on
+ * its stream at the start of each stage; sog_plan_get_timing waits for the
+ * last evaluation and writes the device time of each stage in milliseconds
+ * to ms[SOG_NSTAGES] (host memory; 0 for stages that did not run):
+ *   0 binning and sorts        1 near field (Eq. 2.28)
+ *   2 mid gridding (Eq. 3.7)   3 mid FFT / scaling / inverse FFT (Eq. 3.8)
+ *   4 mid gathering (Eq. 3.10) 5 long gridding onto proxy planes
+ *   6 long 2D FFTs and z-contraction (Eq. 3.17)
+ *   7 long gathering (Eq. 3.19) 8 k = 0 mode       9 assembly and energy
+ */
+#define SOG_NSTAGES 10
+sog_status sog_plan_set_timing(sog_plan* plan, int32_t enable);
+sog_status sog_plan_get_timing(sog_plan* plan, float* ms);
+
+/* Number of kernels the last evaluation launched. */
+int64_t sog_plan_launches(const sog_plan* plan);
+
+/* Release the plan and its device memory (waits for its pending work). */
+void sog_plan_destroy(sog_plan* plan);
+
+/* Static description of a status code. */
+const char* sog_status_str(sog_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOG_H */

@@ -1,0 +1,231 @@
+"""Python binding of the C ABI in include/sog.h (argument marshalling only).
+
+Every computation runs in ``libsog.so``; this module converts PyTorch
+tensors to device pointers and streams and calls the entry points of the
+same names.  It raises if the library is missing: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+SOG_PREC_FP64, SOG_PREC_MIXED = 0, 1
+SOG_WIN_ES, SOG_WIN_GAUSS = 0, 1
+
+STATUS = {0: "SOG_OK", 1: "SOG_ERR_ARG", 2: "SOG_ERR_NONNEUTRAL", 3: "SOG_ERR_OUT_OF_BOX",
+          4: "SOG_ERR_NOMEM", 5: "SOG_ERR_CUDA", 6: "SOG_ERR_PARAMS"}
+
+
+class SogParams(ctypes.Structure):
+    """Mirror of ``sog_params`` (include/sog.h)."""
+    _fields_ = [("L", ctypes.c_double * 3), ("b", ctypes.c_double), ("r0", ctypes.c_double),
+                ("omega", ctypes.c_double), ("sigma", ctypes.c_double), ("rc", ctypes.c_double),
+                ("M", ctypes.c_int32), ("m", ctypes.c_int32), ("I", ctypes.c_int32 * 3),
+                ("hz", ctypes.c_double), ("P_win", ctypes.c_int32), ("shape", ctypes.c_double),
+                ("I_long", ctypes.c_int32 * 2), ("P_long", ctypes.c_int32),
+                ("shape_long", ctypes.c_double), ("P_cheb", ctypes.c_int32),
+                ("window", ctypes.c_int32)]
+
+    def to_dict(self):
+        return dict(L=tuple(self.L), b=self.b, r0=self.r0, omega=self.omega, sigma=self.sigma,
+                    rc=self.rc, M=self.M, m=self.m, I=tuple(self.I), hz=self.hz,
+                    P_win=self.P_win, shape=self.shape, I_long=tuple(self.I_long),
+                    P_long=self.P_long, shape_long=self.shape_long, P_cheb=self.P_cheb,
+                    window="es" if self.window == SOG_WIN_ES else "gauss")
+
+    @classmethod
+    def from_dict(cls, d):
+        p = cls()
+        p.L[:] = list(d["L"])
+        for k in ("b", "r0", "omega", "sigma", "rc", "hz", "shape", "shape_long"):
+            setattr(p, k, float(d[k]))
+        for k in ("M", "m", "P_win", "P_long", "P_cheb"):
+            setattr(p, k, int(d[k]))
+        p.I[:] = list(d["I"])
+        p.I_long[:] = list(d["I_long"])
+        p.window = SOG_WIN_ES if d.get("window", "es") == "es" else SOG_WIN_GAUSS
+        return p
+
+
+class SogOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("n_nb", ctypes.c_double), ("manual", ctypes.POINTER(SogParams))]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsog.so (built by ``_build.build()``).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError("libsog.so is not built: run __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, d, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int32
+    L.sog_select_params.argtypes = [i64, d, d, d, d, ctypes.POINTER(SogOpts), ctypes.POINTER(SogParams)]
+    L.sog_plan_create.argtypes = [ctypes.POINTER(vp), i64, d, d, d, d, ctypes.POINTER(SogOpts)]
+    L.sog_plan_get_params.argtypes = [vp, ctypes.POINTER(SogParams)]
+    L.sog_plan_precision.argtypes = [vp]
+    L.sog_plan_precision.restype = i32
+    L.sog_plan_device_bytes.argtypes = [vp]
+    L.sog_plan_device_bytes.restype = i64
+    L.sog_eval.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.sog_eval_components.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.sog_eval_host.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.sog_plan_check.argtypes = [vp]
+    L.sog_plan_destroy.argtypes = [vp]
+    L.sog_plan_destroy.restype = None
+    L.sog_plan_set_timing.argtypes = [vp, i32]
+    L.sog_plan_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.sog_plan_launches.argtypes = [vp]
+    L.sog_plan_launches.restype = i64
+    L.sog_status_str.argtypes = [ctypes.c_int]
+    L.sog_status_str.restype = ctypes.c_char_p
+    for f in ("sog_select_params", "sog_plan_create", "sog_plan_get_params", "sog_eval",
+              "sog_eval_components", "sog_eval_host", "sog_plan_check", "sog_plan_set_timing",
+              "sog_plan_get_timing"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class SogError(RuntimeError):
+    def __init__(self, code, where):
+        msg = load().sog_status_str(code).decode()
+        super().__init__("%s: %s (%s)" % (where, STATUS.get(code, code), msg))
+        self.code = code
+
+
+def _check(code, where):
+    if code != 0:
+        raise SogError(code, where)
+
+
+def _opts(precision, window, n_nb, manual):
+    o = SogOpts()
+    o.precision = precision
+    o.window = window
+    o.n_nb = float(n_nb) if n_nb else 0.0
+    if manual is not None:
+        mp = manual if isinstance(manual, SogParams) else SogParams.from_dict(manual)
+        o._manual_ref = mp
+        o.manual = ctypes.pointer(mp)
+    return o
+
+
+def sog_select_params(N, Lx, Ly, Lz, tol, window=SOG_WIN_ES, n_nb=None) -> dict:
+    out = SogParams()
+    o = _opts(SOG_PREC_MIXED, window, n_nb, None)
+    _check(load().sog_select_params(int(N), Lx, Ly, Lz, tol, ctypes.byref(o), ctypes.byref(out)),
+           "sog_select_params")
+    return out.to_dict()
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """Owns one ``sog_plan``.  Tensors passed to ``eval`` must be contiguous
+    CUDA tensors of the plan's dtype (float64 for FP64, float32 for mixed)."""
+
+    def __init__(self, N, L, tol, precision=SOG_PREC_MIXED, window=SOG_WIN_ES, n_nb=None,
+                 manual=None):
+        L_ = tuple(map(float, L))
+        self.N = int(N)
+        self._lib = load()
+        self._opts = _opts(precision, window, n_nb, manual)
+        h = ctypes.c_void_p()
+        _check(self._lib.sog_plan_create(ctypes.byref(h), self.N, L_[0], L_[1], L_[2], float(tol),
+                                         ctypes.byref(self._opts)), "sog_plan_create")
+        self._h = h
+        self.precision = precision
+        out = SogParams()
+        _check(self._lib.sog_plan_get_params(h, ctypes.byref(out)), "sog_plan_get_params")
+        self.params = out.to_dict()
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == SOG_PREC_FP64 else torch.float32
+
+    def device_bytes(self) -> int:
+        return int(self._lib.sog_plan_device_bytes(self._h))
+
+    def _check_in(self, *ts):
+        for t in ts:
+            if t is None:
+                continue
+            if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous():
+                raise ValueError("expected contiguous CUDA %s tensors" % self.dtype)
+
+    def eval(self, q, r, phi=None, E=None, F=None, stream=None):
+        """sog_eval: enqueue the evaluation; outputs are written in place."""
+        self._check_in(q, r, phi, F)
+        if E is not None and (not E.is_cuda or E.dtype.itemsize != 8):
+            raise ValueError("E must be a CUDA float64 tensor")
+        _check(self._lib.sog_eval(self._h, _ptr(q), _ptr(r), _ptr(phi), _ptr(E), _ptr(F),
+                                  _stream_ptr(stream)), "sog_eval")
+
+    def eval_components(self, q, r, phi_parts, grad_parts, stream=None):
+        self._check_in(q, r)
+        _check(self._lib.sog_eval_components(self._h, _ptr(q), _ptr(r), _ptr(phi_parts),
+                                             _ptr(grad_parts), _stream_ptr(stream)),
+               "sog_eval_components")
+
+    def eval_host(self, q, r, phi=None, E=None, F=None):
+        """sog_eval_host on numpy arrays or CPU tensors (pinned for speed)."""
+        def hp(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return ctypes.c_void_p(a.data_ptr())
+            return ctypes.c_void_p(a.ctypes.data)
+        return self._lib.sog_eval_host(self._h, hp(q), hp(r), hp(phi), hp(E), hp(F))
+
+    STAGES = ("binning", "near", "mid_spread", "mid_fft", "mid_gather", "long_spread",
+              "long_fft", "long_gather", "k0", "assemble")
+
+    def set_timing(self, enable: bool):
+        _check(self._lib.sog_plan_set_timing(self._h, int(bool(enable))), "sog_plan_set_timing")
+
+    def timing(self) -> dict:
+        """Device milliseconds of each stage of the last evaluation."""
+        buf = (ctypes.c_float * len(self.STAGES))()
+        _check(self._lib.sog_plan_get_timing(self._h, buf), "sog_plan_get_timing")
+        return dict(zip(self.STAGES, [float(x) for x in buf]))
+
+    def launches(self) -> int:
+        return int(self._lib.sog_plan_launches(self._h))
+
+    def check(self) -> int:
+        return int(self._lib.sog_plan_check(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sog_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

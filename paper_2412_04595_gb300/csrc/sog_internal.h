@@ -1,0 +1,158 @@
+// Internal declarations of the GB300 SOG library: the plan, device-side
+// geometry records and the launch helpers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/sog.h"
+
+namespace sogk {
+
+constexpr int kMaxFftStages = 16;
+constexpr int kMaxCheb = 64;
+constexpr int kMaxWin = 16;
+
+// One FFT length: radix sequence of the Stockham stages and the offset of its
+// n roots of unity exp(-2 pi i t / n) in the twiddle table.
+struct FftLen {
+  int n;
+  int nst;
+  int radix[kMaxFftStages];
+  int tw_off;
+};
+
+// Particle record (x, y, z, q) or (local grid coordinates, q).
+template <typename T>
+struct alignas(4 * sizeof(T)) P4 {
+  T x, y, z, q;
+};
+
+// Window of Sec. 3.4 / Remark 3.4 on a support of P grid points,
+// half-width `half` = (P-1)/2 grid units, shape beta (ES) or S (Gaussian).
+struct WinPar {
+  int P;
+  int kind;          // SOG_WIN_ES or SOG_WIN_GAUSS
+  double half;
+  double shape;
+};
+
+// Tiling of a periodic grid for spreading / gathering.
+struct TileGeom {
+  int I[3];          // grid sizes (z unused in 2D)
+  int T[3];          // tile edge
+  int nt[3];         // tiles per dimension
+  int W[3];          // padded tile edge = T + P
+  int pad_lo;        // floor(half): padded tile starts pad_lo before the tile
+  int pitch;         // row pitch of the real grid (I[0] + 2)
+  int chunks;        // CTAs per tile
+};
+
+// Sizes of one evaluation's reduction scratch.
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+// Largest dynamic shared memory of one CTA on sm_100-class GPUs (227 KB).
+constexpr int kMaxDynSmem = 232448;
+// Captured evaluations kept per plan (keyed by the caller's pointers).
+constexpr int kMaxGraphs = 4;
+
+struct GraphEntry {
+  const void* q;
+  const void* r;
+  void* phi;
+  double* E;
+  void* F;
+  double* pp;
+  double* pg;
+  int timing;                      // stage events captured in the graph
+  int ev_used[16];
+  cudaGraphExec_t exec;
+  int64_t launches;
+  uint64_t last_use;
+};
+
+}  // namespace sogk
+
+struct sog_plan {
+  sog_params prm;
+  int prec;
+  int64_t N;
+  int device;
+  // derived geometry
+  double h[3];        // mid grid spacing
+  double Lzs;         // padded box Lz*
+  double hl[2];       // long grid spacing
+  bool has_mid, has_long;
+  int nc[3];          // near-field cells
+  double cell[3];
+  int n_cells;
+  sogk::TileGeom gm, gl;
+  int n_tiles_mid, n_tiles_long;
+  sogk::WinPar wm, wl;
+  sogk::FftLen fx, fy, fz, flx, fly;
+  int near_K, near_D;
+  double selfsum;
+  // device arena and typed views (element type T = plan precision)
+  void* arena;
+  int64_t arena_bytes;
+  void* d_tw;          // twiddles, T2
+  void* d_near_tab;    // near table, T
+  void* d_mult;        // mid scaling factors, T
+  void* d_kmat;        // long z-kernels per mode, T
+  double* d_k0mat;     // k = 0 z-kernel, P x P, double
+  void* d_grid;        // mid grid, T
+  void* d_lA;          // long planes, T
+  void* d_lB;          // long planes after the z-contraction, T
+  void* d_rec_near;    // P4<T>
+  void* d_rec_mid;
+  void* d_rec_long;
+  void* d_rec_tmp;     // 3 x N records in input order (binning)
+  int* d_perm;         // 3 x N
+  int* d_key;          // 3 x N
+  int* d_rank;         // 3 x N
+  int* d_cnt;          // counts / starts of the three bin sets
+  int cnt_off[4];
+  double* d_parts_phi;   // 4 x N
+  double* d_parts_grad;  // 4 x N x 3
+  double* d_red;         // reduction partials
+  double* d_k0nu;        // P
+  int* d_status;         // latched data errors (bit 0 non-neutral, bit 1 out of box)
+  void* d_host_stage;    // device copies of q, r, phi, F, E for sog_eval_host
+  int long_small;        // long planes small enough for one private copy per CTA
+  int long_small_blocks;
+  void* d_long_partial;  // per-CTA copies of the long planes (small path)
+  int launch_error;
+  cudaStream_t last_stream;
+  // stage timers (sog_plan_set_timing) and kernel launch count of the last eval
+  int timing, events_ready;
+  cudaEvent_t ev[SOG_NSTAGES + 1];
+  int ev_used[SOG_NSTAGES + 1];
+  int64_t launches;
+  // captured evaluations replayed with one cudaGraphLaunch
+  cudaStream_t cap_stream;
+  sogk::GraphEntry graphs[sogk::kMaxGraphs];
+  int n_graphs;
+  uint64_t use_clock;
+  int use_graphs;
+};
+
+namespace sogk {
+
+// Host-side launchers (sog_fft.cu).
+template <typename T>
+cudaError_t fft_mid_forward_conv_inverse(const sog_plan* p, cudaStream_t s);
+template <typename T>
+cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s);
+template <typename T>
+cudaError_t fft_prepare();
+
+// One-time kernel attributes for the plan's element type (sog_kernels.cu).
+cudaError_t prepare_kernels(int prec);
+void release_graphs(sog_plan* p);
+
+// Evaluation driver (sog_kernels.cu).
+sog_status eval_device(sog_plan* p, const void* q, const void* r, void* phi, double* E, void* F,
+                       double* phi_parts, double* grad_parts, cudaStream_t s);
+
+}  // namespace sogk

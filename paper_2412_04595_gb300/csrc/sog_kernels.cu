@@ -1,0 +1,1565 @@
+// Device kernels and the evaluation driver of the spectral SOG method.
+//
+// One evaluation (sog_eval) runs, on one stream:
+//   1. binning: every particle gets a near-field cell (cells >= r_c, Sec. 2.2
+//      cell list), a mid-grid tile and a long-grid tile; three counting sorts
+//      produce cell-/tile-sorted particle records;
+//   2. near field Phi^N (Eq. 2.28) over the 27 neighbouring cells, kernel
+//      1/r - F_M(r) from a piecewise-polynomial table (Remark 2.4);
+//   3. mid range, Algorithm 1: gridding (Eq. 3.7) tile by tile in shared
+//      memory, FFT / scaling (Eq. 3.8) / inverse FFT, gathering (Eq. 3.10)
+//      with the window gradient for the forces;
+//   4. long range, Algorithm 2 (anterpolation form): charges times the
+//      Chebyshev polynomials T_n(2z/Lz) spread in x,y onto P proxy planes,
+//      2D FFTs, per-mode z-contraction with the kernel of Eq. 3.13 / 4.40
+//      written in the Chebyshev basis, inverse 2D FFTs, gathering with
+//      T_n(2 z_i/Lz) (and T_n' for the z force);
+//   5. the k = 0 mode of the long range in FP64 from exact Chebyshev moments;
+//   6. assembly Phi = sum of parts - q sum_l w_l (Eq. 3.22, 2.28), forces,
+//      energy U = 1/2 sum q Phi reduced in FP64 in a fixed order.
+// The element type T is float (mixed precision) or double (FP64).
+#include <math.h>
+
+#include "sog_internal.h"
+
+namespace sogk {
+
+template <typename T>
+cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// geometry passed to the kernels
+// ---------------------------------------------------------------------------
+
+struct PrepGeom {
+  double L[3], halfL[3];
+  int nc[3];
+  double icell[3];   // 1 / cell edge
+  int has_mid, has_long;
+  double ih[3], Lzs_half;  // 1 / mid grid spacing
+  int Tm[3], ntm[3];
+  double iTm[3];
+  double ihl[2];     // 1 / long grid spacing
+  int Tl[2], ntl[2];
+  double iTl[2];
+  double ihalfLz;
+};
+
+template <typename T>
+struct WinT {
+  int P, kind;
+  T half, inv_half, shape;
+};
+
+template <typename T>
+__host__ WinT<T> wint(const WinPar& w) {
+  WinT<T> o;
+  o.P = w.P;
+  o.kind = w.kind;
+  o.half = (T)w.half;
+  o.inv_half = (T)(1.0 / w.half);
+  o.shape = (T)w.shape;
+  return o;
+}
+
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dceil(float x) { return ceilf(x); }
+__device__ __forceinline__ double dceil(double x) { return ceil(x); }
+__device__ __forceinline__ float drint(float x) { return rintf(x); }
+__device__ __forceinline__ double drint(double x) { return rint(x); }
+__device__ __forceinline__ float drsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double drsqrt(double x) { return rsqrt(x); }
+
+// Window phi(v) (v = offset / half-width) and d phi / dv; zero outside |v| <= 1.
+template <typename T>
+__device__ __forceinline__ void win_eval(const WinT<T>& w, T v, T& val, T& dval) {
+  const T one = T(1);
+  val = T(0);
+  dval = T(0);
+  if (!(v >= -one && v <= one)) return;
+  if (w.kind == SOG_WIN_ES) {
+    // beta (sqrt(1 - v^2) - 1) written as -beta v^2 / (1 + sqrt(1 - v^2)):
+    // no cancellation near the window centre, where the weights are largest
+    const T a2 = (one - v) * (one + v);
+    const T a = dsqrt(a2);
+    val = dexp(-w.shape * v * v / (one + a));
+    if (a2 > T(0)) dval = -val * w.shape * v * drsqrt(a2);
+  } else {
+    val = dexp(-w.shape * v * v);
+    dval = T(-2) * w.shape * v * val;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 1. binning
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ int floor_clamp(double t, int n) {
+  if (!(t >= 0.0)) return 0;  // also NaN
+  if (t >= (double)n) return n - 1;
+  return (int)t;
+}
+
+// Wrap / clamp one particle and compute its bins and tile-local records.
+template <typename T>
+__device__ void prep_particle(const PrepGeom& g, const T* __restrict__ q, const T* __restrict__ r,
+                              int i, int& bits, P4<T>& rn, int& kn, int& km, P4<T>& rm, int& kl,
+                              P4<T>& rl) {
+  T x = r[3 * i], y = r[3 * i + 1], z = r[3 * i + 2], qi = q[i];
+  T c[3] = {x, y, z};
+  for (int d = 0; d < 2; ++d) {
+    const T Ld = (T)g.L[d];
+    if ((double)c[d] >= g.halfL[d]) c[d] = c[d] - Ld;
+    else if ((double)c[d] < -g.halfL[d]) c[d] = c[d] + Ld;
+    if (!((double)c[d] >= -g.halfL[d] && (double)c[d] < g.halfL[d])) {
+      bits |= 2;
+      c[d] = isfinite((double)c[d]) ? ((double)c[d] < 0 ? (T)(-g.halfL[d]) : (T)0) : (T)0;
+    }
+  }
+  if (!((double)c[2] >= -g.halfL[2] && (double)c[2] <= g.halfL[2])) {
+    bits |= 2;
+    c[2] = isfinite((double)c[2]) ? ((double)c[2] < 0 ? (T)(-g.halfL[2]) : (T)(g.halfL[2])) : (T)0;
+  }
+  if (!isfinite((double)qi)) {
+    bits |= 2;
+    qi = (T)0;
+  }
+  rn = P4<T>{c[0], c[1], c[2], qi};
+  // near-field cell (cells of edge >= r_c; z cells clamp at the open walls)
+  int cc[3];
+  for (int d = 0; d < 3; ++d) cc[d] = floor_clamp(((double)c[d] + g.halfL[d]) * g.icell[d], g.nc[d]);
+  kn = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
+  km = 0;
+  kl = 0;
+  if (g.has_mid) {
+    double t[3];
+    t[0] = ((double)c[0] + g.halfL[0]) * g.ih[0];
+    t[1] = ((double)c[1] + g.halfL[1]) * g.ih[1];
+    t[2] = ((double)c[2] + g.Lzs_half) * g.ih[2];
+    int tt[3];
+    double loc[3];
+    for (int d = 0; d < 3; ++d) {
+      tt[d] = floor_clamp(t[d] * g.iTm[d], g.ntm[d]);
+      loc[d] = t[d] - (double)tt[d] * g.Tm[d];
+    }
+    km = (tt[2] * g.ntm[1] + tt[1]) * g.ntm[0] + tt[0];
+    rm = P4<T>{(T)loc[0], (T)loc[1], (T)loc[2], qi};
+  }
+  if (g.has_long) {
+    double t[2];
+    t[0] = ((double)c[0] + g.halfL[0]) * g.ihl[0];
+    t[1] = ((double)c[1] + g.halfL[1]) * g.ihl[1];
+    int tt[2];
+    double loc[2];
+    for (int d = 0; d < 2; ++d) {
+      tt[d] = floor_clamp(t[d] * g.iTl[d], g.ntl[d]);
+      loc[d] = t[d] - (double)tt[d] * g.Tl[d];
+    }
+    kl = tt[1] * g.ntl[0] + tt[0];
+    rl = P4<T>{(T)loc[0], (T)loc[1], (T)((double)c[2] * g.ihalfLz), qi};
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of a double; result valid in thread 0.
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;
+}
+
+// Rank of this thread's particle inside bin `key`: one atomic per group of
+// lanes of the warp that share the key (many particles share a bin).
+__device__ __forceinline__ int agg_rank(int* __restrict__ cnt, int key) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(cnt + key, __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+template <typename T>
+__global__ void k_bin_count(PrepGeom g, const T* __restrict__ q, const T* __restrict__ r, int N,
+                            int* __restrict__ key, int* __restrict__ rank, int* __restrict__ cnt,
+                            int3 off, P4<T>* __restrict__ tmp, double* __restrict__ red,
+                            int* __restrict__ status) {
+  __shared__ double sh[32];
+  double sq = 0.0, sa = 0.0;
+  int bits = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    P4<T> rn, rm, rl;
+    int kn, km, kl;
+    prep_particle<T>(g, q, r, i, bits, rn, kn, km, rm, kl, rl);
+    key[i] = kn;
+    rank[i] = agg_rank(cnt + off.x, kn);
+    tmp[i] = rn;
+    if (g.has_mid) {
+      key[N + i] = km;
+      rank[N + i] = agg_rank(cnt + off.y, km);
+      tmp[N + i] = rm;
+    }
+    if (g.has_long) {
+      key[2 * N + i] = kl;
+      rank[2 * N + i] = agg_rank(cnt + off.z, kl);
+      tmp[2 * N + i] = rl;
+    }
+    sq += (double)rn.q;
+    sa += fabs((double)rn.q);
+  }
+  if (bits) atomicOr(status, bits);
+  const double tq = block_sum(sq, sh);
+  const double ta = block_sum(sa, sh);
+  if (threadIdx.x == 0) {
+    red[2 * blockIdx.x] = tq;
+    red[2 * blockIdx.x + 1] = ta;
+  }
+}
+
+// Exclusive scan of three count arrays (one CTA each): cnt[off + k] for
+// k < n becomes the start of bin k, cnt[off + n] the total.
+__global__ void k_scan3(int* __restrict__ cnt, int3 off, int3 nbins) {
+  const int which = blockIdx.x;
+  const int o = which == 0 ? off.x : (which == 1 ? off.y : off.z);
+  const int n = which == 0 ? nbins.x : (which == 1 ? nbins.y : nbins.z);
+  if (n <= 0) return;
+  int* a = cnt + o;
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base <= n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = (i < n) ? a[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int s = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, s, d);
+        if (lane >= d) s += y;
+      }
+      wsum[lane] = s;
+    }
+    __syncthreads();
+    const int excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+    if (i <= n) a[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_bin_scatter(int N, int has_mid, int has_long, const int* __restrict__ key,
+                              const int* __restrict__ rank, const int* __restrict__ cnt, int3 off,
+                              const P4<T>* __restrict__ tmp, P4<T>* __restrict__ rec_n,
+                              P4<T>* __restrict__ rec_m, P4<T>* __restrict__ rec_l,
+                              int* __restrict__ perm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    int pos = cnt[off.x + key[i]] + rank[i];
+    rec_n[pos] = tmp[i];
+    perm[pos] = i;
+    if (has_mid) {
+      pos = cnt[off.y + key[N + i]] + rank[N + i];
+      rec_m[pos] = tmp[N + i];
+      perm[N + pos] = i;
+    }
+    if (has_long) {
+      pos = cnt[off.z + key[2 * N + i]] + rank[2 * N + i];
+      rec_l[pos] = tmp[2 * N + i];
+      perm[2 * N + pos] = i;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. near field
+// ---------------------------------------------------------------------------
+
+struct NearGeom {
+  double halfL[3];
+  double cell[3];
+  int nc[3];
+  double L[2];
+  double rc;
+  int K, D;
+};
+
+// Compensated (Neumaier) accumulation for the FP32 path: the near-field sum
+// adds ~100 terms whose largest (1/r of a close pair) sets the rounding of
+// every later addition; the compensation keeps the sum at one rounding.
+template <typename T>
+struct Acc {
+  T s, c;
+  __device__ __forceinline__ void add(T v) {
+    const T t = s + v;
+    c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ T get() const { return s + c; }
+};
+
+constexpr int kNearThreads = 256;
+constexpr int kNearQ = 64;       // per-warp queue of accepted pairs
+// source particles staged per pass and table entries kept in shared memory
+// (static shared memory stays under 48 KB for both element types)
+template <typename T> struct NearCfg;
+template <> struct NearCfg<float> { static constexpr int src = 1280, tab = 2304; };
+template <> struct NearCfg<double> { static constexpr int src = 640, tab = 576; };
+
+// Near field, Eq. (2.28): one CTA per cell, the particles of the (up to 27)
+// neighbouring cells staged in shared memory (whole cells per pass; one pass
+// in the usual case).  A warp takes one target at a time and walks the staged
+// cells: its lanes test 32 candidate sources per step, the pairs inside r_c
+// are compacted into a per-warp queue (ballot + prefix count), and every full
+// batch of 32 queued pairs is evaluated with all lanes busy, so the kernel
+// table is only evaluated for accepted pairs and without divergence.
+//
+// Minimum image: with at least three cells per periodic dimension a source
+// cell beyond the box edge is an image at a known shift, and the difference
+// is formed as (x_i + s) - (x_j - s) with s = +-L/2; both brackets are exact
+// (Sterbenz), so a wrapped pair keeps the accuracy of an unwrapped one.
+// With fewer cells the shift is found per pair by rounding.
+template <typename T>
+__global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* __restrict__ rec,
+                                                      const int* __restrict__ cstart,
+                                                      const int* __restrict__ perm,
+                                                      const T* __restrict__ tab,
+                                                      double* __restrict__ phi_out,
+                                                      double* __restrict__ grad_out) {
+  constexpr int kNearSrc = NearCfg<T>::src, kNearTab = NearCfg<T>::tab;
+  __shared__ P4<T> src[kNearSrc];                  // x - s, y - s, z, q
+  __shared__ P4<T> qd[kNearThreads / 32][kNearQ];  // dx, dy, dz, q_j
+  __shared__ T qr[kNearThreads / 32][kNearQ];      // r^2
+  __shared__ T stab[kNearTab];
+  __shared__ int cb[27], cn[27];                   // first source, count per cell
+  __shared__ T csx[27], csy[27];
+  __shared__ int seg_c[64], seg_b[64], seg_n[64], seg_o[64];  // staged segments
+  __shared__ int ncell, nseg;
+  const int c = blockIdx.x;
+  const int tb = cstart[c], te = cstart[c + 1];
+  if (tb == te) return;
+  const int ntab = g.K * (g.D + 1);
+  const bool tab_sm = ntab <= kNearTab;
+  if (tab_sm)
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) stab[i] = tab[i];
+  const bool shifted = g.nc[0] >= 3 && g.nc[1] >= 3;
+  const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
+  if (threadIdx.x == 0) {
+    int lo[3], hi[3];
+    const int cc[3] = {cx, cy, cz};
+    for (int d = 0; d < 2; ++d) {
+      if (g.nc[d] >= 3) { lo[d] = cc[d] - 1; hi[d] = cc[d] + 1; }
+      else { lo[d] = 0; hi[d] = g.nc[d] - 1; }
+    }
+    lo[2] = max(cz - 1, 0);
+    hi[2] = min(cz + 1, g.nc[2] - 1);
+    int n = 0;
+    for (int z = lo[2]; z <= hi[2]; ++z)
+      for (int y0 = lo[1]; y0 <= hi[1]; ++y0)
+        for (int x0 = lo[0]; x0 <= hi[0]; ++x0) {
+          const int y = (y0 + g.nc[1]) % g.nc[1], x = (x0 + g.nc[0]) % g.nc[0];
+          const int k = (z * g.nc[1] + y) * g.nc[0] + x;
+          cb[n] = cstart[k];
+          cn[n] = cstart[k + 1] - cstart[k];
+          // source beyond the -L/2 edge sits near +L/2: s = +L/2, and vice versa
+          csx[n] = !shifted ? T(0) : (x0 < 0 ? (T)g.halfL[0] : (x0 >= g.nc[0] ? (T)(-g.halfL[0]) : T(0)));
+          csy[n] = !shifted ? T(0) : (y0 < 0 ? (T)g.halfL[1] : (y0 >= g.nc[1] ? (T)(-g.halfL[1]) : T(0)));
+          ++n;
+        }
+    ncell = n;
+  }
+  __syncthreads();
+  const T* tb_ = tab_sm ? stab : tab;
+  const T Lx = (T)g.L[0], Ly = (T)g.L[1];
+  const T iLx = (T)(1.0 / g.L[0]), iLy = (T)(1.0 / g.L[1]);
+  const T rc = (T)g.rc, rc2 = rc * rc;
+  const T hK = rc / (T)g.K, ihK = (T)g.K / rc, ihK2 = T(2) * ihK;
+  const int D = g.D;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNearThreads / 32;
+  const unsigned lt = (1u << lane) - 1u;
+  P4<T>* myq = qd[warp];
+  T* myr = qr[warp];
+  const int ntg = te - tb;
+  // passes over the neighbourhood: whole cells (split if larger than the buffer)
+  int cell0 = 0, off0 = 0;
+  bool first = true;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int used = 0, ns = 0;
+      while (cell0 < ncell && ns < 64) {
+        const int take = min(cn[cell0] - off0, kNearSrc - used);
+        if (take <= 0 && cn[cell0] - off0 > 0) break;  // buffer full
+        if (take > 0) {
+          seg_c[ns] = cell0;
+          seg_b[ns] = cb[cell0] + off0;
+          seg_n[ns] = take;
+          seg_o[ns] = used;
+          ++ns;
+          used += take;
+        }
+        off0 += max(take, 0);
+        if (off0 >= cn[cell0]) {
+          ++cell0;
+          off0 = 0;
+        }
+      }
+      nseg = ns;
+    }
+    __syncthreads();
+    const int ns = nseg;
+    if (ns == 0) break;
+    for (int sgi = warp; sgi < ns; sgi += nw) {
+      const int cc = seg_c[sgi], b0 = seg_b[sgi], n0 = seg_n[sgi], o0 = seg_o[sgi];
+      const T sx = csx[cc], sy = csy[cc];
+      for (int k = lane; k < n0; k += 32) {
+        P4<T> b = rec[b0 + k];
+        b.x = b.x - sx;
+        b.y = b.y - sy;
+        src[o0 + k] = b;
+      }
+    }
+    __syncthreads();
+    for (int t0 = 0; t0 < ntg; t0 += nw) {
+      const int tt = t0 + warp;
+      if (tt >= ntg) break;
+      const int ti = tb + tt;
+      const P4<T> a = rec[ti];
+      Acc<T> phi{0, 0};
+      T gx = 0, gy = 0, gz = 0;
+      int qn = 0, qh = 0;  // queued, evaluated (warp-uniform)
+      auto eval_batch = [&](int cnt) {
+        if (lane < cnt) {
+          const int e = (qh + lane) & (kNearQ - 1);
+          const P4<T> d = myq[e];
+          const T r2 = myr[e];
+          const T rr = dsqrt(r2);
+          const T rinv = T(1) / rr;
+          int kk = (int)(rr * ihK);
+          kk = kk < g.K ? kk : g.K - 1;
+          const T u = (rr - (T)kk * hK) * ihK2 - T(1);
+          const T* cf = tb_ + kk * (D + 1);
+          T p = cf[D], dp = T(0);
+          for (int jj = D - 1; jj >= 0; --jj) {
+            dp = dp * u + p;
+            p = p * u + cf[jj];
+          }
+          // g(r) = 1 - r F_M(r) = p; near kernel G = g/r; dG/dr = (g' - g/r)/r
+          const T gp = dp * ihK2;
+          phi.add(d.q * p * rinv);
+          const T f = d.q * (gp - p * rinv) * rinv * rinv;
+          gx += f * d.x;
+          gy += f * d.y;
+          gz += f * d.z;
+        }
+        qh += cnt;
+      };
+      for (int sgi = 0; sgi < ns; ++sgi) {
+        const int cc = seg_c[sgi], n0 = seg_n[sgi], o0 = seg_o[sgi];
+        const T ax = a.x + csx[cc], ay = a.y + csy[cc];
+        for (int k0 = 0; k0 < n0; k0 += 32) {
+          const int k = k0 + lane;
+          bool in = false;
+          T dx = 0, dy = 0, dz = 0, r2 = 0, qj = 0;
+          if (k < n0) {
+            const P4<T> b = src[o0 + k];
+            dx = ax - b.x;
+            dy = ay - b.y;
+            dz = a.z - b.z;
+            if (!shifted) {
+              dx -= Lx * drint(dx * iLx);
+              dy -= Ly * drint(dy * iLy);
+            }
+            r2 = dx * dx + dy * dy + dz * dz;
+            qj = b.q;
+            // r2 == 0 only for the target itself (coincident charges are invalid input)
+            in = r2 < rc2 && r2 > T(0);
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, in);
+          if (in) {
+            const int e = (qn + __popc(m & lt)) & (kNearQ - 1);
+            myq[e] = P4<T>{dx, dy, dz, qj};
+            myr[e] = r2;
+          }
+          qn += __popc(m);
+          __syncwarp();
+          if (qn - qh >= 32) {
+            eval_batch(32);
+            __syncwarp();
+          }
+        }
+      }
+      if (qn - qh > 0) eval_batch(qn - qh);
+      T v0 = phi.get(), v1 = gx, v2 = gy, v3 = gz;
+      v0 = warp_sum(v0);
+      v1 = warp_sum(v1);
+      v2 = warp_sum(v2);
+      v3 = warp_sum(v3);
+      if (lane == 0) {
+        const int o = perm[ti];
+        if (first) {
+          phi_out[o] = (double)v0;
+          grad_out[3 * o] = (double)v1;
+          grad_out[3 * o + 1] = (double)v2;
+          grad_out[3 * o + 2] = (double)v3;
+        } else {
+          phi_out[o] += (double)v0;
+          grad_out[3 * o] += (double)v1;
+          grad_out[3 * o + 1] += (double)v2;
+          grad_out[3 * o + 2] += (double)v3;
+        }
+      }
+      __syncwarp();
+    }
+    first = false;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. mid range (Algorithm 1): gridding and gathering
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int pmod(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+// Shared-memory layout of the tile kernels: padded tile, then the per-CTA
+// row table (offset of window row (dy, dz) in the padded tile, and dy, dz),
+// then per-warp weight vectors.
+template <typename T>
+struct MidSmem {
+  T* tile;
+  int* rowoff;
+  unsigned char* rdy;
+  unsigned char* rdz;
+  T* ws;
+};
+
+template <typename T>
+__device__ __forceinline__ MidSmem<T> mid_smem_layout(unsigned char* raw, const TileGeom& g, int P) {
+  MidSmem<T> m;
+  const int Wn = g.W[0] * g.W[1] * g.W[2];
+  m.tile = reinterpret_cast<T*>(raw);
+  m.rowoff = reinterpret_cast<int*>(m.tile + Wn);
+  m.rdy = reinterpret_cast<unsigned char*>(m.rowoff + kMaxWin * kMaxWin);
+  m.rdz = m.rdy + kMaxWin * kMaxWin;
+  m.ws = reinterpret_cast<T*>(m.rdz + kMaxWin * kMaxWin);  // offset is a multiple of 8
+  return m;
+}
+
+__device__ __forceinline__ void fill_rows(int* rowoff, unsigned char* rdy, unsigned char* rdz, int P,
+                                          int W0, int W1) {
+  for (int r = threadIdx.x; r < P * P; r += blockDim.x) {
+    const int dy = r % P, dz = r / P;
+    rowoff[r] = (dz * W1 + dy) * W0;
+    rdy[r] = (unsigned char)dy;
+    rdz[r] = (unsigned char)dz;
+  }
+}
+
+// Gridding, Eq. (3.7).  One CTA per (tile, chunk): the tile's particles are
+// spread into a padded tile in shared memory (a warp per particle, a lane per
+// (y, z) row of the P^3 window), then the padded tile is added to the
+// periodic grid.  The grid must be zero on entry.
+template <typename T, int PW>
+__global__ void __launch_bounds__(256) k_mid_spread(TileGeom g, WinT<T> w,
+                                                    const P4<T>* __restrict__ rec,
+                                                    const int* __restrict__ start,
+                                                    T* __restrict__ grid) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int tile = blockIdx.x;
+  const int b = start[tile], e = start[tile + 1];
+  const int chunk = blockIdx.y;
+  if (b + chunk >= e) return;
+  const int W0 = g.W[0], W1 = g.W[1], W2 = g.W[2];
+  const int Wn = W0 * W1 * W2;
+  const int P = PW > 0 ? PW : w.P;
+  const int PP = P * P;
+  MidSmem<T> sm = mid_smem_layout<T>(smraw, g, P);
+  T* st = sm.tile;
+  for (int i = threadIdx.x; i < Wn; i += blockDim.x) st[i] = T(0);
+  fill_rows(sm.rowoff, sm.rdy, sm.rdz, P, W0, W1);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* wsx = sm.ws + warp * 3 * kMaxWin;
+  T* wsy = wsx + kMaxWin;
+  T* wsz = wsy + kMaxWin;
+  for (int pi = b + chunk + warp * g.chunks; pi < e; pi += nw * g.chunks) {
+    const P4<T> a = rec[pi];
+    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half),
+              gz0 = (int)dceil(a.z - w.half);
+    if (lane < P) {
+      T v, dv;
+      win_eval(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
+      wsx[lane] = v;
+      win_eval(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
+      wsy[lane] = v * a.q;
+      win_eval(w, ((T)(gz0 + lane) - a.z) * w.inv_half, v, dv);
+      wsz[lane] = v;
+    }
+    __syncwarp();
+    T* base = st + ((gz0 + g.pad_lo) * W1 + (gy0 + g.pad_lo)) * W0 + gx0 + g.pad_lo;
+    T rwx[PW > 0 ? PW : kMaxWin];
+#pragma unroll
+    for (int dx = 0; dx < (PW > 0 ? PW : kMaxWin); ++dx) rwx[dx] = dx < P ? wsx[dx] : T(0);
+    for (int row = lane; row < PP; row += 32) {
+      const T cyz = wsy[sm.rdy[row]] * wsz[sm.rdz[row]];
+      if (cyz != T(0)) {
+        T* rp = base + sm.rowoff[row];
+#pragma unroll
+        for (int dx = 0; dx < (PW > 0 ? PW : kMaxWin); ++dx)
+          if (dx < P) atomicAdd(rp + dx, cyz * rwx[dx]);
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  const int tz = tile / (g.nt[0] * g.nt[1]);
+  const int ty = (tile / g.nt[0]) % g.nt[1];
+  const int tx = tile % g.nt[0];
+  const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo, oz = tz * g.T[2] - g.pad_lo;
+  // rows of the padded tile, one warp per row, wrapped x index per lane
+  int xw[2];
+  for (int k = 0; k < 2; ++k) xw[k] = (lane + 32 * k < W0) ? pmod(ox + lane + 32 * k, g.I[0]) : 0;
+  for (int row = warp; row < W1 * W2; row += nw) {
+    const int ly = row % W1, lz = row / W1;
+    T* gp = grid + ((size_t)pmod(oz + lz, g.I[2]) * g.I[1] + pmod(oy + ly, g.I[1])) * g.pitch;
+    for (int k = 0; k < 2; ++k) {
+      const int lx = lane + 32 * k;
+      if (lx < W0) {
+        const T v = st[row * W0 + lx];
+        if (v != T(0)) atomicAdd(gp + xw[k], v);
+      }
+    }
+  }
+}
+
+// Gathering, Eq. (3.10): Phi^mid_i = sum_g u[g] W(r_i - r_g) and its gradient.
+template <typename T, int PW>
+__global__ void __launch_bounds__(256) k_mid_gather(TileGeom g, WinT<T> w,
+                                                    const P4<T>* __restrict__ rec,
+                                                    const int* __restrict__ start,
+                                                    const int* __restrict__ perm,
+                                                    const T* __restrict__ grid, double3 invh,
+                                                    double* __restrict__ phi_out,
+                                                    double* __restrict__ grad_out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int tile = blockIdx.x;
+  const int b = start[tile], e = start[tile + 1];
+  const int chunk = blockIdx.y;
+  if (b + chunk >= e) return;
+  const int W0 = g.W[0], W1 = g.W[1], W2 = g.W[2];
+  const int P = PW > 0 ? PW : w.P;
+  const int PP = P * P;
+  MidSmem<T> sm = mid_smem_layout<T>(smraw, g, P);
+  T* st = sm.tile;
+  const int tz = tile / (g.nt[0] * g.nt[1]);
+  const int ty = (tile / g.nt[0]) % g.nt[1];
+  const int tx = tile % g.nt[0];
+  const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo, oz = tz * g.T[2] - g.pad_lo;
+  const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int xw[2];
+  for (int k = 0; k < 2; ++k) xw[k] = (lane + 32 * k < W0) ? pmod(ox + lane + 32 * k, g.I[0]) : 0;
+  for (int row = warp; row < W1 * W2; row += nw) {
+    const int ly = row % W1, lz = row / W1;
+    const T* gp = grid + ((size_t)pmod(oz + lz, g.I[2]) * g.I[1] + pmod(oy + ly, g.I[1])) * g.pitch;
+    for (int k = 0; k < 2; ++k) {
+      const int lx = lane + 32 * k;
+      if (lx < W0) st[row * W0 + lx] = gp[xw[k]];
+    }
+  }
+  fill_rows(sm.rowoff, sm.rdy, sm.rdz, P, W0, W1);
+  __syncthreads();
+  T* ws = sm.ws + warp * 6 * kMaxWin;
+  T *wsx = ws, *wsy = ws + kMaxWin, *wsz = ws + 2 * kMaxWin;
+  T *dsx = ws + 3 * kMaxWin, *dsy = ws + 4 * kMaxWin, *dsz = ws + 5 * kMaxWin;
+  for (int pi = b + chunk + warp * g.chunks; pi < e; pi += nw * g.chunks) {
+    const P4<T> a = rec[pi];
+    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half),
+              gz0 = (int)dceil(a.z - w.half);
+    if (lane < P) {
+      T v, dv;
+      // d/dt of phi((g - t)/half) = -phi'/half
+      win_eval(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
+      wsx[lane] = v;
+      dsx[lane] = -dv * w.inv_half;
+      win_eval(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
+      wsy[lane] = v;
+      dsy[lane] = -dv * w.inv_half;
+      win_eval(w, ((T)(gz0 + lane) - a.z) * w.inv_half, v, dv);
+      wsz[lane] = v;
+      dsz[lane] = -dv * w.inv_half;
+    }
+    __syncwarp();
+    const T* base = st + ((gz0 + g.pad_lo) * W1 + (gy0 + g.pad_lo)) * W0 + gx0 + g.pad_lo;
+    constexpr int PR = PW > 0 ? PW : kMaxWin;
+    T rwx[PR], rdx[PR];
+#pragma unroll
+    for (int dx = 0; dx < PR; ++dx) {
+      rwx[dx] = dx < P ? wsx[dx] : T(0);
+      rdx[dx] = dx < P ? dsx[dx] : T(0);
+    }
+    T f = 0, fx = 0, fy = 0, fz = 0;
+    for (int row = lane; row < PP; row += 32) {
+      const int dy = sm.rdy[row], dz = sm.rdz[row];
+      const T* rp = base + sm.rowoff[row];
+      T sx = 0, sd = 0;
+#pragma unroll
+      for (int dx = 0; dx < PR; ++dx) {
+        if (dx < P) {
+          const T u = rp[dx];
+          sx += u * rwx[dx];
+          sd += u * rdx[dx];
+        }
+      }
+      const T wy = wsy[dy], wz = wsz[dz];
+      const T wyz = wy * wz;
+      f += wyz * sx;
+      fx += wyz * sd;
+      fy += dsy[dy] * wz * sx;
+      fz += wy * dsz[dz] * sx;
+    }
+    f = warp_sum(f);
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    if (lane == 0) {
+      const int o = perm[pi];
+      phi_out[o] = (double)f;
+      grad_out[3 * o] = (double)fx * invh.x;
+      grad_out[3 * o + 1] = (double)fy * invh.y;
+      grad_out[3 * o + 2] = (double)fz * invh.z;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. long range (Algorithm 2, anterpolation form)
+// ---------------------------------------------------------------------------
+
+// Chebyshev polynomials T_0..T_{P-1}(x) into t[].
+template <typename T>
+__device__ __forceinline__ void cheb_all(T x, int P, T* t) {
+  t[0] = T(1);
+  if (P > 1) t[1] = x;
+  for (int n = 2; n < P; ++n) t[n] = T(2) * x * t[n - 1] - t[n - 2];
+}
+
+// T_n(x) and T_n'(x), n < P.
+template <typename T>
+__device__ __forceinline__ void cheb_all_d(T x, int P, T* t, T* dt) {
+  t[0] = T(1);
+  dt[0] = T(0);
+  if (P > 1) {
+    t[1] = x;
+    dt[1] = T(1);
+  }
+  for (int n = 2; n < P; ++n) {
+    t[n] = T(2) * x * t[n - 1] - t[n - 2];
+    dt[n] = T(2) * t[n - 1] + T(2) * x * dt[n - 1] - dt[n - 2];
+  }
+}
+
+// Spread q_j T_n(x_j) W2(rho_g - rho_j) onto the P proxy planes (layout
+// [n][y][x], pitch Ix + 2) through padded tiles; planes zero on entry.  A
+// warp per particle, a lane per Chebyshev index n.
+template <typename T, int PW>
+__global__ void __launch_bounds__(256) k_long_spread(TileGeom g, WinT<T> w, int P,
+                                                     const P4<T>* __restrict__ rec,
+                                                     const int* __restrict__ start,
+                                                     T* __restrict__ planes) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int tile = blockIdx.x;
+  const int b = start[tile], e = start[tile + 1];
+  const int chunk = blockIdx.y;
+  if (b + chunk >= e) return;
+  const int W0 = g.W[0], W1 = g.W[1];
+  const int ps = W0 * W1 + 1;  // odd plane stride in shared memory
+  const int Wn = P * ps;
+  T* st = reinterpret_cast<T*>(smraw);
+  for (int i = threadIdx.x; i < Wn; i += blockDim.x) st[i] = T(0);
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* ws = st + Wn + warp * (2 * kMaxWin + kMaxCheb);
+  T *wsx = ws, *wsy = ws + kMaxWin, *tn = ws + 2 * kMaxWin;
+  const int Pw = PW > 0 ? PW : w.P;
+  constexpr int PR = PW > 0 ? PW : kMaxWin;
+  for (int pi = b + chunk + warp * g.chunks; pi < e; pi += nw * g.chunks) {
+    const P4<T> a = rec[pi];
+    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half);
+    if (lane < Pw) {
+      T v, dv;
+      win_eval(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
+      wsx[lane] = v;
+      win_eval(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
+      wsy[lane] = v * a.q;
+    }
+    if (lane == 0) cheb_all(a.z, P, tn);
+    __syncwarp();
+    T rwx[PR];
+#pragma unroll
+    for (int dx = 0; dx < PR; ++dx) rwx[dx] = dx < Pw ? wsx[dx] : T(0);
+    T* base = st + (gy0 + g.pad_lo) * W0 + gx0 + g.pad_lo;
+    for (int n = lane; n < P; n += 32) {
+      const T t = tn[n];
+      T* pl = base + n * ps;
+      for (int dy = 0; dy < Pw; ++dy) {
+        const T cy = wsy[dy] * t;
+        if (cy == T(0)) continue;
+        T* rp = pl + dy * W0;
+#pragma unroll
+        for (int dx = 0; dx < PR; ++dx)
+          if (dx < Pw) atomicAdd(rp + dx, cy * rwx[dx]);
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  const int ty = tile / g.nt[0], tx = tile % g.nt[0];
+  const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
+  int xw[2];
+  for (int k = 0; k < 2; ++k) xw[k] = (lane + 32 * k < W0) ? pmod(ox + lane + 32 * k, g.I[0]) : 0;
+  for (int row = warp; row < P * W1; row += nw) {
+    const int n = row / W1, ly = row - n * W1;
+    T* gp = planes + ((size_t)n * g.I[1] + pmod(oy + ly, g.I[1])) * g.pitch;
+    for (int k = 0; k < 2; ++k) {
+      const int lx = lane + 32 * k;
+      if (lx < W0) {
+        const T v = st[n * ps + ly * W0 + lx];
+        if (v != T(0)) atomicAdd(gp + xw[k], v);
+      }
+    }
+  }
+}
+
+// Small long-range grids (cubic boxes: I_long of order 16): each CTA takes a
+// slice of the particles; every thread owns grid points of all P planes in
+// registers and adds q_j W2 T_n(x_j) for the particles whose window covers
+// them (no atomics).  The per-CTA planes go to scratch and k_long_reduce adds
+// them in a fixed order.
+constexpr int kSmallBatch = 32;
+
+template <typename T, int PMAX>
+__global__ void __launch_bounds__(256) k_long_spread_small(int I0, int I1, WinT<T> w, int P,
+                                                           const P4<T>* __restrict__ rec, int N,
+                                                           T* __restrict__ partial) {
+  __shared__ T wx[kSmallBatch][16], wy[kSmallBatch][16], tn[kSmallBatch][PMAX];
+  const int G = I0 * I1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per = (N + gridDim.x - 1) / gridDim.x;
+  const int b = blockIdx.x * per, e = min(N, b + per);
+  const T iI0 = T(1) / (T)I0, iI1 = T(1) / (T)I1;
+  for (int g0 = 0; g0 < G; g0 += blockDim.x) {
+    const int gpt = g0 + threadIdx.x;
+    const int gx = gpt % I0, gy = gpt / I0;
+    T acc[PMAX];
+#pragma unroll
+    for (int n = 0; n < PMAX; ++n) acc[n] = T(0);
+    for (int p0 = b; p0 < e; p0 += kSmallBatch) {
+      const int nb = min(kSmallBatch, e - p0);
+      __syncthreads();
+      // one warp per particle: weights over the whole (periodic) grid lines
+      for (int j = warp; j < nb; j += nw) {
+        const P4<T> a = rec[p0 + j];
+        for (int k = lane; k < I0; k += 32) {
+          // nearest image of grid index k relative to the particle
+          T d = (T)k - a.x;
+          d -= (T)I0 * drint(d * iI0);
+          T v, dv;
+          win_eval(w, d * w.inv_half, v, dv);
+          wx[j][k] = v * a.q;
+        }
+        for (int k = lane; k < I1; k += 32) {
+          T d = (T)k - a.y;
+          d -= (T)I1 * drint(d * iI1);
+          T v, dv;
+          win_eval(w, d * w.inv_half, v, dv);
+          wy[j][k] = v;
+        }
+        if (lane == 0) cheb_all(a.z, P, tn[j]);
+      }
+      __syncthreads();
+      if (gpt < G) {
+        for (int j = 0; j < nb; ++j) {
+          const T c = wx[j][gx] * wy[j][gy];
+          if (c != T(0)) {
+#pragma unroll
+            for (int n = 0; n < PMAX; ++n)
+              if (n < P) acc[n] += c * tn[j][n];
+          }
+        }
+      }
+    }
+    if (gpt < G) {
+      T* out = partial + (size_t)blockIdx.x * P * G + gpt;
+#pragma unroll
+      for (int n = 0; n < PMAX; ++n)
+        if (n < P) out[(size_t)n * G] = acc[n];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_long_reduce(const T* __restrict__ partial, int nblk, int I0, int I1, int P,
+                              T* __restrict__ planes) {
+  const int G = I0 * I1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * G) return;
+  T acc = 0;
+  for (int b = 0; b < nblk; ++b) acc += partial[(size_t)b * P * G + i];
+  const int n = i / G, gg = i - n * G;
+  const int y = gg / I0, x = gg - y * I0;
+  planes[((size_t)n * I1 + y) * (I0 + 2) + x] = acc;
+}
+
+// Per-mode z-contraction (Eq. 3.17 in the Chebyshev basis): for every 2D
+// mode (fy, fx) with k != 0, out_n = sum_n' K[mode][n][n'] in_n'.
+template <typename T>
+__global__ void k_long_contract(const T* __restrict__ A, T* __restrict__ B, const T* __restrict__ K,
+                                int P, int Iy, int C) {
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  const int mode = blockIdx.x * (blockDim.x / P) + threadIdx.x / P;
+  const int n = threadIdx.x % P;
+  if (threadIdx.x >= (blockDim.x / P) * P) return;
+  if (mode >= Iy * C) return;
+  const T2* a = reinterpret_cast<const T2*>(A);
+  T2* bo = reinterpret_cast<T2*>(B);
+  const size_t ps = (size_t)Iy * C;
+  T2 acc{T(0), T(0)};
+  if (mode != 0) {
+    const T* k = K + ((size_t)mode * P + n) * P;
+    for (int m = 0; m < P; ++m) {
+      const T2 v = a[(size_t)m * ps + mode];
+      const T kk = k[m];
+      acc.x += kk * v.x;
+      acc.y += kk * v.y;
+    }
+  }
+  bo[(size_t)n * ps + mode] = acc;
+}
+
+// Gathering, Eq. (3.19) discretised: Phi_i = sum_n T_n(x_i) sum_g W2 u_n[g].
+template <typename T, int PW>
+__global__ void __launch_bounds__(256) k_long_gather(TileGeom g, WinT<T> w, int P,
+                                                     const P4<T>* __restrict__ rec,
+                                                     const int* __restrict__ start,
+                                                     const int* __restrict__ perm,
+                                                     const T* __restrict__ planes, double3 sc,
+                                                     double* __restrict__ phi_out,
+                                                     double* __restrict__ grad_out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int tile = blockIdx.x;
+  const int b = start[tile], e = start[tile + 1];
+  const int chunk = blockIdx.y;
+  if (b + chunk >= e) return;
+  const int W0 = g.W[0], W1 = g.W[1];
+  const int ps = W0 * W1 + 1;
+  const int Wn = P * ps;
+  T* st = reinterpret_cast<T*>(smraw);
+  const int ty = tile / g.nt[0], tx = tile % g.nt[0];
+  const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
+  const int nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int xw[2];
+  for (int k = 0; k < 2; ++k) xw[k] = (lane + 32 * k < W0) ? pmod(ox + lane + 32 * k, g.I[0]) : 0;
+  for (int row = warp; row < P * W1; row += nw) {
+    const int n = row / W1, ly = row - n * W1;
+    const T* gp = planes + ((size_t)n * g.I[1] + pmod(oy + ly, g.I[1])) * g.pitch;
+    for (int k = 0; k < 2; ++k) {
+      const int lx = lane + 32 * k;
+      if (lx < W0) st[n * ps + ly * W0 + lx] = gp[xw[k]];
+    }
+  }
+  __syncthreads();
+  T* ws = st + Wn + warp * (4 * kMaxWin + 2 * kMaxCheb);
+  T *wsx = ws, *wsy = ws + kMaxWin, *dsx = ws + 2 * kMaxWin, *dsy = ws + 3 * kMaxWin;
+  T *tnv = ws + 4 * kMaxWin, *dtn = tnv + kMaxCheb;
+  const int Pw = PW > 0 ? PW : w.P;
+  constexpr int PR = PW > 0 ? PW : kMaxWin;
+  for (int pi = b + chunk + warp * g.chunks; pi < e; pi += nw * g.chunks) {
+    const P4<T> a = rec[pi];
+    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half);
+    if (lane < Pw) {
+      T v, dv;
+      win_eval(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
+      wsx[lane] = v;
+      dsx[lane] = -dv * w.inv_half;
+      win_eval(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
+      wsy[lane] = v;
+      dsy[lane] = -dv * w.inv_half;
+    }
+    if (lane == 0) cheb_all_d(a.z, P, tnv, dtn);
+    __syncwarp();
+    const T* base = st + (gy0 + g.pad_lo) * W0 + gx0 + g.pad_lo;
+    T rwx[PR], rdx[PR];
+#pragma unroll
+    for (int dx = 0; dx < PR; ++dx) {
+      rwx[dx] = dx < Pw ? wsx[dx] : T(0);
+      rdx[dx] = dx < Pw ? dsx[dx] : T(0);
+    }
+    T f = 0, fx = 0, fy = 0, fz = 0;
+    for (int n = lane; n < P; n += 32) {
+      const T* pl = base + n * ps;
+      T s = 0, sx = 0, sy = 0;
+      for (int dy = 0; dy < Pw; ++dy) {
+        const T* rp = pl + dy * W0;
+        T rs = 0, rd = 0;
+#pragma unroll
+        for (int dx = 0; dx < PR; ++dx) {
+          if (dx < Pw) {
+            const T u = rp[dx];
+            rs += u * rwx[dx];
+            rd += u * rdx[dx];
+          }
+        }
+        s += wsy[dy] * rs;
+        sx += wsy[dy] * rd;
+        sy += dsy[dy] * rs;
+      }
+      const T tn = tnv[n], dn = dtn[n];
+      f += tn * s;
+      fx += tn * sx;
+      fy += tn * sy;
+      fz += dn * s;
+    }
+    f = warp_sum(f);
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    if (lane == 0) {
+      const int o = perm[pi];
+      phi_out[o] = (double)f;
+      grad_out[3 * o] = (double)fx * sc.x;
+      grad_out[3 * o + 1] = (double)fy * sc.y;
+      grad_out[3 * o + 2] = (double)fz * sc.z;
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. k = 0 mode of the long range, FP64
+// ---------------------------------------------------------------------------
+
+// Per-block partial Chebyshev moments sum_j q_j T_n(x_j), n < P: T_n by the
+// recurrence in the element type (|T_n| <= 1 on [-1, 1]), products summed in
+// FP64 per thread, then per block.
+template <typename T, int PMAX>
+__global__ void __launch_bounds__(256) k_k0_moments(const T* __restrict__ q,
+                                                    const T* __restrict__ r, int N, int P,
+                                                    double halfLz, double* __restrict__ part) {
+  __shared__ double wsum[8][PMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double mom[PMAX];
+#pragma unroll
+  for (int n = 0; n < PMAX; ++n) mom[n] = 0.0;
+  const double ih = 1.0 / halfLz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double z = (double)r[3 * i + 2];
+    if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
+    const T x = (T)(z * ih);
+    T qi = q[i];
+    if (!isfinite((double)qi)) qi = T(0);
+    T t0 = T(1), t1 = x;
+#pragma unroll
+    for (int n = 0; n < PMAX; ++n) {
+      if (n < P) {
+        T tn;
+        if (n == 0) tn = T(1);
+        else if (n == 1) tn = x;
+        else {
+          tn = T(2) * x * t1 - t0;
+          t0 = t1;
+          t1 = tn;
+        }
+        mom[n] += (double)(qi * tn);
+      }
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < PMAX; ++n) {
+    if (n < P) {
+      const double v = warp_sum(mom[n]);
+      if (lane == 0) wsum[warp][n] = v;
+    }
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n < P; n += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w][n];
+    part[(size_t)blockIdx.x * P + n] = t;
+  }
+}
+
+// Sum of nblk partials of stride P for entry n, by one warp in a fixed order.
+__device__ __forceinline__ double warp_sum_partials(const double* __restrict__ part, int nblk,
+                                                    int P, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * P + n];
+  return warp_sum(s);
+}
+
+// mu_n = sum of the partial moments, nu = K0 mu; also the charge neutrality
+// check of Eq. (2.4) from the binning partials.  One warp per entry.
+__global__ void k_k0_finalize(const double* __restrict__ part, int nblk, int P,
+                              const double* __restrict__ K0, double* __restrict__ nu,
+                              const double* __restrict__ qred, int* __restrict__ status) {
+  __shared__ double mu[kMaxCheb];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int n = warp; n < P; n += nw) {
+    const double v = warp_sum_partials(part, nblk, P, n);
+    if (lane == 0) mu[n] = v;
+  }
+  if (warp == nw - 1 && qred) {
+    const double sq = warp_sum_partials(qred, nblk, 2, 0);
+    const double sa = warp_sum_partials(qred, nblk, 2, 1);
+    if (lane == 0 && fabs(sq) > 1e-10 * sa) atomicOr(status, 1);
+  }
+  __syncthreads();
+  for (int n = threadIdx.x; n < P; n += blockDim.x) {
+    double s = 0.0;
+    for (int m = 0; m < P; ++m) s += K0[n * P + m] * mu[m];
+    nu[n] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_k0_eval(const T* __restrict__ r, int N, int P, double halfLz,
+                          const double* __restrict__ nu, double* __restrict__ phi_out,
+                          double* __restrict__ grad_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double z = (double)r[3 * i + 2];
+  if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
+  const double x = z / halfLz;
+  double t0 = 1.0, t1 = x, d0 = 0.0, d1 = 1.0;
+  double f = nu[0], fz = 0.0;
+  if (P > 1) {
+    f += nu[1] * x;
+    fz += nu[1];
+  }
+  for (int n = 2; n < P; ++n) {
+    const double t2 = 2.0 * x * t1 - t0;
+    const double d2 = 2.0 * t1 + 2.0 * x * d1 - d0;
+    f += nu[n] * t2;
+    fz += nu[n] * d2;
+    t0 = t1; t1 = t2; d0 = d1; d1 = d2;
+  }
+  phi_out[i] = f;
+  grad_out[3 * i] = 0.0;
+  grad_out[3 * i + 1] = 0.0;
+  grad_out[3 * i + 2] = fz / halfLz;
+}
+
+// ---------------------------------------------------------------------------
+// 6. assembly and energy
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_assemble(const T* __restrict__ q, int N, const double* __restrict__ pp,
+                           const double* __restrict__ pg, double selfsum, T* __restrict__ phi,
+                           T* __restrict__ F, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double e = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double qi = (double)q[i];
+    if (!isfinite(qi)) qi = 0.0;
+    const double ph = pp[i] + pp[N + i] + pp[2 * (size_t)N + i] + pp[3 * (size_t)N + i] - qi * selfsum;
+    double g[3];
+    for (int d = 0; d < 3; ++d)
+      g[d] = pg[3 * i + d] + pg[3 * ((size_t)N + i) + d] + pg[3 * (2 * (size_t)N + i) + d] +
+             pg[3 * (3 * (size_t)N + i) + d];
+    if (phi) phi[i] = (T)ph;
+    if (F)
+      for (int d = 0; d < 3; ++d) F[3 * i + d] = (T)(-qi * g[d]);
+    e += qi * ph;
+  }
+  const double t = block_sum(e, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void k_energy(const double* __restrict__ part, int nblk, double* __restrict__ E) {
+  if (threadIdx.x < 32) {
+    const double v = warp_sum_partials(part, nblk, 1, 0);
+    if (threadIdx.x == 0) *E = 0.5 * v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// driver
+// ---------------------------------------------------------------------------
+
+// Window supports with dedicated (unrolled) kernels; others use the generic
+// instantiation (PW = 0).
+#define SOG_DISPATCH_PW(P_, KER, GRID, SMEM, STREAM, ...)                 \
+  do {                                                                     \
+    switch (P_) {                                                          \
+      case 6: KER<T, 6><<<GRID, 256, SMEM, STREAM>>>(__VA_ARGS__); break;   \
+      case 8: KER<T, 8><<<GRID, 256, SMEM, STREAM>>>(__VA_ARGS__); break;   \
+      case 9: KER<T, 9><<<GRID, 256, SMEM, STREAM>>>(__VA_ARGS__); break;   \
+      case 12: KER<T, 12><<<GRID, 256, SMEM, STREAM>>>(__VA_ARGS__); break; \
+      default: KER<T, 0><<<GRID, 256, SMEM, STREAM>>>(__VA_ARGS__); break;  \
+    }                                                                      \
+  } while (0)
+
+template <typename T, int PW>
+static cudaError_t allow_pw() {
+  cudaError_t e = cudaFuncSetAttribute(k_mid_spread<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mid_gather<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_long_spread<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_long_gather<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  return e;
+}
+
+static size_t mid_smem(const sog_plan* p, size_t es, bool gather) {
+  const TileGeom& g = p->gm;
+  return (size_t)g.W[0] * g.W[1] * g.W[2] * es + kMaxWin * kMaxWin * (sizeof(int) + 2) +
+         (size_t)8 * (gather ? 6 : 3) * kMaxWin * es;
+}
+static size_t long_smem(const sog_plan* p, size_t es, bool gather) {
+  const TileGeom& g = p->gl;
+  const size_t pl = (size_t)p->prm.P_cheb * (g.W[0] * g.W[1] + 1);
+  return (pl + 8 * (gather ? 4 * kMaxWin + 2 * kMaxCheb : 2 * kMaxWin + kMaxCheb)) * es;
+}
+
+#define SOG_CK(x)                      \
+  do {                                 \
+    cudaError_t e_ = (x);              \
+    if (e_ != cudaSuccess) return e_;  \
+  } while (0)
+
+static void mark(sog_plan* p, int stage, cudaStream_t s) {
+  if (!p->timing) return;
+  // inside a graph the record must be an external node to be timed later
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(p->ev[stage], s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(p->ev[stage], s);
+  p->ev_used[stage] = 1;
+}
+
+#define LAUNCH_CHECK()                 \
+  do {                                 \
+    ++p->launches;                     \
+    SOG_CK(cudaGetLastError());        \
+  } while (0)
+
+template <typename T>
+static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E, T* F,
+                         double* pp, double* pg, cudaStream_t s) {
+  p->launches = 0;
+  for (int i = 0; i <= SOG_NSTAGES; ++i) p->ev_used[i] = 0;
+  const int N = (int)p->N;
+  const sog_params& m = p->prm;
+  PrepGeom g{};
+  for (int d = 0; d < 3; ++d) {
+    g.L[d] = m.L[d];
+    g.halfL[d] = 0.5 * m.L[d];
+    g.nc[d] = p->nc[d];
+    g.icell[d] = 1.0 / p->cell[d];
+    g.ih[d] = p->has_mid ? 1.0 / p->h[d] : 0.0;
+    g.Tm[d] = p->gm.T[d];
+    g.ntm[d] = p->gm.nt[d];
+    g.iTm[d] = p->has_mid ? 1.0 / p->gm.T[d] : 0.0;
+  }
+  g.has_mid = p->has_mid;
+  g.has_long = p->has_long;
+  g.Lzs_half = 0.5 * p->Lzs;
+  for (int d = 0; d < 2; ++d) {
+    g.ihl[d] = p->has_long ? 1.0 / p->hl[d] : 0.0;
+    g.Tl[d] = p->gl.T[d];
+    g.ntl[d] = p->gl.nt[d];
+    g.iTl[d] = p->has_long ? 1.0 / p->gl.T[d] : 0.0;
+  }
+  g.ihalfLz = 2.0 / m.L[2];
+  const int3 off = make_int3(p->cnt_off[0], p->cnt_off[1], p->cnt_off[2]);
+  const int3 nb = make_int3(p->n_cells, p->has_mid ? p->n_tiles_mid : 0,
+                            p->has_long ? p->n_tiles_long : 0);
+  P4<T>* rn = reinterpret_cast<P4<T>*>(p->d_rec_near);
+  P4<T>* rm = reinterpret_cast<P4<T>*>(p->d_rec_mid);
+  P4<T>* rl = reinterpret_cast<P4<T>*>(p->d_rec_long);
+
+  // 1. binning
+  mark(p, 0, s);
+  SOG_CK(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * p->cnt_off[3], s));
+  P4<T>* tmp = reinterpret_cast<P4<T>*>(p->d_rec_tmp);
+  k_bin_count<T><<<kRedBlocks, 256, 0, s>>>(g, q, r, N, p->d_key, p->d_rank, p->d_cnt, off, tmp,
+                                           p->d_red, p->d_status);
+  LAUNCH_CHECK();
+  k_scan3<<<3, 1024, 0, s>>>(p->d_cnt, off, nb);
+  LAUNCH_CHECK();
+  k_bin_scatter<T><<<(N + 255) / 256, 256, 0, s>>>(N, p->has_mid, p->has_long, p->d_key,
+                                                   p->d_rank, p->d_cnt, off, tmp, rn, rm, rl,
+                                                   p->d_perm);
+  LAUNCH_CHECK();
+
+  // 2. near field
+  NearGeom ng{};
+  for (int d = 0; d < 3; ++d) {
+    ng.halfL[d] = 0.5 * m.L[d];
+    ng.cell[d] = p->cell[d];
+    ng.nc[d] = p->nc[d];
+  }
+  ng.L[0] = m.L[0];
+  ng.L[1] = m.L[1];
+  ng.rc = m.rc;
+  ng.K = p->near_K;
+  ng.D = p->near_D;
+  mark(p, 1, s);
+  k_near<T><<<p->n_cells, kNearThreads, 0, s>>>(ng, rn, p->d_cnt + off.x, p->d_perm,
+                                                reinterpret_cast<const T*>(p->d_near_tab), pp, pg);
+  LAUNCH_CHECK();
+
+  // 3. mid range
+  if (p->has_mid) {
+    mark(p, 2, s);
+    T* grid = reinterpret_cast<T*>(p->d_grid);
+    const size_t gbytes = (size_t)m.I[2] * m.I[1] * (m.I[0] + 2) * sizeof(T);
+    SOG_CK(cudaMemsetAsync(grid, 0, gbytes, s));
+    const WinT<T> w = wint<T>(p->wm);
+    const size_t sm = mid_smem(p, sizeof(T), false);
+    const dim3 mgrid(p->n_tiles_mid, p->gm.chunks);
+    SOG_DISPATCH_PW(p->wm.P, k_mid_spread, mgrid, sm, s, p->gm, w, rm, p->d_cnt + off.y, grid);
+    LAUNCH_CHECK();
+    mark(p, 3, s);
+    SOG_CK(fft_mid_forward_conv_inverse<T>(p, s));
+    p->launches += 5;
+    mark(p, 4, s);
+    const size_t sm2 = mid_smem(p, sizeof(T), true);
+    const double3 invh = make_double3(1.0 / p->h[0], 1.0 / p->h[1], 1.0 / p->h[2]);
+    SOG_DISPATCH_PW(p->wm.P, k_mid_gather, mgrid, sm2, s, p->gm, w, rm, p->d_cnt + off.y,
+                    p->d_perm + N, grid, invh, pp + N, pg + 3 * (size_t)N);
+    LAUNCH_CHECK();
+  } else {
+    SOG_CK(cudaMemsetAsync(pp + N, 0, sizeof(double) * N, s));
+    SOG_CK(cudaMemsetAsync(pg + 3 * (size_t)N, 0, sizeof(double) * 3 * N, s));
+  }
+
+  // 4-5. long range and its k = 0 mode
+  if (p->has_long) {
+    mark(p, 5, s);
+    const int P = m.P_cheb;
+    T* A = reinterpret_cast<T*>(p->d_lA);
+    T* B = reinterpret_cast<T*>(p->d_lB);
+    const WinT<T> w = wint<T>(p->wl);
+    if (p->long_small) {
+      const int I0 = m.I_long[0], I1 = m.I_long[1];
+      T* part = reinterpret_cast<T*>(p->d_long_partial);
+      if (P <= 16)
+        k_long_spread_small<T, 16><<<p->long_small_blocks, 256, 0, s>>>(I0, I1, w, P, rl, N, part);
+      else if (P <= 32)
+        k_long_spread_small<T, 32><<<p->long_small_blocks, 256, 0, s>>>(I0, I1, w, P, rl, N, part);
+      else
+        k_long_spread_small<T, 64><<<p->long_small_blocks, 256, 0, s>>>(I0, I1, w, P, rl, N, part);
+      LAUNCH_CHECK();
+      const int tot = P * I0 * I1;
+      k_long_reduce<T><<<(tot + 255) / 256, 256, 0, s>>>(
+          reinterpret_cast<const T*>(p->d_long_partial), p->long_small_blocks, I0, I1, P, A);
+      LAUNCH_CHECK();
+    } else {
+      const size_t pbytes = (size_t)P * m.I_long[1] * (m.I_long[0] + 2) * sizeof(T);
+      SOG_CK(cudaMemsetAsync(A, 0, pbytes, s));
+      const size_t sm = long_smem(p, sizeof(T), false);
+      const dim3 lgrid(p->n_tiles_long, p->gl.chunks);
+      SOG_DISPATCH_PW(p->wl.P, k_long_spread, lgrid, sm, s, p->gl, w, P, rl, p->d_cnt + off.z, A);
+      LAUNCH_CHECK();
+    }
+    mark(p, 6, s);
+    SOG_CK(fft_long_pass<T>(p, false, s));
+    p->launches += 2;
+    const int C = m.I_long[0] / 2 + 1;
+    const int modes = m.I_long[1] * C;
+    const int per = 256 / P;
+    k_long_contract<T><<<(modes + per - 1) / per, 256, 0, s>>>(
+        A, B, reinterpret_cast<const T*>(p->d_kmat), P, m.I_long[1], C);
+    LAUNCH_CHECK();
+    SOG_CK(fft_long_pass<T>(p, true, s));
+    p->launches += 2;
+    mark(p, 7, s);
+    const size_t sm2 = long_smem(p, sizeof(T), true);
+    const double3 sc = make_double3(1.0 / p->hl[0], 1.0 / p->hl[1], 2.0 / m.L[2]);
+    const dim3 lgrid2(p->n_tiles_long, p->gl.chunks);
+    SOG_DISPATCH_PW(p->wl.P, k_long_gather, lgrid2, sm2, s, p->gl, w, P, rl, p->d_cnt + off.z,
+                    p->d_perm + 2 * (size_t)N, B, sc, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
+    LAUNCH_CHECK();
+    mark(p, 8, s);
+    double* mpart = p->d_red + 2 * kRedBlocks;
+    if (P <= 16)
+      k_k0_moments<T, 16><<<kRedBlocks, 256, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+    else if (P <= 32)
+      k_k0_moments<T, 32><<<kRedBlocks, 256, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+    else
+      k_k0_moments<T, 64><<<kRedBlocks, 256, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+    LAUNCH_CHECK();
+    k_k0_finalize<<<1, 1024, 0, s>>>(p->d_red + 2 * kRedBlocks, kRedBlocks, P, p->d_k0mat,
+                                     p->d_k0nu, p->d_red, p->d_status);
+    LAUNCH_CHECK();
+    k_k0_eval<T><<<(N + 255) / 256, 256, 0, s>>>(r, N, P, 0.5 * m.L[2], p->d_k0nu,
+                                                pp + 3 * (size_t)N, pg + 9 * (size_t)N);
+    LAUNCH_CHECK();
+  } else {
+    SOG_CK(cudaMemsetAsync(pp + 2 * (size_t)N, 0, sizeof(double) * 2 * N, s));
+    SOG_CK(cudaMemsetAsync(pg + 6 * (size_t)N, 0, sizeof(double) * 6 * N, s));
+    k_k0_finalize<<<1, 1024, 0, s>>>(p->d_red + 2 * kRedBlocks, kRedBlocks, 0, p->d_k0mat,
+                                     p->d_k0nu, p->d_red, p->d_status);
+    LAUNCH_CHECK();
+  }
+
+  // 6. assembly
+  mark(p, 9, s);
+  if (phi || F || E) {
+    double* epart = p->d_red + 2 * kRedBlocks + (size_t)kRedBlocks * kMaxCheb;
+    k_assemble<T><<<kRedBlocks, 256, 0, s>>>(q, N, pp, pg, p->selfsum, phi, F, epart);
+    LAUNCH_CHECK();
+    if (E) {
+      k_energy<<<1, 32, 0, s>>>(epart, kRedBlocks, E);
+      LAUNCH_CHECK();
+    }
+  }
+  mark(p, SOG_NSTAGES, s);
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t prepare_t() {
+  cudaError_t e = allow_pw<T, 0>();
+  if (e == cudaSuccess) e = allow_pw<T, 6>();
+  if (e == cudaSuccess) e = allow_pw<T, 8>();
+  if (e == cudaSuccess) e = allow_pw<T, 9>();
+  if (e == cudaSuccess) e = allow_pw<T, 12>();
+  if (e == cudaSuccess) e = fft_prepare<T>();
+  return e;
+}
+
+cudaError_t prepare_kernels(int prec) {
+  return prec == SOG_PREC_FP64 ? prepare_t<double>() : prepare_t<float>();
+}
+
+static cudaError_t eval_direct(sog_plan* p, const void* q, const void* r, void* phi, double* E,
+                               void* F, double* pp, double* pg, cudaStream_t s) {
+  if (p->prec == SOG_PREC_FP64)
+    return eval_t<double>(p, (const double*)q, (const double*)r, (double*)phi, E, (double*)F, pp,
+                          pg, s);
+  return eval_t<float>(p, (const float*)q, (const float*)r, (float*)phi, E, (float*)F, pp, pg, s);
+}
+
+void release_graphs(sog_plan* p) {
+  for (int i = 0; i < p->n_graphs; ++i) cudaGraphExecDestroy(p->graphs[i].exec);
+  p->n_graphs = 0;
+}
+
+// Replays a captured graph of the whole evaluation for this set of caller
+// pointers (and timing mode), capturing it on the plan's private stream the
+// first time.  With timing on, the stage events are part of the graph.
+static cudaError_t eval_graph(sog_plan* p, const void* q, const void* r, void* phi, double* E,
+                              void* F, double* pp, double* pg, cudaStream_t s) {
+  GraphEntry* hit = nullptr;
+  for (int i = 0; i < p->n_graphs; ++i) {
+    GraphEntry& g = p->graphs[i];
+    if (g.q == q && g.r == r && g.phi == phi && g.E == E && g.F == F && g.pp == pp &&
+        g.pg == pg && g.timing == p->timing) {
+      hit = &g;
+      break;
+    }
+  }
+  if (!hit) {
+    int slot = p->n_graphs;
+    if (slot == kMaxGraphs) {
+      slot = 0;
+      for (int i = 1; i < kMaxGraphs; ++i)
+        if (p->graphs[i].last_use < p->graphs[slot].last_use) slot = i;
+      // the evicted graph may still be running on the caller's stream
+      cudaStreamSynchronize(p->last_stream);
+      cudaGraphExecDestroy(p->graphs[slot].exec);
+      // move the last entry into the hole so entries stay contiguous
+      p->graphs[slot] = p->graphs[p->n_graphs - 1];
+      slot = --p->n_graphs;
+    }
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t e1 = eval_direct(p, q, r, phi, E, F, pp, pg, p->cap_stream);
+    e = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (e1 != cudaSuccess || e != cudaSuccess) {
+      if (e == cudaSuccess) cudaGraphDestroy(graph);
+      return e1 != cudaSuccess ? e1 : e;
+    }
+    GraphEntry& g = p->graphs[slot];
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    ++p->n_graphs;
+    g.q = q;
+    g.r = r;
+    g.phi = phi;
+    g.E = E;
+    g.F = F;
+    g.pp = pp;
+    g.pg = pg;
+    g.timing = p->timing;
+    for (int i = 0; i <= SOG_NSTAGES; ++i) g.ev_used[i] = p->ev_used[i];
+    g.launches = p->launches;
+    hit = &g;
+  }
+  hit->last_use = ++p->use_clock;
+  p->launches = hit->launches;
+  for (int i = 0; i <= SOG_NSTAGES; ++i) p->ev_used[i] = hit->ev_used[i];
+  return cudaGraphLaunch(hit->exec, s);
+}
+
+sog_status eval_device(sog_plan* p, const void* q, const void* r, void* phi, double* E, void* F,
+                       double* phi_parts, double* grad_parts, cudaStream_t s) {
+  double* pp = phi_parts ? phi_parts : p->d_parts_phi;
+  double* pg = grad_parts ? grad_parts : p->d_parts_grad;
+  const cudaError_t e = p->use_graphs ? eval_graph(p, q, r, phi, E, F, pp, pg, s)
+                                      : eval_direct(p, q, r, phi, E, F, pp, pg, s);
+  p->last_stream = s;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    p->launch_error = 1;
+    return SOG_ERR_CUDA;
+  }
+  return SOG_OK;
+}
+
+}  // namespace sogk

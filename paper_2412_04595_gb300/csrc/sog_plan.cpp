@@ -1,0 +1,923 @@
+// Host side of the GB300 SOG library: parameter selection (Sec. 4.4), the
+// FP64 tables every evaluation reads, device memory, and the C ABI of sog.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sog_internal.h"
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+// Table 1 (Sec. 2.3): b, r0, omega, energy error, M.
+const double kTable1[6][5] = {
+    {2.0, 1.9892536839080267, 0.9944464927622323, 3.12e-2, 16},
+    {1.62976708826776469, 2.7520026668023417, 1.0078069793438068, 2.33e-3, 31},
+    {1.48783512395703226, 3.7554672283554990, 0.9919117057598183, 2.29e-4, 46},
+    {1.32070036405934420, 4.3914554711638349, 1.0018891411481198, 1.18e-6, 76},
+    {1.21812525709410644, 5.6355288151271085, 1.0009014615603334, 7.14e-10, 166},
+    {1.14878150173321925, 7.2956245490719404, 1.0000368348358225, 1.30e-15, 271},
+};
+
+// w_l and s_l of Eq. (2.22), w_0 scaled by omega (Eq. 2.25).
+void sog_table(double b, double sigma, double omega, int M, std::vector<double>& w,
+               std::vector<double>& s) {
+  w.resize(M + 1);
+  s.resize(M + 1);
+  const double c = pow(kPi / 2.0, -0.5);
+  for (int l = 0; l <= M; ++l) {
+    w[l] = c * pow(b, -(double)l) / sigma * log(b);
+    s[l] = sqrt(2.0) * pow(b, (double)l) * sigma;
+  }
+  w[0] *= omega;
+}
+
+int fft_size(long n) {
+  if (n < 8) n = 8;
+  n = (n + 7) / 8 * 8;
+  for (;; n += 8) {
+    long k = n;
+    for (int p : {2, 3, 5, 7})
+      while (k % p == 0) k /= p;
+    if (k == 1) return (int)n;
+  }
+}
+
+long clog2(long n) {
+  long v = n - 1;
+  long b = 0;
+  while (v > 0) {
+    ++b;
+    v >>= 1;
+  }
+  return b < 1 ? 1 : b;
+}
+
+// Inverse of erfc on (0, 2) by bisection then Newton, to double rounding.
+double erfcinv(double y) {
+  double lo = -30.0, hi = 30.0;
+  for (int i = 0; i < 200; ++i) {
+    const double mid = 0.5 * (lo + hi);
+    if (erfc(mid) > y) lo = mid;
+    else hi = mid;
+  }
+  double x = 0.5 * (lo + hi);
+  for (int i = 0; i < 3; ++i) {
+    const double f = erfc(x) - y;
+    const double d = -2.0 / sqrt(kPi) * exp(-x * x);
+    if (d == 0.0) break;
+    x -= f / d;
+  }
+  return x;
+}
+
+double shape_default(int window, int P) {
+  return window == SOG_WIN_ES ? 1.9 * P : 0.455 * kPi * P;
+}
+
+sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol, int window,
+                         double n_nb, sog_params* out) {
+  int row = 5;
+  for (int i = 0; i < 6; ++i)
+    if (kTable1[i][3] <= 1.5 * tol) {
+      row = i;
+      break;
+    }
+  const double b = kTable1[row][0], r0 = kTable1[row][1], omega = kTable1[row][2];
+  const int M_tab = (int)kTable1[row][4];
+  const double rho = (double)N / (Lx * Ly * Lz);
+  const double A = Lx * Ly;
+  const double eps = 0.3 * tol;
+  const double phis = pow(rho, 1.0 / 3.0);
+  double rc = pow(3.0 * n_nb / (4.0 * kPi * rho), 1.0 / 3.0);
+  rc = std::min(rc, 0.5 * std::min(Lx, Ly));
+  const double sigma = rc / r0;
+  const double cw = pow(kPi / 2.0, -0.5) * log(b) / sigma;
+  int M = M_tab;
+  const double lmax = std::max(Lx, std::max(Ly, Lz));
+  for (;;) {
+    const double tail = cw * pow(b, -(double)(M + 1)) / (1.0 - 1.0 / b);
+    const double s_next = sqrt(2.0) * pow(b, (double)(M + 1)) * sigma;
+    if (kPi * rho * pow(Lz, 3) / sqrt((double)N) * tail <= 0.1 * eps * phis && s_next >= 20.0 * lmax)
+      break;
+    ++M;
+    if (M > 2000) return SOG_ERR_PARAMS;
+  }
+  std::vector<double> w, s;
+  sog_table(b, sigma, omega, M, w, s);
+  const double C = window == SOG_WIN_ES ? 1.226 : 1.563;
+  int P_win = (int)ceil(pow(erfcinv(eps) / C, 2));
+  P_win = std::min(std::max(P_win, 4), 16);
+  const double lne = log(1.0 / eps);
+
+  bool have = false;
+  long best_cost = 0;
+  int bm = 0, bI[3] = {0, 0, 0}, bPw = 0, bIl[2] = {0, 0}, bPl = 0, bPc = 0;
+  double bhz = 0.0;
+  for (int m = -1; m <= M; ++m) {
+    long cost = 0;
+    int Ix = 0, Iy = 0, Izs = 0, Pw = 0;
+    double hz = 0.0;
+    if (m >= 0) {
+      const double K = 2.0 * sqrt(lne) / s[0];
+      const double nx = ceil(K * Lx / kPi), ny = ceil(K * Ly / kPi);
+      const double Izb = std::max(1.0, ceil(Lz * K / kPi));
+      hz = Lz / Izb;
+      Pw = P_win;
+      const double Hz = 0.5 * (Pw - 1) * hz;
+      const double pad = std::max(2.0 * Hz, s[m] * sqrt(lne));
+      const double nz = ceil((Lz + pad) / hz);
+      if (nz > 8192 || nx > 4096 || ny > 4096) continue;
+      Ix = fft_size((long)nx);
+      Iy = fft_size((long)ny);
+      Izs = fft_size((long)nz);
+      Pw = std::min(P_win, std::min(Ix, Iy));
+      const long G = (long)Ix * Iy * Izs;
+      cost += 4 * N * (long)Pw * Pw * Pw + 10 * G * clog2(G);
+    }
+    int Ilx = 0, Ily = 0, Pl = 0, Pc = 0;
+    if (m < M) {
+      const double s1 = s[m + 1];
+      const double Kl = 2.0 * sqrt(lne) / s1;
+      const double nx = std::max(ceil(Kl * Lx / kPi), (double)(P_win + 4));
+      const double ny = std::max(ceil(Kl * Ly / kPi), (double)(P_win + 4));
+      if (nx > 4096 || ny > 4096) continue;
+      Ilx = fft_size((long)nx);
+      Ily = fft_size((long)ny);
+      Pl = P_win;
+      for (int P = 2; P <= 64; ++P) {
+        double err = 0.0;
+        const double lg = 0.5 * lgamma(P + 1.0);
+        for (int l = m + 1; l <= M; ++l) {
+          const double amp = w[l] * std::max(1.0, kPi * s[l] * s[l] / A);
+          const double x = 2.0 * sqrt(2.0) * s[l] / Lz;
+          err += amp * exp(-P * log(x) - lg);
+        }
+        if (2.0 * err <= eps * phis) {
+          Pc = P;
+          break;
+        }
+      }
+      if (Pc == 0) continue;
+      const long Gl = (long)Ilx * Ily;
+      cost += 4 * N * (long)Pl * Pl * Pc + 10 * Gl * Pc * clog2(Gl) + 2 * Gl * (long)Pc * Pc +
+              N * (long)Pc;
+    }
+    if (!have || cost < best_cost) {
+      have = true;
+      best_cost = cost;
+      bm = m;
+      bI[0] = Ix;
+      bI[1] = Iy;
+      bI[2] = Izs;
+      bhz = hz;
+      bPw = Pw;
+      bIl[0] = Ilx;
+      bIl[1] = Ily;
+      bPl = Pl;
+      bPc = Pc;
+    }
+  }
+  if (!have) return SOG_ERR_PARAMS;
+  memset(out, 0, sizeof(*out));
+  out->L[0] = Lx;
+  out->L[1] = Ly;
+  out->L[2] = Lz;
+  out->b = b;
+  out->r0 = r0;
+  out->omega = omega;
+  out->sigma = sigma;
+  out->rc = rc;
+  out->M = M;
+  out->m = bm;
+  for (int d = 0; d < 3; ++d) out->I[d] = bI[d];
+  out->hz = bhz;
+  out->P_win = bPw ? bPw : 4;
+  out->shape = shape_default(window, out->P_win);
+  out->I_long[0] = bIl[0];
+  out->I_long[1] = bIl[1];
+  out->P_long = bPl ? bPl : 4;
+  out->shape_long = shape_default(window, out->P_long);
+  out->P_cheb = bPc;
+  out->window = window;
+  return SOG_OK;
+}
+
+bool smooth_even(int n) {
+  if (n < 2 || n % 2) return false;
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+sog_status check_params(const sog_params& p) {
+  for (int d = 0; d < 3; ++d)
+    if (!(p.L[d] > 0.0) || !isfinite(p.L[d])) return SOG_ERR_ARG;
+  if (!(p.b > 1.0) || !(p.sigma > 0.0) || !(p.rc > 0.0) || !(p.omega > 0.0)) return SOG_ERR_PARAMS;
+  if (p.rc > 0.5 * std::min(p.L[0], p.L[1]) * (1.0 + 1e-12)) return SOG_ERR_PARAMS;
+  if (p.M < 0 || p.M > 4000 || p.m < -1 || p.m > p.M) return SOG_ERR_PARAMS;
+  if (p.window != SOG_WIN_ES && p.window != SOG_WIN_GAUSS) return SOG_ERR_PARAMS;
+  if (p.m >= 0) {
+    for (int d = 0; d < 3; ++d)
+      if (!smooth_even(p.I[d])) return SOG_ERR_PARAMS;
+    if (p.P_win < 2 || p.P_win > sogk::kMaxWin || p.P_win > std::min(p.I[0], std::min(p.I[1], p.I[2])))
+      return SOG_ERR_PARAMS;
+    if (!(p.hz > 0.0) || p.I[2] * p.hz < p.L[2] + (p.P_win - 1) * p.hz - 1e-9 * p.L[2])
+      return SOG_ERR_PARAMS;
+    if (!(p.shape > 0.0)) return SOG_ERR_PARAMS;
+  }
+  if (p.m < p.M) {
+    for (int d = 0; d < 2; ++d)
+      if (!smooth_even(p.I_long[d])) return SOG_ERR_PARAMS;
+    if (p.P_long < 2 || p.P_long > sogk::kMaxWin || p.P_long > std::min(p.I_long[0], p.I_long[1]))
+      return SOG_ERR_PARAMS;
+    if (p.P_cheb < 2 || p.P_cheb > sogk::kMaxCheb) return SOG_ERR_PARAMS;
+    if (!(p.shape_long > 0.0)) return SOG_ERR_PARAMS;
+  }
+  return SOG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+
+void factorize(int n, sogk::FftLen& f) {
+  f.n = n;
+  f.nst = 0;
+  int k = n;
+  while (k % 8 == 0 && k > 1) { f.radix[f.nst++] = 8; k /= 8; }
+  while (k % 4 == 0) { f.radix[f.nst++] = 4; k /= 4; }
+  while (k % 2 == 0) { f.radix[f.nst++] = 2; k /= 2; }
+  for (int p : {3, 5, 7})
+    while (k % p == 0) { f.radix[f.nst++] = p; k /= p; }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1].
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wt) {
+  x.resize(n);
+  wt.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// hat W(k) of the window W(x) = phi(x/H): Gaussian closed form (Eq. 4.7);
+// ES by Gauss-Legendre quadrature of
+//   H int_{-pi/2}^{pi/2} exp(beta(cos t - 1)) cos(k H sin t) cos t dt.
+struct WinFT {
+  int kind;
+  double shape, H;
+  std::vector<double> gx, gw;
+  WinFT(int kind_, double shape_, double H_) : kind(kind_), shape(shape_), H(H_) {
+    if (kind == SOG_WIN_ES) gauss_legendre(256, gx, gw);
+  }
+  double operator()(double k) const {
+    if (kind == SOG_WIN_GAUSS) return sqrt(kPi / shape) * H * exp(-k * k * H * H / (4.0 * shape));
+    double acc = 0.0;
+    for (size_t i = 0; i < gx.size(); ++i) {
+      const double t = 0.5 * kPi * gx[i];
+      acc += gw[i] * exp(shape * (cos(t) - 1.0)) * cos(k * H * sin(t)) * cos(t);
+    }
+    return H * 0.5 * kPi * acc;
+  }
+};
+
+// Near kernel table: g(r) = 1 - r F_M(r) on [0, rc], K intervals, degree D
+// monomials in u = 2 (r - r_k)/(rc/K) - 1 (fitted at Chebyshev points).
+bool near_table(const std::vector<double>& w, const std::vector<double>& s, double rc, int D,
+                double target, int& Kout, std::vector<double>& coef) {
+  auto gfun = [&](double r) {
+    double F = 0.0;
+    for (size_t l = 0; l < w.size(); ++l) F += w[l] * exp(-(r * r) / (s[l] * s[l]));
+    return 1.0 - r * F;
+  };
+  for (int K = 16; K <= 8192; K *= 2) {
+    const double hK = rc / K;
+    coef.assign((size_t)K * (D + 1), 0.0);
+    double maxerr = 0.0;
+    for (int k = 0; k < K && maxerr <= target; ++k) {
+      // Vandermonde solve at D+1 Chebyshev points
+      const int n = D + 1;
+      std::vector<double> Amat(n * n), rhs(n);
+      for (int j = 0; j < n; ++j) {
+        const double u = cos(kPi * (j + 0.5) / n);
+        double pw = 1.0;
+        for (int c = 0; c < n; ++c) {
+          Amat[j * n + c] = pw;
+          pw *= u;
+        }
+        rhs[j] = gfun(k * hK + 0.5 * (u + 1.0) * hK);
+      }
+      for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int rr = c + 1; rr < n; ++rr)
+          if (fabs(Amat[rr * n + c]) > fabs(Amat[piv * n + c])) piv = rr;
+        for (int cc = 0; cc < n; ++cc) std::swap(Amat[c * n + cc], Amat[piv * n + cc]);
+        std::swap(rhs[c], rhs[piv]);
+        for (int rr = c + 1; rr < n; ++rr) {
+          const double f = Amat[rr * n + c] / Amat[c * n + c];
+          for (int cc = c; cc < n; ++cc) Amat[rr * n + cc] -= f * Amat[c * n + cc];
+          rhs[rr] -= f * rhs[c];
+        }
+      }
+      for (int c = n - 1; c >= 0; --c) {
+        double v = rhs[c];
+        for (int cc = c + 1; cc < n; ++cc) v -= Amat[c * n + cc] * coef[(size_t)k * n + cc];
+        coef[(size_t)k * n + c] = v / Amat[c * n + c];
+      }
+      for (int t = 0; t <= 24; ++t) {
+        const double u = -1.0 + 2.0 * t / 24.0;
+        double p = coef[(size_t)k * n + D];
+        for (int c = D - 1; c >= 0; --c) p = p * u + coef[(size_t)k * n + c];
+        maxerr = std::max(maxerr, fabs(p - gfun(k * hK + 0.5 * (u + 1.0) * hK)));
+      }
+    }
+    if (maxerr <= target) {
+      Kout = K;
+      return true;
+    }
+  }
+  return false;
+}
+
+// Float32 twiddle (c, s) near (cos, sin) whose norm c^2 + s^2 is closest to
+// 1: independently rounded cosines and sines leave every butterfly of a given
+// radix with the same small gain error, which a forward/backward pair turns
+// into a bias of the particles' self-interaction (and of the energy).
+// Candidates are the float32 values within two ulps of each rounded value.
+void unit_norm_f32(double& c, double& s) {
+  const float c0 = (float)c, s0 = (float)s;
+  float bc = c0, bs = s0;
+  double best = fabs((double)c0 * c0 + (double)s0 * s0 - 1.0);
+  double bang = fabs((double)c0 - c) + fabs((double)s0 - s);
+  float cc = c0;
+  for (int i = 0; i < 2; ++i) cc = nextafterf(cc, -2.0f);
+  for (int i = -2; i <= 2; ++i, cc = nextafterf(cc, 2.0f)) {
+    float ss = s0;
+    for (int k = 0; k < 2; ++k) ss = nextafterf(ss, -2.0f);
+    for (int j = -2; j <= 2; ++j, ss = nextafterf(ss, 2.0f)) {
+      const double nrm = fabs((double)cc * cc + (double)ss * ss - 1.0);
+      const double ang = fabs((double)cc - c) + fabs((double)ss - s);
+      if (nrm < best - 1e-18 || (fabs(nrm - best) <= 1e-18 && ang < bang)) {
+        best = nrm;
+        bang = ang;
+        bc = cc;
+        bs = ss;
+      }
+    }
+  }
+  c = bc;
+  s = bs;
+}
+
+template <typename T>
+void put(std::vector<unsigned char>& buf, size_t off, const std::vector<double>& v) {
+  T* d = reinterpret_cast<T*>(buf.data() + off);
+  for (size_t i = 0; i < v.size(); ++i) d[i] = (T)v[i];
+}
+
+struct Arena {
+  size_t size = 0;
+  size_t take(size_t bytes) {
+    const size_t o = size;
+    size += (bytes + 255) / 256 * 256;
+    return o;
+  }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char* sog_status_str(sog_status s) {
+  switch (s) {
+    case SOG_OK: return "ok";
+    case SOG_ERR_ARG: return "invalid argument";
+    case SOG_ERR_NONNEUTRAL: return "charges are not neutral (|sum q| > 1e-10 sum |q|)";
+    case SOG_ERR_OUT_OF_BOX: return "a z coordinate is outside [-Lz/2, Lz/2] or a coordinate is not finite";
+    case SOG_ERR_NOMEM: return "out of memory";
+    case SOG_ERR_CUDA: return "CUDA error";
+    case SOG_ERR_PARAMS: return "no feasible or an inconsistent parameter set";
+  }
+  return "unknown status";
+}
+
+static sog_status check_args(int64_t N, double Lx, double Ly, double Lz, double tol) {
+  if (N < 2 || N > (int64_t)1 << 30) return SOG_ERR_ARG;
+  if (!(Lx > 0.0) || !(Ly > 0.0) || !(Lz > 0.0) || !isfinite(Lx) || !isfinite(Ly) || !isfinite(Lz))
+    return SOG_ERR_ARG;
+  if (!(tol > 0.0) || !(tol <= 0.1)) return SOG_ERR_ARG;
+  return SOG_OK;
+}
+
+sog_status sog_select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
+                             const sog_opts* opts, sog_params* out) {
+  if (!out) return SOG_ERR_ARG;
+  sog_status st = check_args(N, Lx, Ly, Lz, tol);
+  if (st != SOG_OK) return st;
+  const int window = opts ? opts->window : SOG_WIN_ES;
+  if (window != SOG_WIN_ES && window != SOG_WIN_GAUSS) return SOG_ERR_ARG;
+  const double nnb = (opts && opts->n_nb > 0.0) ? opts->n_nb : 120.0;
+  return select_params(N, Lx, Ly, Lz, tol, window, nnb, out);
+}
+
+sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, double Lz, double tol,
+                           const sog_opts* opts) {
+  if (!plan) return SOG_ERR_ARG;
+  *plan = nullptr;
+  sog_status st = check_args(N, Lx, Ly, Lz, tol);
+  if (st != SOG_OK) return st;
+  const int prec = opts ? opts->precision : SOG_PREC_MIXED;
+  if (prec != SOG_PREC_FP64 && prec != SOG_PREC_MIXED) return SOG_ERR_ARG;
+  sog_params prm;
+  if (opts && opts->manual) {
+    prm = *opts->manual;
+    if (prm.L[0] != Lx || prm.L[1] != Ly || prm.L[2] != Lz) return SOG_ERR_ARG;
+  } else {
+    st = sog_select_params(N, Lx, Ly, Lz, tol, opts, &prm);
+    if (st != SOG_OK) return st;
+  }
+  st = check_params(prm);
+  if (st != SOG_OK) return st;
+
+  if (sogk::prepare_kernels(prec) != cudaSuccess) {
+    cudaGetLastError();
+    return SOG_ERR_CUDA;
+  }
+  sog_plan* p = new (std::nothrow) sog_plan();
+  if (!p) return SOG_ERR_NOMEM;
+  p->prm = prm;
+  p->prec = prec;
+  p->N = N;
+  cudaGetDevice(&p->device);
+  const size_t es = prec == SOG_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const double* L = prm.L;
+
+  // SOG table and derived geometry
+  std::vector<double> w, s;
+  sog_table(prm.b, prm.sigma, prm.omega, prm.M, w, s);
+  p->selfsum = 0.0;
+  for (double v : w) p->selfsum += v;
+  p->has_mid = prm.m >= 0;
+  p->has_long = prm.m < prm.M;
+  for (int d = 0; d < 3; ++d) {
+    p->nc[d] = std::max(1, (int)floor(L[d] / prm.rc));
+    p->cell[d] = L[d] / p->nc[d];
+  }
+  p->n_cells = p->nc[0] * p->nc[1] * p->nc[2];
+  const int Ix = prm.I[0], Iy = prm.I[1], Iz = prm.I[2];
+  const int Ilx = prm.I_long[0], Ily = prm.I_long[1];
+  const int P = prm.P_cheb;
+  if (p->has_mid) {
+    p->h[0] = L[0] / Ix;
+    p->h[1] = L[1] / Iy;
+    p->h[2] = prm.hz;
+    p->Lzs = Iz * prm.hz;
+    p->wm = sogk::WinPar{prm.P_win, prm.window, 0.5 * (prm.P_win - 1), prm.shape};
+    int T = 16;
+    if (prec == SOG_PREC_FP64 || (size_t)(16 + prm.P_win) * (16 + prm.P_win) * (16 + prm.P_win) * es > 72 * 1024)
+      T = 8;
+    sogk::TileGeom& g = p->gm;
+    g.I[0] = Ix;
+    g.I[1] = Iy;
+    g.I[2] = Iz;
+    for (int d = 0; d < 3; ++d) {
+      g.T[d] = std::min(T, g.I[d]);
+      g.nt[d] = (g.I[d] + g.T[d] - 1) / g.T[d];
+      g.W[d] = g.T[d] + prm.P_win;
+    }
+    g.pad_lo = (int)floor(p->wm.half);
+    g.pitch = Ix + 2;
+    p->n_tiles_mid = g.nt[0] * g.nt[1] * g.nt[2];
+    const double per_tile = (double)N / p->n_tiles_mid;
+    int ch = (int)ceil(600.0 / p->n_tiles_mid);
+    ch = std::max(1, std::min(ch, (int)(per_tile / 32.0)));
+    g.chunks = std::max(1, ch);
+  }
+  if (p->has_long) {
+    p->hl[0] = L[0] / Ilx;
+    p->hl[1] = L[1] / Ily;
+    p->wl = sogk::WinPar{prm.P_long, prm.window, 0.5 * (prm.P_long - 1), prm.shape_long};
+    int T = 16;
+    if ((size_t)P * ((16 + prm.P_long) * (16 + prm.P_long) + 1) * es > 96 * 1024) T = 8;
+    sogk::TileGeom& g = p->gl;
+    g.I[0] = Ilx;
+    g.I[1] = Ily;
+    g.I[2] = 1;
+    for (int d = 0; d < 2; ++d) {
+      g.T[d] = std::min(T, g.I[d]);
+      g.nt[d] = (g.I[d] + g.T[d] - 1) / g.T[d];
+      g.W[d] = g.T[d] + prm.P_long;
+    }
+    g.T[2] = g.nt[2] = g.W[2] = 1;
+    g.pad_lo = (int)floor(p->wl.half);
+    g.pitch = Ilx + 2;
+    p->n_tiles_long = g.nt[0] * g.nt[1];
+    // one tile covering the grid and planes that fit shared memory: private
+    // copies per CTA plus a reduction instead of atomics on a few addresses
+    p->long_small = (g.nt[0] == 1 && g.nt[1] == 1 &&
+                     (size_t)P * (Ilx * Ily + 1) * es <= 64 * 1024) ? 1 : 0;
+    p->long_small_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sogk::kRedBlocks, N / 128));
+    const double per_tile = (double)N / p->n_tiles_long;
+    int ch = (int)ceil(600.0 / p->n_tiles_long);
+    ch = std::max(1, std::min(ch, (int)(per_tile / 32.0)));
+    g.chunks = std::max(1, ch);
+  }
+
+  // FFT lengths and twiddles exp(-2 pi i t/n)
+  std::vector<double> tw;
+  auto add_len = [&](int n, sogk::FftLen& f) {
+    factorize(n, f);
+    f.tw_off = (int)(tw.size() / 2);
+    for (int t = 0; t < n; ++t) {
+      double c = cos(2.0 * kPi * t / n), sn = -sin(2.0 * kPi * t / n);
+      if (prec == SOG_PREC_MIXED) unit_norm_f32(c, sn);
+      tw.push_back(c);
+      tw.push_back(sn);
+    }
+  };
+  if (p->has_mid) {
+    add_len(Ix, p->fx);
+    add_len(Iy, p->fy);
+    add_len(Iz, p->fz);
+  }
+  if (p->has_long) {
+    add_len(Ilx, p->flx);
+    add_len(Ily, p->fly);
+  }
+  if (tw.empty()) tw.assign(2, 0.0);
+
+  // near table
+  p->near_D = 8;
+  std::vector<double> ntab;
+  if (!near_table(w, s, prm.rc, p->near_D, prec == SOG_PREC_FP64 ? 3e-15 : 1e-9, p->near_K, ntab)) {
+    delete p;
+    return SOG_ERR_PARAMS;
+  }
+
+  // mid scaling factors, Eq. (3.8) for unnormalised DFTs
+  std::vector<double> mult;
+  if (p->has_mid) {
+    const int C = Ix / 2 + 1;
+    WinFT fx(prm.window, prm.shape, p->wm.half * p->h[0]);
+    WinFT fy(prm.window, prm.shape, p->wm.half * p->h[1]);
+    WinFT fz(prm.window, prm.shape, p->wm.half * p->h[2]);
+    std::vector<double> kx(C), ky(Iy), kz(Iz), Wx(C), Wy(Iy), Wz(Iz);
+    for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
+    for (int f = 0; f < Iy; ++f) { ky[f] = 2.0 * kPi * std::min(f, Iy - f) / L[1]; Wy[f] = fy(ky[f]); }
+    for (int f = 0; f < Iz; ++f) { kz[f] = 2.0 * kPi * std::min(f, Iz - f) / p->Lzs; Wz[f] = fz(kz[f]); }
+    const double pre = pow(p->h[0] * p->h[1] * p->h[2], 2) / (L[0] * L[1] * p->Lzs);
+    mult.resize((size_t)Iz * Iy * C);
+    for (int z = 0; z < Iz; ++z)
+      for (int y = 0; y < Iy; ++y)
+        for (int x = 0; x < C; ++x) {
+          const double k2 = kx[x] * kx[x] + ky[y] * ky[y] + kz[z] * kz[z];
+          double kh = 0.0;
+          for (int l = 0; l <= prm.m; ++l)
+            kh += pow(kPi, 1.5) * w[l] * s[l] * s[l] * s[l] * exp(-s[l] * s[l] * k2 / 4.0);
+          const double W2 = pow(Wx[x] * Wy[y] * Wz[z], 2);
+          mult[((size_t)z * Iy + y) * C + x] = (x == 0 && y == 0 && z == 0) ? 0.0 : pre * kh / W2;
+        }
+  }
+
+  // long range: per-mode z-kernel in the Chebyshev basis and the k = 0 kernel
+  std::vector<double> kmat, k0mat((size_t)std::max(P, 1) * std::max(P, 1), 0.0);
+  if (p->has_long) {
+    const double A = L[0] * L[1];
+    std::vector<double> zc(P), Cm((size_t)P * P);
+    for (int c = 0; c < P; ++c) {
+      const double x = cos((c + 0.5) * kPi / P);
+      zc[c] = 0.5 * L[2] * x;
+      double t0 = 1.0, t1 = x;
+      for (int n = 0; n < P; ++n) {
+        double tn = n == 0 ? 1.0 : (n == 1 ? x : 0.0);
+        if (n >= 2) {
+          tn = 2.0 * x * t1 - t0;
+          t0 = t1;
+          t1 = tn;
+        }
+        Cm[(size_t)c * P + n] = (n == 0 ? 1.0 : 2.0) / P * tn;
+      }
+    }
+    // B_l = C^T E_l C with E_l[c][c'] = exp(-(z_c - z_c')^2 / s_l^2)
+    const int nl = prm.M - prm.m;
+    std::vector<double> Bl((size_t)nl * P * P);
+    std::vector<double> E((size_t)P * P), tmp((size_t)P * P);
+    for (int li = 0; li < nl; ++li) {
+      const int l = prm.m + 1 + li;
+      for (int c = 0; c < P; ++c)
+        for (int c2 = 0; c2 < P; ++c2) {
+          const double d = zc[c] - zc[c2];
+          E[(size_t)c * P + c2] = exp(-d * d / (s[l] * s[l]));
+        }
+      for (int c = 0; c < P; ++c)
+        for (int n2 = 0; n2 < P; ++n2) {
+          double a = 0.0;
+          for (int c2 = 0; c2 < P; ++c2) a += E[(size_t)c * P + c2] * Cm[(size_t)c2 * P + n2];
+          tmp[(size_t)c * P + n2] = a;
+        }
+      for (int n = 0; n < P; ++n)
+        for (int n2 = 0; n2 < P; ++n2) {
+          double a = 0.0;
+          for (int c = 0; c < P; ++c) a += Cm[(size_t)c * P + n] * tmp[(size_t)c * P + n2];
+          Bl[((size_t)li * P + n) * P + n2] = a;
+        }
+    }
+    const int C = Ilx / 2 + 1;
+    const size_t kbytes = (size_t)Ily * C * P * P * es;
+    if (kbytes > ((size_t)1 << 30)) {
+      delete p;
+      return SOG_ERR_PARAMS;
+    }
+    WinFT fx(prm.window, prm.shape_long, p->wl.half * p->hl[0]);
+    WinFT fy(prm.window, prm.shape_long, p->wl.half * p->hl[1]);
+    std::vector<double> Wx(C), Wy(Ily), kx(C), ky(Ily);
+    for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
+    for (int f = 0; f < Ily; ++f) { ky[f] = 2.0 * kPi * std::min(f, Ily - f) / L[1]; Wy[f] = fy(ky[f]); }
+    kmat.assign((size_t)Ily * C * P * P, 0.0);
+    std::vector<double> a(nl);
+    for (int y = 0; y < Ily; ++y)
+      for (int x = 0; x < C; ++x) {
+        if (x == 0 && y == 0) continue;
+        const double k2 = kx[x] * kx[x] + ky[y] * ky[y];
+        const double fac = kPi / A * pow(p->hl[0] * p->hl[1], 2) / pow(Wx[x] * Wy[y], 2);
+        double* K = &kmat[((size_t)y * C + x) * P * P];
+        for (int li = 0; li < nl; ++li) {
+          const int l = prm.m + 1 + li;
+          const double al = w[l] * s[l] * s[l] * exp(-s[l] * s[l] * k2 / 4.0);
+          if (al == 0.0) continue;
+          const double* B = &Bl[(size_t)li * P * P];
+          for (int i = 0; i < P * P; ++i) K[i] += fac * al * B[i];
+        }
+      }
+    // k = 0: (pi/A) C^T K0 C, K0(d) = -sum_{l>m} w_l d^2 phi1(d^2/s_l^2)
+    std::vector<double> K0((size_t)P * P, 0.0);
+    for (int c = 0; c < P; ++c)
+      for (int c2 = 0; c2 < P; ++c2) {
+        const double d = zc[c] - zc[c2];
+        double acc = 0.0;
+        for (int l = prm.m + 1; l <= prm.M; ++l) {
+          const double x = d * d / (s[l] * s[l]);
+          const double ph1 = x == 0.0 ? 1.0 : -expm1(-x) / x;
+          acc -= w[l] * d * d * ph1;
+        }
+        K0[(size_t)c * P + c2] = acc;
+      }
+    for (int c = 0; c < P; ++c)
+      for (int n2 = 0; n2 < P; ++n2) {
+        double acc = 0.0;
+        for (int c2 = 0; c2 < P; ++c2) acc += K0[(size_t)c * P + c2] * Cm[(size_t)c2 * P + n2];
+        tmp[(size_t)c * P + n2] = acc;
+      }
+    for (int n = 0; n < P; ++n)
+      for (int n2 = 0; n2 < P; ++n2) {
+        double acc = 0.0;
+        for (int c = 0; c < P; ++c) acc += Cm[(size_t)c * P + n] * tmp[(size_t)c * P + n2];
+        k0mat[(size_t)n * P + n2] = kPi / A * acc;
+      }
+  }
+
+  // device arena
+  Arena ar;
+  const size_t o_tw = ar.take(tw.size() * es);
+  const size_t o_near = ar.take(ntab.size() * es);
+  const size_t o_mult = ar.take(mult.size() * es);
+  const size_t o_kmat = ar.take(kmat.size() * es);
+  const size_t o_k0 = ar.take(k0mat.size() * sizeof(double));
+  const size_t tables_end = ar.size;
+  const size_t o_grid = ar.take(p->has_mid ? (size_t)Iz * Iy * (Ix + 2) * es : 0);
+  const size_t lbytes = p->has_long ? (size_t)P * Ily * (Ilx + 2) * es : 0;
+  const size_t o_lA = ar.take(lbytes);
+  const size_t o_lB = ar.take(lbytes);
+  const size_t o_rn = ar.take((size_t)N * 4 * es);
+  const size_t o_rm = ar.take(p->has_mid ? (size_t)N * 4 * es : 0);
+  const size_t o_rl = ar.take(p->has_long ? (size_t)N * 4 * es : 0);
+  const size_t o_rt = ar.take((size_t)3 * N * 4 * es);
+  const size_t o_perm = ar.take((size_t)3 * N * sizeof(int));
+  const size_t o_key = ar.take((size_t)3 * N * sizeof(int));
+  const size_t o_rank = ar.take((size_t)3 * N * sizeof(int));
+  p->cnt_off[0] = 0;
+  p->cnt_off[1] = p->n_cells + 1;
+  p->cnt_off[2] = p->cnt_off[1] + (p->has_mid ? p->n_tiles_mid + 1 : 1);
+  p->cnt_off[3] = p->cnt_off[2] + (p->has_long ? p->n_tiles_long + 1 : 1);
+  const size_t o_cnt = ar.take((size_t)p->cnt_off[3] * sizeof(int));
+  const size_t o_pp = ar.take((size_t)4 * N * sizeof(double));
+  const size_t o_pg = ar.take((size_t)12 * N * sizeof(double));
+  const size_t o_red = ar.take((size_t)sogk::kRedBlocks * (3 + sogk::kMaxCheb) * sizeof(double));
+  const size_t o_nu = ar.take(sogk::kMaxCheb * sizeof(double));
+  const size_t o_st = ar.take(sizeof(int));
+  const size_t o_host = ar.take((size_t)N * 8 * es + sizeof(double));
+  const size_t o_lpart = ar.take(p->has_long && p->long_small
+                                     ? (size_t)p->long_small_blocks * P * Ilx * Ily * es : 0);
+  void* base = nullptr;
+  if (cudaMalloc(&base, ar.size) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return SOG_ERR_NOMEM;
+  }
+  p->arena = base;
+  p->arena_bytes = (int64_t)ar.size;
+  char* b = static_cast<char*>(base);
+  p->d_tw = b + o_tw;
+  p->d_near_tab = b + o_near;
+  p->d_mult = b + o_mult;
+  p->d_kmat = b + o_kmat;
+  p->d_k0mat = reinterpret_cast<double*>(b + o_k0);
+  p->d_grid = b + o_grid;
+  p->d_lA = b + o_lA;
+  p->d_lB = b + o_lB;
+  p->d_rec_near = b + o_rn;
+  p->d_rec_mid = b + o_rm;
+  p->d_rec_long = b + o_rl;
+  p->d_rec_tmp = b + o_rt;
+  p->d_perm = reinterpret_cast<int*>(b + o_perm);
+  p->d_key = reinterpret_cast<int*>(b + o_key);
+  p->d_rank = reinterpret_cast<int*>(b + o_rank);
+  p->d_cnt = reinterpret_cast<int*>(b + o_cnt);
+  p->d_parts_phi = reinterpret_cast<double*>(b + o_pp);
+  p->d_parts_grad = reinterpret_cast<double*>(b + o_pg);
+  p->d_red = reinterpret_cast<double*>(b + o_red);
+  p->d_k0nu = reinterpret_cast<double*>(b + o_nu);
+  p->d_status = reinterpret_cast<int*>(b + o_st);
+  p->d_host_stage = b + o_host;
+  p->d_long_partial = b + o_lpart;
+
+  // upload tables (one host staging buffer)
+  std::vector<unsigned char> host(tables_end, 0);
+  if (es == sizeof(double)) {
+    put<double>(host, o_tw, tw);
+    put<double>(host, o_near, ntab);
+    put<double>(host, o_mult, mult);
+    put<double>(host, o_kmat, kmat);
+  } else {
+    put<float>(host, o_tw, tw);
+    put<float>(host, o_near, ntab);
+    put<float>(host, o_mult, mult);
+    put<float>(host, o_kmat, kmat);
+  }
+  put<double>(host, o_k0, k0mat);
+  cudaError_t e = cudaMemcpy(base, host.data(), tables_end, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(p->d_k0nu, 0, sogk::kMaxCheb * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    delete p;
+    return SOG_ERR_CUDA;
+  }
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(base);
+    delete p;
+    return SOG_ERR_CUDA;
+  }
+  p->use_graphs = 1;
+  p->last_stream = nullptr;
+  p->launch_error = 0;
+  *plan = p;
+  return SOG_OK;
+}
+
+sog_status sog_plan_get_params(const sog_plan* plan, sog_params* out) {
+  if (!plan || !out) return SOG_ERR_ARG;
+  *out = plan->prm;
+  return SOG_OK;
+}
+
+int32_t sog_plan_precision(const sog_plan* plan) { return plan ? plan->prec : -1; }
+
+int64_t sog_plan_device_bytes(const sog_plan* plan) { return plan ? plan->arena_bytes : 0; }
+
+sog_status sog_eval(sog_plan* plan, const void* q, const void* r, void* phi, double* E, void* F,
+                    void* stream) {
+  if (!plan || !q || !r) return SOG_ERR_ARG;
+  return sogk::eval_device(plan, q, r, phi, E, F, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+sog_status sog_eval_components(sog_plan* plan, const void* q, const void* r, double* phi_parts,
+                               double* grad_parts, void* stream) {
+  if (!plan || !q || !r) return SOG_ERR_ARG;
+  const cudaStream_t s = (cudaStream_t)stream;
+  sog_status st = sogk::eval_device(plan, q, r, nullptr, nullptr, nullptr, phi_parts, grad_parts, s);
+  return st;
+}
+
+sog_status sog_eval_host(sog_plan* plan, const void* q, const void* r, void* phi, double* E, void* F) {
+  if (!plan || !q || !r) return SOG_ERR_ARG;
+  const size_t es = plan->prec == SOG_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t N = (size_t)plan->N;
+  void* buf = plan->d_host_stage;
+  char* b = static_cast<char*>(buf);
+  void* dq = b;
+  void* dr = b + N * es;
+  void* dphi = b + 4 * N * es;
+  void* dF = b + 5 * N * es;
+  double* dE = reinterpret_cast<double*>(b + ((8 * N * es + 7) / 8) * 8);
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaMemcpyAsync(dq, q, N * es, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dr, r, 3 * N * es, cudaMemcpyHostToDevice, s);
+  sog_status st = SOG_OK;
+  if (e == cudaSuccess)
+    st = sogk::eval_device(plan, dq, dr, phi ? dphi : nullptr, E ? dE : nullptr, F ? dF : nullptr,
+                           nullptr, nullptr, s);
+  if (e == cudaSuccess && st == SOG_OK) {
+    if (phi) e = cudaMemcpyAsync(phi, dphi, N * es, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && F) e = cudaMemcpyAsync(F, dF, 3 * N * es, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && E) e = cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) return SOG_ERR_CUDA;
+  if (st != SOG_OK) return st;
+  return sog_plan_check(plan);
+}
+
+sog_status sog_plan_check(sog_plan* plan) {
+  if (!plan) return SOG_ERR_ARG;
+  if (cudaStreamSynchronize(plan->last_stream) != cudaSuccess) return SOG_ERR_CUDA;
+  int st = 0;
+  if (cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SOG_ERR_CUDA;
+  if (cudaMemset(plan->d_status, 0, sizeof(int)) != cudaSuccess) return SOG_ERR_CUDA;
+  if (plan->launch_error) {
+    plan->launch_error = 0;
+    return SOG_ERR_CUDA;
+  }
+  if (st & 2) return SOG_ERR_OUT_OF_BOX;
+  if (st & 1) return SOG_ERR_NONNEUTRAL;
+  return SOG_OK;
+}
+
+sog_status sog_plan_set_timing(sog_plan* plan, int32_t enable) {
+  if (!plan) return SOG_ERR_ARG;
+  if (enable && !plan->events_ready) {
+    for (int i = 0; i <= SOG_NSTAGES; ++i)
+      if (cudaEventCreate(&plan->ev[i]) != cudaSuccess) return SOG_ERR_CUDA;
+    plan->events_ready = 1;
+  }
+  plan->timing = enable ? 1 : 0;
+  return SOG_OK;
+}
+
+sog_status sog_plan_get_timing(sog_plan* plan, float* ms) {
+  if (!plan || !ms) return SOG_ERR_ARG;
+  for (int i = 0; i < SOG_NSTAGES; ++i) ms[i] = 0.0f;
+  if (!plan->events_ready || !plan->ev_used[SOG_NSTAGES]) return SOG_OK;
+  if (cudaEventSynchronize(plan->ev[SOG_NSTAGES]) != cudaSuccess) return SOG_ERR_CUDA;
+  // each recorded stage runs until the next recorded event
+  int prev = -1;
+  for (int i = 0; i <= SOG_NSTAGES; ++i) {
+    if (!plan->ev_used[i]) continue;
+    if (prev >= 0) {
+      float t = 0.0f;
+      if (cudaEventElapsedTime(&t, plan->ev[prev], plan->ev[i]) != cudaSuccess) return SOG_ERR_CUDA;
+      ms[prev] = t;
+    }
+    prev = i;
+  }
+  return SOG_OK;
+}
+
+int64_t sog_plan_launches(const sog_plan* plan) { return plan ? plan->launches : 0; }
+
+void sog_plan_destroy(sog_plan* plan) {
+  if (!plan) return;
+  cudaStreamSynchronize(plan->last_stream);
+  if (plan->events_ready)
+    for (int i = 0; i <= SOG_NSTAGES; ++i) cudaEventDestroy(plan->ev[i]);
+  sogk::release_graphs(plan);
+  cudaStreamDestroy(plan->cap_stream);
+  cudaFree(plan->arena);
+  delete plan;
+}
+
+}  // extern "C"

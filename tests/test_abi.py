@@ -1,0 +1,61 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+entry point declared in include/sog.h; the binding fails loudly without it."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "sog.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(sog_[a-z_]+)\s*\(", src)
+    return sorted(set(n for n in names if n != "sog_status"))
+
+
+def test_header_declares_the_documented_entry_points():
+    names = declared_functions()
+    for n in ("sog_plan_create", "sog_eval", "sog_plan_destroy", "sog_select_params",
+              "sog_eval_host", "sog_plan_check", "sog_eval_components"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2412_04595_gb300 import _build
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_select_params_through_the_abi_without_gpu(oracle_mod):
+    """sog_select_params is host-only: callable here and equal to the
+    oracle's own selection (Sec. 4.4) for the benchmark configuration."""
+    from paper_2412_04595_gb300 import _build, binding
+    _build.build()
+    a = binding.sog_select_params(100000, 100.0, 100.0, 100.0, 1e-6, n_nb=120)
+    b = oracle_mod.select_params(100000, 100.0, 100.0, 100.0, 1e-6, n_nb=120)
+    for k in ("M", "m", "I", "P_win", "I_long", "P_cheb"):
+        assert tuple(map(int, __import__("numpy").atleast_1d(a[k]))) == \
+            tuple(map(int, __import__("numpy").atleast_1d(b[k]))), k
+    for k in ("rc", "sigma", "hz"):
+        assert abs(a[k] - b[k]) <= 1e-13 * abs(b[k])
+
+
+def test_argument_errors_are_reported():
+    from paper_2412_04595_gb300 import binding
+    with pytest.raises(binding.SogError):
+        binding.sog_select_params(1, 10.0, 10.0, 10.0, 1e-6)
+    with pytest.raises(binding.SogError):
+        binding.sog_select_params(100, 10.0, 10.0, 10.0, 0.0)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    from paper_2412_04595_gb300 import _build, binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", os.path.join(ROOT, "no_such_dir", "libsog.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.load()
