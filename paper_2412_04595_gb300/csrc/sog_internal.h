@@ -66,7 +66,7 @@ struct GraphEntry {
   double* pp;
   double* pg;
   int timing;                      // stage events captured in the graph
-  int ev_used[16];
+  int ev_used[2 * SOG_NSTAGES];
   cudaGraphExec_t exec;
   int64_t launches;
   uint64_t last_use;
@@ -126,11 +126,14 @@ struct sog_plan {
   cudaStream_t last_stream;
   // stage timers (sog_plan_set_timing) and kernel launch count of the last eval
   int timing, events_ready;
-  cudaEvent_t ev[SOG_NSTAGES + 1];
-  int ev_used[SOG_NSTAGES + 1];
+  cudaEvent_t ev[2 * SOG_NSTAGES];   // start and end of each stage
+  int ev_used[2 * SOG_NSTAGES];
   int64_t launches;
-  // captured evaluations replayed with one cudaGraphLaunch
+  // captured evaluations replayed with one cudaGraphLaunch; the near field
+  // runs on side_stream concurrently with the mid and long ranges
   cudaStream_t cap_stream;
+  cudaStream_t side_stream;
+  cudaEvent_t ev_fork, ev_join;
   sogk::GraphEntry graphs[sogk::kMaxGraphs];
   int n_graphs;
   uint64_t use_clock;

@@ -71,6 +71,8 @@ __device__ __forceinline__ double dceil(double x) { return ceil(x); }
 __device__ __forceinline__ float drint(float x) { return rintf(x); }
 __device__ __forceinline__ double drint(double x) { return rint(x); }
 __device__ __forceinline__ float drsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float ddiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
 __device__ __forceinline__ double drsqrt(double x) { return rsqrt(x); }
 
 // Window phi(v) (v = offset / half-width) and d phi / dv; zero outside |v| <= 1.
@@ -85,7 +87,7 @@ __device__ __forceinline__ void win_eval(const WinT<T>& w, T v, T& val, T& dval)
     // no cancellation near the window centre, where the weights are largest
     const T a2 = (one - v) * (one + v);
     const T a = dsqrt(a2);
-    val = dexp(-w.shape * v * v / (one + a));
+    val = dexp(-w.shape * ddiv(v * v, one + a));
     if (a2 > T(0)) dval = -val * w.shape * v * drsqrt(a2);
   } else {
     val = dexp(-w.shape * v * v);
@@ -332,22 +334,104 @@ constexpr int kNearQ = 64;       // per-warp queue of accepted pairs
 // source particles staged per pass and table entries kept in shared memory
 // (static shared memory stays under 48 KB for both element types)
 template <typename T> struct NearCfg;
-template <> struct NearCfg<float> { static constexpr int src = 1280, tab = 2304; };
-template <> struct NearCfg<double> { static constexpr int src = 640, tab = 576; };
+template <> struct NearCfg<float> { static constexpr int src = 1088, tab = 2304; };
+template <> struct NearCfg<double> { static constexpr int src = 448, tab = 576; };
 
-// Near field, Eq. (2.28): one CTA per cell, the particles of the (up to 27)
-// neighbouring cells staged in shared memory (whole cells per pass; one pass
-// in the usual case).  A warp takes one target at a time and walks the staged
-// cells: its lanes test 32 candidate sources per step, the pairs inside r_c
-// are compacted into a per-warp queue (ballot + prefix count), and every full
-// batch of 32 queued pairs is evaluated with all lanes busy, so the kernel
-// table is only evaluated for accepted pairs and without divergence.
-//
-// Minimum image: with at least three cells per periodic dimension a source
-// cell beyond the box edge is an image at a known shift, and the difference
-// is formed as (x_i + s) - (x_j - s) with s = +-L/2; both brackets are exact
-// (Sterbenz), so a wrapped pair keeps the accuracy of an unwrapped one.
-// With fewer cells the shift is found per pair by rounding.
+// 1/sqrt and sqrt of the squared distance.  FP32: the hardware reciprocal
+// square root (relative error ~1e-7) in place of an IEEE sqrt and division.
+__device__ __forceinline__ void inv_dist(float r2, float& rr, float& rinv) {
+  rinv = rsqrtf(r2);
+  rr = r2 * rinv;
+}
+__device__ __forceinline__ void inv_dist(double r2, double& rr, double& rinv) {
+  rr = sqrt(r2);
+  rinv = 1.0 / rr;
+}
+
+// One warp, one target: test the staged sources 32 at a time, queue the
+// pairs inside r_c (ballot + prefix count) and evaluate every full batch of
+// 32 queued pairs with all lanes busy.  SHIFT: sources carry a periodic
+// shift s (dx = (x_i + s) - (x_j - s), both brackets exact).
+template <typename T, bool SHIFT>
+__device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restrict__ src,
+                                            const float2* __restrict__ sh, int nsteps, T rc2,
+                                            const T* __restrict__ tab, int K, int D, T hK, T ihK,
+                                            P4<T>* __restrict__ myq, T* __restrict__ myr,
+                                            T& o_phi, T& o_gx, T& o_gy, T& o_gz) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const T ihK2 = T(2) * ihK;
+  Acc<T> phi{0, 0};
+  T gx = 0, gy = 0, gz = 0;
+  int qn = 0, qh = 0;
+  auto eval_batch = [&](int cnt) {
+    if (lane < cnt) {
+      const int e = (qh + lane) & (kNearQ - 1);
+      const P4<T> d = myq[e];
+      T rr, rinv;
+      inv_dist(myr[e], rr, rinv);
+      int kk = (int)(rr * ihK);
+      kk = kk < K ? kk : K - 1;
+      const T u = (rr - (T)kk * hK) * ihK2 - T(1);
+      const T* cf = tab + kk * (D + 1);
+      T p = cf[D], dp = T(0);
+      for (int jj = D - 1; jj >= 0; --jj) {
+        dp = dp * u + p;
+        p = p * u + cf[jj];
+      }
+      // g(r) = 1 - r F_M(r) = p; near kernel G = g/r; dG/dr = (g' - g/r)/r
+      const T gp = dp * ihK2;
+      phi.add(d.q * p * rinv);
+      const T f = d.q * (gp - p * rinv) * rinv * rinv;
+      gx += f * d.x;
+      gy += f * d.y;
+      gz += f * d.z;
+    }
+    qh += cnt;
+  };
+  for (int st = 0; st < nsteps; ++st) {
+    const int k = st * 32 + lane;
+    const P4<T> b = src[k];
+    T dx, dy;
+    if (SHIFT) {
+      const float2 s2 = sh[k];
+      dx = (a.x + (T)s2.x) - b.x;
+      dy = (a.y + (T)s2.y) - b.y;
+    } else {
+      dx = a.x - b.x;
+      dy = a.y - b.y;
+    }
+    const T dz = a.z - b.z;
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    // r2 == 0 only for the target itself (coincident charges are invalid input)
+    const bool in = r2 < rc2 && r2 > T(0);
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) {
+      const int e = (qn + __popc(m & lt)) & (kNearQ - 1);
+      myq[e] = P4<T>{dx, dy, dz, b.q};
+      myr[e] = r2;
+    }
+    qn += __popc(m);
+    __syncwarp();
+    if (qn - qh >= 32) {
+      eval_batch(32);
+      __syncwarp();
+    }
+  }
+  if (qn - qh > 0) eval_batch(qn - qh);
+  __syncwarp();
+  o_phi = phi.get();
+  o_gx = gx;
+  o_gy = gy;
+  o_gz = gz;
+}
+
+// Near field, Eq. (2.28): one CTA per cell.  The particles of the (up to 27)
+// neighbouring cells are staged contiguously in shared memory (padded to a
+// multiple of 32 with inert far-away sources); warps take the cell's
+// targets one at a time (near_target).  Cells away from the periodic edges
+// need no shifts; with fewer than three cells per periodic dimension the
+// minimum image is found per pair by rounding instead.
 template <typename T>
 __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* __restrict__ rec,
                                                       const int* __restrict__ cstart,
@@ -357,13 +441,13 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
                                                       double* __restrict__ grad_out) {
   constexpr int kNearSrc = NearCfg<T>::src, kNearTab = NearCfg<T>::tab;
   __shared__ P4<T> src[kNearSrc];                  // x - s, y - s, z, q
+  __shared__ float2 shs[kNearSrc];                 // s (periodic shift) per source
   __shared__ P4<T> qd[kNearThreads / 32][kNearQ];  // dx, dy, dz, q_j
   __shared__ T qr[kNearThreads / 32][kNearQ];      // r^2
   __shared__ T stab[kNearTab];
-  __shared__ int cb[27], cn[27];                   // first source, count per cell
-  __shared__ T csx[27], csy[27];
-  __shared__ int seg_c[64], seg_b[64], seg_n[64], seg_o[64];  // staged segments
-  __shared__ int ncell, nseg;
+  __shared__ int cb[27], coff[28];
+  __shared__ float csx[27], csy[27];
+  __shared__ int ncell, any_shift;
   const int c = blockIdx.x;
   const int tb = cstart[c], te = cstart[c + 1];
   if (tb == te) return;
@@ -371,7 +455,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
   const bool tab_sm = ntab <= kNearTab;
   if (tab_sm)
     for (int i = threadIdx.x; i < ntab; i += blockDim.x) stab[i] = tab[i];
-  const bool shifted = g.nc[0] >= 3 && g.nc[1] >= 3;
+  const bool periodic_cells = g.nc[0] >= 3 && g.nc[1] >= 3;
   const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
   if (threadIdx.x == 0) {
     int lo[3], hi[3];
@@ -382,70 +466,61 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
     }
     lo[2] = max(cz - 1, 0);
     hi[2] = min(cz + 1, g.nc[2] - 1);
-    int n = 0;
+    int n = 0, off = 0, anys = 0;
     for (int z = lo[2]; z <= hi[2]; ++z)
       for (int y0 = lo[1]; y0 <= hi[1]; ++y0)
         for (int x0 = lo[0]; x0 <= hi[0]; ++x0) {
           const int y = (y0 + g.nc[1]) % g.nc[1], x = (x0 + g.nc[0]) % g.nc[0];
           const int k = (z * g.nc[1] + y) * g.nc[0] + x;
           cb[n] = cstart[k];
-          cn[n] = cstart[k + 1] - cstart[k];
+          coff[n] = off;
           // source beyond the -L/2 edge sits near +L/2: s = +L/2, and vice versa
-          csx[n] = !shifted ? T(0) : (x0 < 0 ? (T)g.halfL[0] : (x0 >= g.nc[0] ? (T)(-g.halfL[0]) : T(0)));
-          csy[n] = !shifted ? T(0) : (y0 < 0 ? (T)g.halfL[1] : (y0 >= g.nc[1] ? (T)(-g.halfL[1]) : T(0)));
+          float sx = 0.f, sy = 0.f;
+          if (periodic_cells) {
+            sx = x0 < 0 ? (float)g.halfL[0] : (x0 >= g.nc[0] ? (float)(-g.halfL[0]) : 0.f);
+            sy = y0 < 0 ? (float)g.halfL[1] : (y0 >= g.nc[1] ? (float)(-g.halfL[1]) : 0.f);
+          }
+          csx[n] = sx;
+          csy[n] = sy;
+          anys |= (sx != 0.f || sy != 0.f);
+          off += cstart[k + 1] - cstart[k];
           ++n;
         }
+    coff[n] = off;
     ncell = n;
+    any_shift = anys;
   }
   __syncthreads();
   const T* tb_ = tab_sm ? stab : tab;
-  const T Lx = (T)g.L[0], Ly = (T)g.L[1];
-  const T iLx = (T)(1.0 / g.L[0]), iLy = (T)(1.0 / g.L[1]);
   const T rc = (T)g.rc, rc2 = rc * rc;
-  const T hK = rc / (T)g.K, ihK = (T)g.K / rc, ihK2 = T(2) * ihK;
-  const int D = g.D;
+  const T hK = rc / (T)g.K, ihK = (T)g.K / rc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNearThreads / 32;
-  const unsigned lt = (1u << lane) - 1u;
   P4<T>* myq = qd[warp];
   T* myr = qr[warp];
   const int ntg = te - tb;
-  // passes over the neighbourhood: whole cells (split if larger than the buffer)
-  int cell0 = 0, off0 = 0;
-  bool first = true;
-  while (true) {
+  const int nsrc = coff[ncell];
+  const bool shifted = any_shift != 0;
+  const T Lx = (T)g.L[0], Ly = (T)g.L[1];
+  const T iLx = (T)(1.0 / g.L[0]), iLy = (T)(1.0 / g.L[1]);
+  // sources in passes of at most kNearSrc (one pass in the usual case)
+  for (int s0 = 0; s0 < nsrc; s0 += kNearSrc) {
+    const int ns = min(kNearSrc, nsrc - s0);
+    const int nsteps = (ns + 31) >> 5;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int used = 0, ns = 0;
-      while (cell0 < ncell && ns < 64) {
-        const int take = min(cn[cell0] - off0, kNearSrc - used);
-        if (take <= 0 && cn[cell0] - off0 > 0) break;  // buffer full
-        if (take > 0) {
-          seg_c[ns] = cell0;
-          seg_b[ns] = cb[cell0] + off0;
-          seg_n[ns] = take;
-          seg_o[ns] = used;
-          ++ns;
-          used += take;
-        }
-        off0 += max(take, 0);
-        if (off0 >= cn[cell0]) {
-          ++cell0;
-          off0 = 0;
-        }
-      }
-      nseg = ns;
-    }
-    __syncthreads();
-    const int ns = nseg;
-    if (ns == 0) break;
-    for (int sgi = warp; sgi < ns; sgi += nw) {
-      const int cc = seg_c[sgi], b0 = seg_b[sgi], n0 = seg_n[sgi], o0 = seg_o[sgi];
-      const T sx = csx[cc], sy = csy[cc];
-      for (int k = lane; k < n0; k += 32) {
-        P4<T> b = rec[b0 + k];
-        b.x = b.x - sx;
-        b.y = b.y - sy;
-        src[o0 + k] = b;
+    for (int k = threadIdx.x; k < nsteps * 32; k += blockDim.x) {
+      if (k < ns) {
+        const int gk = s0 + k;
+        int cc = 0;
+        while (coff[cc + 1] <= gk) ++cc;
+        P4<T> b = rec[cb[cc] + gk - coff[cc]];
+        const float sx = csx[cc], sy = csy[cc];
+        b.x = b.x - (T)sx;
+        b.y = b.y - (T)sy;
+        src[k] = b;
+        shs[k] = make_float2(sx, sy);
+      } else {
+        src[k] = P4<T>{T(1e30), T(1e30), T(1e30), T(0)};
+        shs[k] = make_float2(0.f, 0.f);
       }
     }
     __syncthreads();
@@ -454,79 +529,54 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
       if (tt >= ntg) break;
       const int ti = tb + tt;
       const P4<T> a = rec[ti];
-      Acc<T> phi{0, 0};
-      T gx = 0, gy = 0, gz = 0;
-      int qn = 0, qh = 0;  // queued, evaluated (warp-uniform)
-      auto eval_batch = [&](int cnt) {
-        if (lane < cnt) {
-          const int e = (qh + lane) & (kNearQ - 1);
-          const P4<T> d = myq[e];
-          const T r2 = myr[e];
-          const T rr = dsqrt(r2);
-          const T rinv = T(1) / rr;
+      T v0, v1, v2, v3;
+      if (!periodic_cells) {
+        // few cells: minimum image per pair (sources unshifted)
+        Acc<T> phi{0, 0};
+        T gx = 0, gy = 0, gz = 0;
+        const T ihK2 = T(2) * ihK;
+        for (int k = lane; k < ns; k += 32) {  // padding excluded: rounding would fold it back
+          const P4<T> b = src[k];
+          T dx = a.x - b.x, dy = a.y - b.y;
+          const T dz = a.z - b.z;
+          dx -= Lx * drint(dx * iLx);
+          dy -= Ly * drint(dy * iLy);
+          const T r2 = dx * dx + dy * dy + dz * dz;
+          if (!(r2 < rc2 && r2 > T(0))) continue;
+          T rr, rinv;
+          inv_dist(r2, rr, rinv);
           int kk = (int)(rr * ihK);
           kk = kk < g.K ? kk : g.K - 1;
           const T u = (rr - (T)kk * hK) * ihK2 - T(1);
-          const T* cf = tb_ + kk * (D + 1);
-          T p = cf[D], dp = T(0);
-          for (int jj = D - 1; jj >= 0; --jj) {
+          const T* cf = tb_ + kk * (g.D + 1);
+          T p = cf[g.D], dp = T(0);
+          for (int jj = g.D - 1; jj >= 0; --jj) {
             dp = dp * u + p;
             p = p * u + cf[jj];
           }
-          // g(r) = 1 - r F_M(r) = p; near kernel G = g/r; dG/dr = (g' - g/r)/r
           const T gp = dp * ihK2;
-          phi.add(d.q * p * rinv);
-          const T f = d.q * (gp - p * rinv) * rinv * rinv;
-          gx += f * d.x;
-          gy += f * d.y;
-          gz += f * d.z;
+          phi.add(b.q * p * rinv);
+          const T f = b.q * (gp - p * rinv) * rinv * rinv;
+          gx += f * dx;
+          gy += f * dy;
+          gz += f * dz;
         }
-        qh += cnt;
-      };
-      for (int sgi = 0; sgi < ns; ++sgi) {
-        const int cc = seg_c[sgi], n0 = seg_n[sgi], o0 = seg_o[sgi];
-        const T ax = a.x + csx[cc], ay = a.y + csy[cc];
-        for (int k0 = 0; k0 < n0; k0 += 32) {
-          const int k = k0 + lane;
-          bool in = false;
-          T dx = 0, dy = 0, dz = 0, r2 = 0, qj = 0;
-          if (k < n0) {
-            const P4<T> b = src[o0 + k];
-            dx = ax - b.x;
-            dy = ay - b.y;
-            dz = a.z - b.z;
-            if (!shifted) {
-              dx -= Lx * drint(dx * iLx);
-              dy -= Ly * drint(dy * iLy);
-            }
-            r2 = dx * dx + dy * dy + dz * dz;
-            qj = b.q;
-            // r2 == 0 only for the target itself (coincident charges are invalid input)
-            in = r2 < rc2 && r2 > T(0);
-          }
-          const unsigned m = __ballot_sync(0xffffffffu, in);
-          if (in) {
-            const int e = (qn + __popc(m & lt)) & (kNearQ - 1);
-            myq[e] = P4<T>{dx, dy, dz, qj};
-            myr[e] = r2;
-          }
-          qn += __popc(m);
-          __syncwarp();
-          if (qn - qh >= 32) {
-            eval_batch(32);
-            __syncwarp();
-          }
-        }
+        v0 = phi.get();
+        v1 = gx;
+        v2 = gy;
+        v3 = gz;
+      } else if (shifted) {
+        near_target<T, true>(a, src, shs, nsteps, rc2, tb_, g.K, g.D, hK, ihK, myq, myr, v0, v1, v2, v3);
+      } else {
+        near_target<T, false>(a, src, shs, nsteps, rc2, tb_, g.K, g.D, hK, ihK, myq, myr, v0, v1, v2, v3);
       }
-      if (qn - qh > 0) eval_batch(qn - qh);
-      T v0 = phi.get(), v1 = gx, v2 = gy, v3 = gz;
       v0 = warp_sum(v0);
       v1 = warp_sum(v1);
       v2 = warp_sum(v2);
       v3 = warp_sum(v3);
       if (lane == 0) {
         const int o = perm[ti];
-        if (first) {
+        if (s0 == 0) {
           phi_out[o] = (double)v0;
           grad_out[3 * o] = (double)v1;
           grad_out[3 * o + 1] = (double)v2;
@@ -538,9 +588,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
           grad_out[3 * o + 2] += (double)v3;
         }
       }
-      __syncwarp();
     }
-    first = false;
   }
 }
 
@@ -1266,17 +1314,20 @@ static size_t long_smem(const sog_plan* p, size_t es, bool gather) {
     if (e_ != cudaSuccess) return e_;  \
   } while (0)
 
-static void mark(sog_plan* p, int stage, cudaStream_t s) {
+// Stage timers: event 2k at the start of stage k, 2k+1 at its end, on the
+// stream the stage runs on.  Inside a graph the records are external nodes.
+static void mark_ev(sog_plan* p, int idx, cudaStream_t s) {
   if (!p->timing) return;
-  // inside a graph the record must be an external node to be timed later
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cs);
   if (cs == cudaStreamCaptureStatusActive)
-    cudaEventRecordWithFlags(p->ev[stage], s, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(p->ev[idx], s, cudaEventRecordExternal);
   else
-    cudaEventRecord(p->ev[stage], s);
-  p->ev_used[stage] = 1;
+    cudaEventRecord(p->ev[idx], s);
+  p->ev_used[idx] = 1;
 }
+static void mark_begin(sog_plan* p, int stage, cudaStream_t s) { mark_ev(p, 2 * stage, s); }
+static void mark_end(sog_plan* p, int stage, cudaStream_t s) { mark_ev(p, 2 * stage + 1, s); }
 
 #define LAUNCH_CHECK()                 \
   do {                                 \
@@ -1288,7 +1339,7 @@ template <typename T>
 static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E, T* F,
                          double* pp, double* pg, cudaStream_t s) {
   p->launches = 0;
-  for (int i = 0; i <= SOG_NSTAGES; ++i) p->ev_used[i] = 0;
+  for (int i = 0; i < 2 * SOG_NSTAGES; ++i) p->ev_used[i] = 0;
   const int N = (int)p->N;
   const sog_params& m = p->prm;
   PrepGeom g{};
@@ -1320,7 +1371,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   P4<T>* rl = reinterpret_cast<P4<T>*>(p->d_rec_long);
 
   // 1. binning
-  mark(p, 0, s);
+  mark_begin(p, 0, s);
   SOG_CK(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * p->cnt_off[3], s));
   P4<T>* tmp = reinterpret_cast<P4<T>*>(p->d_rec_tmp);
   k_bin_count<T><<<kRedBlocks, 256, 0, s>>>(g, q, r, N, p->d_key, p->d_rank, p->d_cnt, off, tmp,
@@ -1332,6 +1383,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
                                                    p->d_rank, p->d_cnt, off, tmp, rn, rm, rl,
                                                    p->d_perm);
   LAUNCH_CHECK();
+  mark_end(p, 0, s);
 
   // 2. near field
   NearGeom ng{};
@@ -1345,14 +1397,20 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   ng.rc = m.rc;
   ng.K = p->near_K;
   ng.D = p->near_D;
-  mark(p, 1, s);
-  k_near<T><<<p->n_cells, kNearThreads, 0, s>>>(ng, rn, p->d_cnt + off.x, p->d_perm,
-                                                reinterpret_cast<const T*>(p->d_near_tab), pp, pg);
+  // the near field depends only on the binning: fork it onto the side stream
+  const cudaStream_t sn = p->side_stream;
+  SOG_CK(cudaEventRecord(p->ev_fork, s));
+  SOG_CK(cudaStreamWaitEvent(sn, p->ev_fork, 0));
+  mark_begin(p, 1, sn);
+  k_near<T><<<p->n_cells, kNearThreads, 0, sn>>>(ng, rn, p->d_cnt + off.x, p->d_perm,
+                                                 reinterpret_cast<const T*>(p->d_near_tab), pp, pg);
   LAUNCH_CHECK();
+  mark_end(p, 1, sn);
+  SOG_CK(cudaEventRecord(p->ev_join, sn));
 
   // 3. mid range
   if (p->has_mid) {
-    mark(p, 2, s);
+    mark_begin(p, 2, s);
     T* grid = reinterpret_cast<T*>(p->d_grid);
     const size_t gbytes = (size_t)m.I[2] * m.I[1] * (m.I[0] + 2) * sizeof(T);
     SOG_CK(cudaMemsetAsync(grid, 0, gbytes, s));
@@ -1361,15 +1419,18 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     const dim3 mgrid(p->n_tiles_mid, p->gm.chunks);
     SOG_DISPATCH_PW(p->wm.P, k_mid_spread, mgrid, sm, s, p->gm, w, rm, p->d_cnt + off.y, grid);
     LAUNCH_CHECK();
-    mark(p, 3, s);
+    mark_end(p, 2, s);
+    mark_begin(p, 3, s);
     SOG_CK(fft_mid_forward_conv_inverse<T>(p, s));
     p->launches += 5;
-    mark(p, 4, s);
+    mark_end(p, 3, s);
+    mark_begin(p, 4, s);
     const size_t sm2 = mid_smem(p, sizeof(T), true);
     const double3 invh = make_double3(1.0 / p->h[0], 1.0 / p->h[1], 1.0 / p->h[2]);
     SOG_DISPATCH_PW(p->wm.P, k_mid_gather, mgrid, sm2, s, p->gm, w, rm, p->d_cnt + off.y,
                     p->d_perm + N, grid, invh, pp + N, pg + 3 * (size_t)N);
     LAUNCH_CHECK();
+    mark_end(p, 4, s);
   } else {
     SOG_CK(cudaMemsetAsync(pp + N, 0, sizeof(double) * N, s));
     SOG_CK(cudaMemsetAsync(pg + 3 * (size_t)N, 0, sizeof(double) * 3 * N, s));
@@ -1377,7 +1438,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
 
   // 4-5. long range and its k = 0 mode
   if (p->has_long) {
-    mark(p, 5, s);
+    mark_begin(p, 5, s);
     const int P = m.P_cheb;
     T* A = reinterpret_cast<T*>(p->d_lA);
     T* B = reinterpret_cast<T*>(p->d_lB);
@@ -1404,7 +1465,8 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
       SOG_DISPATCH_PW(p->wl.P, k_long_spread, lgrid, sm, s, p->gl, w, P, rl, p->d_cnt + off.z, A);
       LAUNCH_CHECK();
     }
-    mark(p, 6, s);
+    mark_end(p, 5, s);
+    mark_begin(p, 6, s);
     SOG_CK(fft_long_pass<T>(p, false, s));
     p->launches += 2;
     const int C = m.I_long[0] / 2 + 1;
@@ -1415,14 +1477,16 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     LAUNCH_CHECK();
     SOG_CK(fft_long_pass<T>(p, true, s));
     p->launches += 2;
-    mark(p, 7, s);
+    mark_end(p, 6, s);
+    mark_begin(p, 7, s);
     const size_t sm2 = long_smem(p, sizeof(T), true);
     const double3 sc = make_double3(1.0 / p->hl[0], 1.0 / p->hl[1], 2.0 / m.L[2]);
     const dim3 lgrid2(p->n_tiles_long, p->gl.chunks);
     SOG_DISPATCH_PW(p->wl.P, k_long_gather, lgrid2, sm2, s, p->gl, w, P, rl, p->d_cnt + off.z,
                     p->d_perm + 2 * (size_t)N, B, sc, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     LAUNCH_CHECK();
-    mark(p, 8, s);
+    mark_end(p, 7, s);
+    mark_begin(p, 8, s);
     double* mpart = p->d_red + 2 * kRedBlocks;
     if (P <= 16)
       k_k0_moments<T, 16><<<kRedBlocks, 256, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
@@ -1437,6 +1501,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     k_k0_eval<T><<<(N + 255) / 256, 256, 0, s>>>(r, N, P, 0.5 * m.L[2], p->d_k0nu,
                                                 pp + 3 * (size_t)N, pg + 9 * (size_t)N);
     LAUNCH_CHECK();
+    mark_end(p, 8, s);
   } else {
     SOG_CK(cudaMemsetAsync(pp + 2 * (size_t)N, 0, sizeof(double) * 2 * N, s));
     SOG_CK(cudaMemsetAsync(pg + 6 * (size_t)N, 0, sizeof(double) * 6 * N, s));
@@ -1445,8 +1510,9 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     LAUNCH_CHECK();
   }
 
-  // 6. assembly
-  mark(p, 9, s);
+  // join the near field, then 6. assembly
+  SOG_CK(cudaStreamWaitEvent(s, p->ev_join, 0));
+  mark_begin(p, 9, s);
   if (phi || F || E) {
     double* epart = p->d_red + 2 * kRedBlocks + (size_t)kRedBlocks * kMaxCheb;
     k_assemble<T><<<kRedBlocks, 256, 0, s>>>(q, N, pp, pg, p->selfsum, phi, F, epart);
@@ -1456,7 +1522,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
       LAUNCH_CHECK();
     }
   }
-  mark(p, SOG_NSTAGES, s);
+  mark_end(p, 9, s);
   return cudaSuccess;
 }
 
@@ -1537,13 +1603,13 @@ static cudaError_t eval_graph(sog_plan* p, const void* q, const void* r, void* p
     g.pp = pp;
     g.pg = pg;
     g.timing = p->timing;
-    for (int i = 0; i <= SOG_NSTAGES; ++i) g.ev_used[i] = p->ev_used[i];
+    for (int i = 0; i < 2 * SOG_NSTAGES; ++i) g.ev_used[i] = p->ev_used[i];
     g.launches = p->launches;
     hit = &g;
   }
   hit->last_use = ++p->use_clock;
   p->launches = hit->launches;
-  for (int i = 0; i <= SOG_NSTAGES; ++i) p->ev_used[i] = hit->ev_used[i];
+  for (int i = 0; i < 2 * SOG_NSTAGES; ++i) p->ev_used[i] = hit->ev_used[i];
   return cudaGraphLaunch(hit->exec, s);
 }
 

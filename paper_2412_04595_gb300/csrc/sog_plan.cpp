@@ -795,7 +795,10 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     delete p;
     return SOG_ERR_CUDA;
   }
-  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(base);
     delete p;
@@ -880,7 +883,7 @@ sog_status sog_plan_check(sog_plan* plan) {
 sog_status sog_plan_set_timing(sog_plan* plan, int32_t enable) {
   if (!plan) return SOG_ERR_ARG;
   if (enable && !plan->events_ready) {
-    for (int i = 0; i <= SOG_NSTAGES; ++i)
+    for (int i = 0; i < 2 * SOG_NSTAGES; ++i)
       if (cudaEventCreate(&plan->ev[i]) != cudaSuccess) return SOG_ERR_CUDA;
     plan->events_ready = 1;
   }
@@ -891,18 +894,14 @@ sog_status sog_plan_set_timing(sog_plan* plan, int32_t enable) {
 sog_status sog_plan_get_timing(sog_plan* plan, float* ms) {
   if (!plan || !ms) return SOG_ERR_ARG;
   for (int i = 0; i < SOG_NSTAGES; ++i) ms[i] = 0.0f;
-  if (!plan->events_ready || !plan->ev_used[SOG_NSTAGES]) return SOG_OK;
-  if (cudaEventSynchronize(plan->ev[SOG_NSTAGES]) != cudaSuccess) return SOG_ERR_CUDA;
-  // each recorded stage runs until the next recorded event
-  int prev = -1;
-  for (int i = 0; i <= SOG_NSTAGES; ++i) {
-    if (!plan->ev_used[i]) continue;
-    if (prev >= 0) {
-      float t = 0.0f;
-      if (cudaEventElapsedTime(&t, plan->ev[prev], plan->ev[i]) != cudaSuccess) return SOG_ERR_CUDA;
-      ms[prev] = t;
-    }
-    prev = i;
+  if (!plan->events_ready) return SOG_OK;
+  for (int k = 0; k < SOG_NSTAGES; ++k) {
+    if (!plan->ev_used[2 * k] || !plan->ev_used[2 * k + 1]) continue;
+    if (cudaEventSynchronize(plan->ev[2 * k + 1]) != cudaSuccess) return SOG_ERR_CUDA;
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, plan->ev[2 * k], plan->ev[2 * k + 1]) != cudaSuccess)
+      return SOG_ERR_CUDA;
+    ms[k] = t;
   }
   return SOG_OK;
 }
@@ -913,9 +912,12 @@ void sog_plan_destroy(sog_plan* plan) {
   if (!plan) return;
   cudaStreamSynchronize(plan->last_stream);
   if (plan->events_ready)
-    for (int i = 0; i <= SOG_NSTAGES; ++i) cudaEventDestroy(plan->ev[i]);
+    for (int i = 0; i < 2 * SOG_NSTAGES; ++i) cudaEventDestroy(plan->ev[i]);
   sogk::release_graphs(plan);
   cudaStreamDestroy(plan->cap_stream);
+  cudaStreamDestroy(plan->side_stream);
+  cudaEventDestroy(plan->ev_fork);
+  cudaEventDestroy(plan->ev_join);
   cudaFree(plan->arena);
   delete plan;
 }
