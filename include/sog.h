@@ -192,6 +192,33 @@ sog_status sog_plan_get_timing(sog_plan* plan, float* ms);
 /* Number of kernels the last evaluation launched. */
 int64_t sog_plan_launches(const sog_plan* plan);
 
+/*
+ * Assembly of Phi, F and U from the four parts that sog_eval_components
+ * returns, with no plan and no memory allocation.  The paper has no
+ * counterpart: it is a library convenience for callers that must not allocate
+ * device memory during a run, e.g. an integrator that has handed all free
+ * device memory to its own pools, or a loop on several streams that cannot
+ * afford the device-wide synchronisation of cudaMalloc / cudaFree.
+ *   N           number of charges, 1 <= N <= 715827882 (else SOG_ERR_ARG)
+ *   precision   SOG_PREC_FP64 or SOG_PREC_MIXED: element type of q, phi, F
+ *   prm         host; b, sigma, omega, M give the self-term coefficient
+ *               sum_l w_l (Eq. 2.22, 2.25)
+ *   q           [N]          device, plan type
+ *   phi_parts   [4 x N]      device, double, as from sog_eval_components
+ *   grad_parts  [4 x N x 3]  device, double; may be NULL when F is NULL
+ *   phi, E, F   outputs as in sog_eval; any may be NULL
+ * Enqueued on `stream`; returns without waiting.  The energy's partial sums
+ * go to a fixed device array of 304 doubles inside the library (any N uses
+ * it; nothing in it has to start at zero).  Its address is looked up on the
+ * first call on each device, which should come before any stream capture is
+ * begun on that device.  Calls that may run at the same time on one device
+ * (different streams or host threads without ordering) share that array and
+ * race on E; calls ordered on one stream do not.
+ */
+sog_status sog_assemble_noalloc(int64_t N, int32_t precision, const sog_params* prm,
+                                const void* q, const double* phi_parts, const double* grad_parts,
+                                void* phi, double* E, void* F, void* stream);
+
 /* Release the plan and its device memory (waits for its pending work). */
 void sog_plan_destroy(sog_plan* plan);
 

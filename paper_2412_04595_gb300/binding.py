@@ -92,9 +92,11 @@ def load(build_if_missing: bool = False):
     L.sog_plan_launches.restype = i64
     L.sog_status_str.argtypes = [ctypes.c_int]
     L.sog_status_str.restype = ctypes.c_char_p
+    L.sog_assemble_noalloc.argtypes = [i64, i32, ctypes.POINTER(SogParams), vp, vp, vp, vp, vp,
+                                       vp, vp]
     for f in ("sog_select_params", "sog_plan_create", "sog_plan_get_params", "sog_eval",
               "sog_eval_components", "sog_eval_host", "sog_plan_check", "sog_plan_set_timing",
-              "sog_plan_get_timing"):
+              "sog_plan_get_timing", "sog_assemble_noalloc"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -130,6 +132,31 @@ def sog_select_params(N, Lx, Ly, Lz, tol, window=SOG_WIN_ES, n_nb=None) -> dict:
     _check(load().sog_select_params(int(N), Lx, Ly, Lz, tol, ctypes.byref(o), ctypes.byref(out)),
            "sog_select_params")
     return out.to_dict()
+
+
+def sog_assemble_noalloc(params, q, phi_parts, grad_parts=None, phi=None, E=None, F=None,
+                         stream=None):
+    """sog_assemble_noalloc: Phi, U and F from the four parts of
+    ``Plan.eval_components`` without a plan or any device allocation.
+    ``params`` is a dict or SogParams; q, phi, F are contiguous CUDA tensors of
+    one dtype (float64: FP64, float32: mixed); the parts are float64."""
+    import torch
+    prec = {torch.float64: SOG_PREC_FP64, torch.float32: SOG_PREC_MIXED}.get(q.dtype)
+    if prec is None:
+        raise ValueError("q must be float32 or float64")
+    for t in (q, phi_parts, grad_parts, phi, E, F):
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("expected contiguous CUDA tensors")
+    for t in (phi, F):
+        if t is not None and t.dtype != q.dtype:
+            raise ValueError("phi and F must have the dtype of q")
+    for t in (phi_parts, grad_parts, E):
+        if t is not None and t.dtype != torch.float64:
+            raise ValueError("parts and E must be float64")
+    prm = params if isinstance(params, SogParams) else SogParams.from_dict(params)
+    _check(load().sog_assemble_noalloc(int(q.numel()), prec, ctypes.byref(prm), _ptr(q),
+                                       _ptr(phi_parts), _ptr(grad_parts), _ptr(phi), _ptr(E),
+                                       _ptr(F), _stream_ptr(stream)), "sog_assemble_noalloc")
 
 
 def _stream_ptr(stream):
