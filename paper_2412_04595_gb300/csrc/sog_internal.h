@@ -50,6 +50,25 @@ struct TileGeom {
   int chunks;        // CTAs per tile
 };
 
+// Tile kernels of the spreading and gathering steps.
+constexpr int kTileThreads = 256;  // 8 warps; the spread's row ownership relies on it
+constexpr int kTileBatch = 32;     // particles whose window weights are staged at once
+constexpr int kTileHeader = 896;   // bytes of row tables and per-particle offsets
+
+__host__ __device__ inline int mod32(int a) { return ((a % 32) + 32) % 32; }
+// Shared-memory strides of the padded tile (in elements), chosen so that the
+// 32 lanes of a warp touch 32 different banks:
+//   spreading: lanes over (dz, dx) of a window row, plane stride = P (mod 32);
+//   gathering: lanes over (dz, dy) rows, odd row pitch rp and plane stride
+//   = P rp (mod 32), so that lane e reads word e rp + dx (mod 32).
+__host__ __device__ inline int spread_plane_stride(int W0, int W1, int P) {
+  return W0 * W1 + mod32(P - W0 * W1);
+}
+__host__ __device__ inline int gather_row_pitch(int W0) { return W0 | 1; }
+__host__ __device__ inline int gather_plane_stride(int rp, int W1, int P) {
+  return rp * W1 + mod32(P * rp - rp * W1);
+}
+
 // Sizes of one evaluation's reduction scratch.
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
 // Largest dynamic shared memory of one CTA on sm_100-class GPUs (227 KB).

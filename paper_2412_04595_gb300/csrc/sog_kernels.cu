@@ -601,216 +601,310 @@ __device__ __forceinline__ int pmod(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Shared-memory layout of the tile kernels: padded tile, then the per-CTA
-// row table (offset of window row (dy, dz) in the padded tile, and dy, dz),
-// then per-warp weight vectors.
-template <typename T>
-struct MidSmem {
-  T* tile;
-  int* rowoff;
-  unsigned char* rdy;
-  unsigned char* rdz;
-  T* ws;
-};
-
-template <typename T>
-__device__ __forceinline__ MidSmem<T> mid_smem_layout(unsigned char* raw, const TileGeom& g, int P) {
-  MidSmem<T> m;
-  const int Wn = g.W[0] * g.W[1] * g.W[2];
-  m.tile = reinterpret_cast<T*>(raw);
-  m.rowoff = reinterpret_cast<int*>(m.tile + Wn);
-  m.rdy = reinterpret_cast<unsigned char*>(m.rowoff + kMaxWin * kMaxWin);
-  m.rdz = m.rdy + kMaxWin * kMaxWin;
-  m.ws = reinterpret_cast<T*>(m.rdz + kMaxWin * kMaxWin);  // offset is a multiple of 8
-  return m;
+// Particles [b, e) of a tile, split into contiguous parts when several CTAs
+// (blockIdx.y) share the tile; false when this CTA's part is empty.
+__device__ __forceinline__ bool chunk_range(int& b, int& e, int chunks) {
+  const int len = (e - b + chunks - 1) / chunks;
+  b += blockIdx.y * len;
+  e = min(e, b + len);
+  return b < e;
 }
 
-__device__ __forceinline__ void fill_rows(int* rowoff, unsigned char* rdy, unsigned char* rdz, int P,
-                                          int W0, int W1) {
-  for (int r = threadIdx.x; r < P * P; r += blockDim.x) {
-    const int dy = r % P, dz = r / P;
-    rowoff[r] = (dz * W1 + dy) * W0;
-    rdy[r] = (unsigned char)dy;
-    rdz[r] = (unsigned char)dz;
-  }
+// Offsets in the periodic grid of the rows of a padded tile whose corner is
+// (oy, oz): yoff[ly] = ((oy + ly) mod I1) * pitch, zoff[lz] = ((oz + lz) mod
+// I2) * I1 * pitch.  zplanes: for proxy planes, lz is the plane index n.
+__device__ __forceinline__ void tile_tables(const TileGeom& g, int oy, int oz, int nz, bool zplanes,
+                                            int* yoff, long long* zoff) {
+  for (int i = threadIdx.x; i < g.W[1]; i += blockDim.x) yoff[i] = pmod(oy + i, g.I[1]) * g.pitch;
+  for (int i = threadIdx.x; i < nz; i += blockDim.x)
+    zoff[i] = (long long)(zplanes ? i : pmod(oz + i, g.I[2])) * g.I[1] * g.pitch;
 }
 
-// Gridding, Eq. (3.7).  One CTA per (tile, chunk): the tile's particles are
-// spread into a padded tile in shared memory (a warp per particle, a lane per
-// (y, z) row of the P^3 window), then the padded tile is added to the
-// periodic grid.  The grid must be zero on entry.
-template <typename T, int PW>
-__global__ void __launch_bounds__(256) k_mid_spread(TileGeom g, WinT<T> w,
-                                                    const P4<T>* __restrict__ rec,
-                                                    const int* __restrict__ start,
-                                                    T* __restrict__ grid) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int tile = blockIdx.x;
-  const int b = start[tile], e = start[tile + 1];
-  const int chunk = blockIdx.y;
-  if (b + chunk >= e) return;
-  const int W0 = g.W[0], W1 = g.W[1], W2 = g.W[2];
-  const int Wn = W0 * W1 * W2;
-  const int P = PW > 0 ? PW : w.P;
-  const int PP = P * P;
-  MidSmem<T> sm = mid_smem_layout<T>(smraw, g, P);
-  T* st = sm.tile;
-  for (int i = threadIdx.x; i < Wn; i += blockDim.x) st[i] = T(0);
-  fill_rows(sm.rowoff, sm.rdy, sm.rdz, P, W0, W1);
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* wsx = sm.ws + warp * 3 * kMaxWin;
-  T* wsy = wsx + kMaxWin;
-  T* wsz = wsy + kMaxWin;
-  for (int pi = b + chunk + warp * g.chunks; pi < e; pi += nw * g.chunks) {
-    const P4<T> a = rec[pi];
-    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half),
-              gz0 = (int)dceil(a.z - w.half);
-    if (lane < P) {
-      T v, dv;
-      win_eval(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
-      wsx[lane] = v;
-      win_eval(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
-      wsy[lane] = v * a.q;
-      win_eval(w, ((T)(gz0 + lane) - a.z) * w.inv_half, v, dv);
-      wsz[lane] = v;
-    }
-    __syncwarp();
-    T* base = st + ((gz0 + g.pad_lo) * W1 + (gy0 + g.pad_lo)) * W0 + gx0 + g.pad_lo;
-    T rwx[PW > 0 ? PW : kMaxWin];
-#pragma unroll
-    for (int dx = 0; dx < (PW > 0 ? PW : kMaxWin); ++dx) rwx[dx] = dx < P ? wsx[dx] : T(0);
-    for (int row = lane; row < PP; row += 32) {
-      const T cyz = wsy[sm.rdy[row]] * wsz[sm.rdz[row]];
-      if (cyz != T(0)) {
-        T* rp = base + sm.rowoff[row];
-#pragma unroll
-        for (int dx = 0; dx < (PW > 0 ? PW : kMaxWin); ++dx)
-          if (dx < P) atomicAdd(rp + dx, cyz * rwx[dx]);
+// Asynchronous global -> shared copy of one element (cp.async): the loads of
+// a whole tile are in flight together instead of one row at a time.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Moves the padded tile between shared memory (row pitch rp, plane stride
+// ps) and the periodic grid, one warp per row (W0 <= 32): LOAD copies grid
+// to tile, otherwise the tile is added to the grid with atomics (tiles
+// overlap in their halos).  xw = wrapped x index of this lane.
+template <typename T, bool LOAD>
+__device__ __forceinline__ void tile_rows(T* __restrict__ grid, T* __restrict__ st, int W0, int W1,
+                                          int nz, int rp, int ps, const int* __restrict__ yoff,
+                                          const long long* __restrict__ zoff, int xw) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int ly = warp, lz = 0;
+  while (ly >= W1) { ly -= W1; ++lz; }
+  for (int row = warp; row < W1 * nz; row += nw) {
+    if (lane < W0) {
+      T* gp = grid + zoff[lz] + yoff[ly] + xw;
+      T* sp = st + lz * ps + ly * rp + lane;
+      if (LOAD) {
+        cp_async_elem(sp, gp);
+      } else {
+        const T v = *sp;
+        if (v != T(0)) atomicAdd(gp, v);
       }
     }
-    __syncwarp();
+    ly += nw;
+    while (ly >= W1) { ly -= W1; ++lz; }
   }
-  __syncthreads();
+  if (LOAD) cp_async_wait_all();
+}
+
+// Fixed-point accumulator of the spreading tile: int32 for FP32 plans, int64
+// for FP64 plans (integer shared-memory atomics are native; the sum is
+// exact and independent of the order of the additions).
+template <typename T> struct FixAcc;
+template <> struct FixAcc<float> {
+  using t = int;
+  static constexpr int bits = 30;
+  __device__ static int cvt(float v) { return __float2int_rn(v); }
+};
+template <> struct FixAcc<double> {
+  using t = long long;
+  static constexpr int bits = 62;
+  __device__ static long long cvt(double v) { return __double2ll_rn(v); }
+};
+
+__device__ __forceinline__ void fix_add(int* p, int v) { atomicAdd(p, v); }
+__device__ __forceinline__ void fix_add(long long* p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+// Gridding, Eq. (3.7).  One CTA per tile (or part of a tile).  The CTA's
+// particles are spread into a padded tile in shared memory held in fixed
+// point: the scale S = 2^(bits - e) with sum_j |q_j| < 2^e bounds every
+// partial sum by 2^bits, so the integer atomics cannot overflow.  A warp per
+// particle, lanes over the (dz, dy) rows of its window.  The padded tile is
+// then added to the grid (zero on entry).
+template <typename T, int PW>
+__global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T> w,
+                                                             const P4<T>* __restrict__ rec,
+                                                             const int* __restrict__ start,
+                                                             T* __restrict__ grid) {
+  using A = typename FixAcc<T>::t;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int tile = blockIdx.x;
+  int b = start[tile], e = start[tile + 1];
+  if (!chunk_range(b, e, g.chunks)) return;
+  const int W0 = g.W[0], W1 = g.W[1], W2 = g.W[2];
+  const int P = PW > 0 ? PW : w.P;
+  const int PP = P * P;
+  const int RP = gather_row_pitch(W0);
+  const int PS = gather_plane_stride(RP, W1, P);
+  long long* zoff = reinterpret_cast<long long*>(smraw);
+  int* yoff = reinterpret_cast<int*>(zoff + 64);
+  int* bofs = yoff + 32;
+  T* red = reinterpret_cast<T*>(bofs + kTileBatch);     // [8] warp sums of |q|
+  T* wgt = reinterpret_cast<T*>(smraw + kTileHeader);  // [j][axis][k], q folded into x
+  A* st = reinterpret_cast<A*>(wgt + kTileBatch * 3 * kMaxWin);
   const int tz = tile / (g.nt[0] * g.nt[1]);
   const int ty = (tile / g.nt[0]) % g.nt[1];
   const int tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo, oz = tz * g.T[2] - g.pad_lo;
-  // rows of the padded tile, one warp per row, wrapped x index per lane
-  int xw[2];
-  for (int k = 0; k < 2; ++k) xw[k] = (lane + 32 * k < W0) ? pmod(ox + lane + 32 * k, g.I[0]) : 0;
-  for (int row = warp; row < W1 * W2; row += nw) {
-    const int ly = row % W1, lz = row / W1;
-    T* gp = grid + ((size_t)pmod(oz + lz, g.I[2]) * g.I[1] + pmod(oy + ly, g.I[1])) * g.pitch;
-    for (int k = 0; k < 2; ++k) {
-      const int lx = lane + 32 * k;
-      if (lx < W0) {
-        const T v = st[row * W0 + lx];
-        if (v != T(0)) atomicAdd(gp + xw[k], v);
+  for (int i = threadIdx.x; i < W2 * PS; i += blockDim.x) st[i] = A(0);
+  tile_tables(g, oy, oz, W2, false, yoff, zoff);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // scale of the fixed-point tile
+  T qa = 0;
+  for (int i = b + threadIdx.x; i < e; i += blockDim.x) qa += fabs(rec[i].q);
+  qa = warp_sum(qa);
+  if (lane == 0) red[warp] = qa;
+  __syncthreads();
+  T qsum = 0;
+  for (int k = 0; k < nw; ++k) qsum += red[k];
+  int ex = 0;
+  frexp(qsum > T(0) ? qsum : T(1), &ex);  // qsum < 2^ex
+  const T S = (T)ldexp(1.0, FixAcc<T>::bits - ex), iS = (T)ldexp(1.0, ex - FixAcc<T>::bits);
+  constexpr int NIT = PW > 0 ? (PW * PW + 31) / 32 : (kMaxWin * kMaxWin) / 32;
+  constexpr int PR = PW > 0 ? PW : kMaxWin;
+  int roff[NIT], rdy[NIT], rdz[NIT];  // this lane's (dz, dy) rows, roff -1: none
+#pragma unroll
+  for (int it = 0; it < NIT; ++it) {
+    const int s2 = lane + 32 * it;
+    const int dz = s2 / P, dy = s2 - dz * P;
+    const bool ok = s2 < PP;
+    roff[it] = ok ? dz * PS + dy * RP : -1;
+    rdy[it] = ok ? dy : 0;
+    rdz[it] = ok ? dz : 0;
+  }
+  for (int p0 = b; p0 < e; p0 += kTileBatch) {
+    const int nb = min(kTileBatch, e - p0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * 3 * kMaxWin; idx += blockDim.x) {
+      const int j = idx / (3 * kMaxWin);
+      const int r = idx - j * 3 * kMaxWin;
+      const int ax = r / kMaxWin, k = r - ax * kMaxWin;
+      if (k < P) {
+        const P4<T> a = rec[p0 + j];
+        const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
+        const int g0 = (int)dceil(c - w.half);
+        T v, dv;
+        win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
+        wgt[idx] = ax == 0 ? v * a.q : v;
+        if (r == 0) {
+          const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
+          bofs[j] = (gz0 + g.pad_lo) * PS + (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
+        }
       }
     }
+    __syncthreads();
+    for (int j = warp; j < nb; j += nw) {
+      const T* wj = wgt + j * 3 * kMaxWin;
+      T rwx[PR];
+#pragma unroll
+      for (int dx = 0; dx < PR; ++dx) rwx[dx] = dx < P ? wj[dx] : T(0);
+      A* bj = st + bofs[j];
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (roff[it] >= 0) {
+          const T c = wj[kMaxWin + rdy[it]] * wj[2 * kMaxWin + rdz[it]] * S;
+          A* rp = bj + roff[it];
+#pragma unroll
+          for (int dx = 0; dx < PR; ++dx)
+            if (dx < P) fix_add(rp + dx, FixAcc<T>::cvt(c * rwx[dx]));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int xw = lane < W0 ? pmod(ox + lane, g.I[0]) : 0;
+  int ly = warp, lz = 0;
+  while (ly >= W1) { ly -= W1; ++lz; }
+  for (int row = warp; row < W1 * W2; row += nw) {
+    if (lane < W0) {
+      const A v = st[lz * PS + ly * RP + lane];
+      if (v != A(0)) atomicAdd(grid + zoff[lz] + yoff[ly] + xw, (T)v * iS);
+    }
+    ly += nw;
+    while (ly >= W1) { ly -= W1; ++lz; }
   }
 }
 
 // Gathering, Eq. (3.10): Phi^mid_i = sum_g u[g] W(r_i - r_g) and its gradient.
+// The padded tile is loaded into shared memory once; a warp per particle,
+// lanes over the (dz, dy) rows of its window, each lane summing along x.
 template <typename T, int PW>
-__global__ void __launch_bounds__(256) k_mid_gather(TileGeom g, WinT<T> w,
-                                                    const P4<T>* __restrict__ rec,
-                                                    const int* __restrict__ start,
-                                                    const int* __restrict__ perm,
-                                                    const T* __restrict__ grid, double3 invh,
-                                                    double* __restrict__ phi_out,
-                                                    double* __restrict__ grad_out) {
+__global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T> w,
+                                                             const P4<T>* __restrict__ rec,
+                                                             const int* __restrict__ start,
+                                                             const int* __restrict__ perm,
+                                                             const T* __restrict__ grid, double3 invh,
+                                                             double* __restrict__ phi_out,
+                                                             double* __restrict__ grad_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int tile = blockIdx.x;
-  const int b = start[tile], e = start[tile + 1];
-  const int chunk = blockIdx.y;
-  if (b + chunk >= e) return;
+  int b = start[tile], e = start[tile + 1];
+  if (!chunk_range(b, e, g.chunks)) return;
   const int W0 = g.W[0], W1 = g.W[1], W2 = g.W[2];
   const int P = PW > 0 ? PW : w.P;
   const int PP = P * P;
-  MidSmem<T> sm = mid_smem_layout<T>(smraw, g, P);
-  T* st = sm.tile;
+  const int RP = gather_row_pitch(W0);
+  const int PS = gather_plane_stride(RP, W1, P);
+  long long* zoff = reinterpret_cast<long long*>(smraw);
+  int* yoff = reinterpret_cast<int*>(zoff + 64);
+  int* bofs = yoff + 32;
+  T* wgt = reinterpret_cast<T*>(smraw + kTileHeader);  // [j][6][k]: w, w' for x, y, z
+  T* st = wgt + kTileBatch * 6 * kMaxWin;
   const int tz = tile / (g.nt[0] * g.nt[1]);
   const int ty = (tile / g.nt[0]) % g.nt[1];
   const int tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo, oz = tz * g.T[2] - g.pad_lo;
-  const int nw = blockDim.x >> 5;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int xw[2];
-  for (int k = 0; k < 2; ++k) xw[k] = (lane + 32 * k < W0) ? pmod(ox + lane + 32 * k, g.I[0]) : 0;
-  for (int row = warp; row < W1 * W2; row += nw) {
-    const int ly = row % W1, lz = row / W1;
-    const T* gp = grid + ((size_t)pmod(oz + lz, g.I[2]) * g.I[1] + pmod(oy + ly, g.I[1])) * g.pitch;
-    for (int k = 0; k < 2; ++k) {
-      const int lx = lane + 32 * k;
-      if (lx < W0) st[row * W0 + lx] = gp[xw[k]];
-    }
-  }
-  fill_rows(sm.rowoff, sm.rdy, sm.rdz, P, W0, W1);
+  tile_tables(g, oy, oz, W2, false, yoff, zoff);
   __syncthreads();
-  T* ws = sm.ws + warp * 6 * kMaxWin;
-  T *wsx = ws, *wsy = ws + kMaxWin, *wsz = ws + 2 * kMaxWin;
-  T *dsx = ws + 3 * kMaxWin, *dsy = ws + 4 * kMaxWin, *dsz = ws + 5 * kMaxWin;
-  for (int pi = b + chunk + warp * g.chunks; pi < e; pi += nw * g.chunks) {
-    const P4<T> a = rec[pi];
-    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half),
-              gz0 = (int)dceil(a.z - w.half);
-    if (lane < P) {
-      T v, dv;
-      // d/dt of phi((g - t)/half) = -phi'/half
-      win_eval(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
-      wsx[lane] = v;
-      dsx[lane] = -dv * w.inv_half;
-      win_eval(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
-      wsy[lane] = v;
-      dsy[lane] = -dv * w.inv_half;
-      win_eval(w, ((T)(gz0 + lane) - a.z) * w.inv_half, v, dv);
-      wsz[lane] = v;
-      dsz[lane] = -dv * w.inv_half;
-    }
-    __syncwarp();
-    const T* base = st + ((gz0 + g.pad_lo) * W1 + (gy0 + g.pad_lo)) * W0 + gx0 + g.pad_lo;
-    constexpr int PR = PW > 0 ? PW : kMaxWin;
-    T rwx[PR], rdx[PR];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int xw = lane < W0 ? pmod(ox + lane, g.I[0]) : 0;
+  tile_rows<T, true>(const_cast<T*>(grid), st, W0, W1, W2, RP, PS, yoff, zoff, xw);
+  constexpr int NIT = PW > 0 ? (PW * PW + 31) / 32 : (kMaxWin * kMaxWin) / 32;
+  constexpr int PR = PW > 0 ? PW : kMaxWin;
+  int roff[NIT], rdy[NIT], rdz[NIT];  // this lane's (dz, dy) rows
 #pragma unroll
-    for (int dx = 0; dx < PR; ++dx) {
-      rwx[dx] = dx < P ? wsx[dx] : T(0);
-      rdx[dx] = dx < P ? dsx[dx] : T(0);
-    }
-    T f = 0, fx = 0, fy = 0, fz = 0;
-    for (int row = lane; row < PP; row += 32) {
-      const int dy = sm.rdy[row], dz = sm.rdz[row];
-      const T* rp = base + sm.rowoff[row];
-      T sx = 0, sd = 0;
-#pragma unroll
-      for (int dx = 0; dx < PR; ++dx) {
-        if (dx < P) {
-          const T u = rp[dx];
-          sx += u * rwx[dx];
-          sd += u * rdx[dx];
+  for (int it = 0; it < NIT; ++it) {
+    const int s2 = lane + 32 * it;
+    const int dz = s2 / P, dy = s2 - dz * P;
+    const bool ok = s2 < PP;
+    roff[it] = ok ? dz * PS + dy * RP : -1;
+    rdy[it] = ok ? dy : 0;
+    rdz[it] = ok ? dz : 0;
+  }
+  for (int p0 = b; p0 < e; p0 += kTileBatch) {
+    const int nb = min(kTileBatch, e - p0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * 3 * kMaxWin; idx += blockDim.x) {
+      const int j = idx / (3 * kMaxWin);
+      const int r = idx - j * 3 * kMaxWin;
+      const int ax = r / kMaxWin, k = r - ax * kMaxWin;
+      if (k < P) {
+        const P4<T> a = rec[p0 + j];
+        const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
+        const int g0 = (int)dceil(c - w.half);
+        T v, dv;
+        // d/dt of phi((g - t)/half) = -phi'/half
+        win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
+        T* wj = wgt + (j * 6 + 2 * ax) * kMaxWin;
+        wj[k] = v;
+        wj[kMaxWin + k] = -dv * w.inv_half;
+        if (r == 0) {
+          const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
+          bofs[j] = (gz0 + g.pad_lo) * PS + (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
         }
       }
-      const T wy = wsy[dy], wz = wsz[dz];
-      const T wyz = wy * wz;
-      f += wyz * sx;
-      fx += wyz * sd;
-      fy += dsy[dy] * wz * sx;
-      fz += wy * dsz[dz] * sx;
     }
-    f = warp_sum(f);
-    fx = warp_sum(fx);
-    fy = warp_sum(fy);
-    fz = warp_sum(fz);
-    if (lane == 0) {
-      const int o = perm[pi];
-      phi_out[o] = (double)f;
-      grad_out[3 * o] = (double)fx * invh.x;
-      grad_out[3 * o + 1] = (double)fy * invh.y;
-      grad_out[3 * o + 2] = (double)fz * invh.z;
+    __syncthreads();
+    for (int j = warp; j < nb; j += nw) {
+      const T* wj = wgt + j * 6 * kMaxWin;
+      const T *wx = wj, *dwx = wj + kMaxWin, *wy = wj + 2 * kMaxWin, *dwy = wj + 3 * kMaxWin;
+      const T *wz = wj + 4 * kMaxWin, *dwz = wj + 5 * kMaxWin;
+      T rwx[PR], rdx[PR];
+#pragma unroll
+      for (int dx = 0; dx < PR; ++dx) {
+        rwx[dx] = dx < P ? wx[dx] : T(0);
+        rdx[dx] = dx < P ? dwx[dx] : T(0);
+      }
+      const T* bj = st + bofs[j];
+      T f = 0, fx = 0, fy = 0, fz = 0;
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (roff[it] >= 0) {
+          const T* rp = bj + roff[it];
+          T sx = 0, sd = 0;
+#pragma unroll
+          for (int dx = 0; dx < PR; ++dx) {
+            if (dx < P) {
+              const T u = rp[dx];
+              sx += u * rwx[dx];
+              sd += u * rdx[dx];
+            }
+          }
+          const T wyv = wy[rdy[it]], wzv = wz[rdz[it]];
+          const T wyz = wyv * wzv;
+          f += wyz * sx;
+          fx += wyz * sd;
+          fy += dwy[rdy[it]] * wzv * sx;
+          fz += wyv * dwz[rdz[it]] * sx;
+        }
+      }
+      f = warp_sum(f);
+      fx = warp_sum(fx);
+      fy = warp_sum(fy);
+      fz = warp_sum(fz);
+      if (lane == 0) {
+        const int o = perm[p0 + j];
+        phi_out[o] = (double)f;
+        grad_out[3 * o] = (double)fx * invh.x;
+        grad_out[3 * o + 1] = (double)fy * invh.y;
+        grad_out[3 * o + 2] = (double)fz * invh.z;
+      }
     }
-    __syncwarp();
   }
 }
 
@@ -896,22 +990,14 @@ __global__ void __launch_bounds__(256) k_long_spread(TileGeom g, WinT<T> w, int 
     }
     __syncwarp();
   }
-  __syncthreads();
+  __shared__ long long zoff[kMaxCheb];
+  __shared__ int yoff[32];
   const int ty = tile / g.nt[0], tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
-  int xw[2];
-  for (int k = 0; k < 2; ++k) xw[k] = (lane + 32 * k < W0) ? pmod(ox + lane + 32 * k, g.I[0]) : 0;
-  for (int row = warp; row < P * W1; row += nw) {
-    const int n = row / W1, ly = row - n * W1;
-    T* gp = planes + ((size_t)n * g.I[1] + pmod(oy + ly, g.I[1])) * g.pitch;
-    for (int k = 0; k < 2; ++k) {
-      const int lx = lane + 32 * k;
-      if (lx < W0) {
-        const T v = st[n * ps + ly * W0 + lx];
-        if (v != T(0)) atomicAdd(gp + xw[k], v);
-      }
-    }
-  }
+  tile_tables(g, oy, 0, P, true, yoff, zoff);
+  __syncthreads();
+  const int xw = lane < W0 ? pmod(ox + lane, g.I[0]) : 0;
+  tile_rows<T, false>(planes, st, W0, W1, P, W0, ps, yoff, zoff, xw);
 }
 
 // Small long-range grids (cubic boxes: I_long of order 16): each CTA takes a
@@ -1021,101 +1107,110 @@ __global__ void k_long_contract(const T* __restrict__ A, T* __restrict__ B, cons
 }
 
 // Gathering, Eq. (3.19) discretised: Phi_i = sum_n T_n(x_i) sum_g W2 u_n[g].
+// The padded tile of all P proxy planes is loaded into shared memory; window
+// weights and Chebyshev values are staged per batch of particles; a warp per
+// particle, lanes over the (n, dy) rows of its window, each summing along x.
 template <typename T, int PW>
-__global__ void __launch_bounds__(256) k_long_gather(TileGeom g, WinT<T> w, int P,
-                                                     const P4<T>* __restrict__ rec,
-                                                     const int* __restrict__ start,
-                                                     const int* __restrict__ perm,
-                                                     const T* __restrict__ planes, double3 sc,
-                                                     double* __restrict__ phi_out,
-                                                     double* __restrict__ grad_out) {
+__global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T> w, int P,
+                                                              const P4<T>* __restrict__ rec,
+                                                              const int* __restrict__ start,
+                                                              const int* __restrict__ perm,
+                                                              const T* __restrict__ planes, double3 sc,
+                                                              double* __restrict__ phi_out,
+                                                              double* __restrict__ grad_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int tile = blockIdx.x;
-  const int b = start[tile], e = start[tile + 1];
-  const int chunk = blockIdx.y;
-  if (b + chunk >= e) return;
+  int b = start[tile], e = start[tile + 1];
+  if (!chunk_range(b, e, g.chunks)) return;
   const int W0 = g.W[0], W1 = g.W[1];
-  const int ps = W0 * W1 + 1;
-  const int Wn = P * ps;
-  T* st = reinterpret_cast<T*>(smraw);
+  const int Pw = PW > 0 ? PW : w.P;
+  const int RP = gather_row_pitch(W0);
+  const int PS = gather_plane_stride(RP, W1, Pw);
+  const int nrow = P * Pw;
+  long long* zoff = reinterpret_cast<long long*>(smraw);
+  int* yoff = reinterpret_cast<int*>(zoff + 64);
+  int* bofs = yoff + 32;
+  // per particle: wx, w'x, wy, w'y [kMaxWin each], T_n, T'_n [kMaxCheb each]
+  constexpr int kRec = 4 * kMaxWin + 2 * kMaxCheb;
+  T* wgt = reinterpret_cast<T*>(smraw + kTileHeader);
+  T* st = wgt + kTileBatch * kRec;
   const int ty = tile / g.nt[0], tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
-  const int nw = blockDim.x >> 5;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int xw[2];
-  for (int k = 0; k < 2; ++k) xw[k] = (lane + 32 * k < W0) ? pmod(ox + lane + 32 * k, g.I[0]) : 0;
-  for (int row = warp; row < P * W1; row += nw) {
-    const int n = row / W1, ly = row - n * W1;
-    const T* gp = planes + ((size_t)n * g.I[1] + pmod(oy + ly, g.I[1])) * g.pitch;
-    for (int k = 0; k < 2; ++k) {
-      const int lx = lane + 32 * k;
-      if (lx < W0) st[n * ps + ly * W0 + lx] = gp[xw[k]];
-    }
-  }
+  tile_tables(g, oy, 0, P, true, yoff, zoff);
   __syncthreads();
-  T* ws = st + Wn + warp * (4 * kMaxWin + 2 * kMaxCheb);
-  T *wsx = ws, *wsy = ws + kMaxWin, *dsx = ws + 2 * kMaxWin, *dsy = ws + 3 * kMaxWin;
-  T *tnv = ws + 4 * kMaxWin, *dtn = tnv + kMaxCheb;
-  const int Pw = PW > 0 ? PW : w.P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int xw = lane < W0 ? pmod(ox + lane, g.I[0]) : 0;
+  tile_rows<T, true>(const_cast<T*>(planes), st, W0, W1, P, RP, PS, yoff, zoff, xw);
   constexpr int PR = PW > 0 ? PW : kMaxWin;
-  for (int pi = b + chunk + warp * g.chunks; pi < e; pi += nw * g.chunks) {
-    const P4<T> a = rec[pi];
-    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half);
-    if (lane < Pw) {
-      T v, dv;
-      win_eval(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
-      wsx[lane] = v;
-      dsx[lane] = -dv * w.inv_half;
-      win_eval(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
-      wsy[lane] = v;
-      dsy[lane] = -dv * w.inv_half;
+  for (int p0 = b; p0 < e; p0 += kTileBatch) {
+    const int nb = min(kTileBatch, e - p0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * 2 * kMaxWin; idx += blockDim.x) {
+      const int j = idx / (2 * kMaxWin);
+      const int r = idx - j * 2 * kMaxWin;
+      const int ax = r / kMaxWin, k = r - ax * kMaxWin;
+      if (k < Pw) {
+        const P4<T> a = rec[p0 + j];
+        const T c = ax == 0 ? a.x : a.y;
+        const int g0 = (int)dceil(c - w.half);
+        T v, dv;
+        win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
+        T* wj = wgt + j * kRec + 2 * ax * kMaxWin;
+        wj[k] = v;
+        wj[kMaxWin + k] = -dv * w.inv_half;
+        if (r == 0) {
+          const int gy0 = (int)dceil(a.y - w.half);
+          bofs[j] = (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
+        }
+      }
     }
-    if (lane == 0) cheb_all_d(a.z, P, tnv, dtn);
-    __syncwarp();
-    const T* base = st + (gy0 + g.pad_lo) * W0 + gx0 + g.pad_lo;
-    T rwx[PR], rdx[PR];
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      T* wj = wgt + j * kRec + 4 * kMaxWin;
+      cheb_all_d(rec[p0 + j].z, P, wj, wj + kMaxCheb);
+    }
+    __syncthreads();
+    for (int j = warp; j < nb; j += nw) {
+      const T* wj = wgt + j * kRec;
+      const T *wy = wj + 2 * kMaxWin, *dwy = wj + 3 * kMaxWin;
+      const T *tn = wj + 4 * kMaxWin, *dtn = tn + kMaxCheb;
+      T rwx[PR], rdx[PR];
 #pragma unroll
-    for (int dx = 0; dx < PR; ++dx) {
-      rwx[dx] = dx < Pw ? wsx[dx] : T(0);
-      rdx[dx] = dx < Pw ? dsx[dx] : T(0);
-    }
-    T f = 0, fx = 0, fy = 0, fz = 0;
-    for (int n = lane; n < P; n += 32) {
-      const T* pl = base + n * ps;
-      T s = 0, sx = 0, sy = 0;
-      for (int dy = 0; dy < Pw; ++dy) {
-        const T* rp = pl + dy * W0;
-        T rs = 0, rd = 0;
+      for (int dx = 0; dx < PR; ++dx) {
+        rwx[dx] = dx < Pw ? wj[dx] : T(0);
+        rdx[dx] = dx < Pw ? wj[kMaxWin + dx] : T(0);
+      }
+      const T* bj = st + bofs[j];
+      T f = 0, fx = 0, fy = 0, fz = 0;
+      for (int rr = lane; rr < nrow; rr += 32) {
+        const int n = rr / Pw, dy = rr - n * Pw;
+        const T* rp = bj + n * PS + dy * RP;
+        T sx = 0, sd = 0;
 #pragma unroll
         for (int dx = 0; dx < PR; ++dx) {
           if (dx < Pw) {
             const T u = rp[dx];
-            rs += u * rwx[dx];
-            rd += u * rdx[dx];
+            sx += u * rwx[dx];
+            sd += u * rdx[dx];
           }
         }
-        s += wsy[dy] * rs;
-        sx += wsy[dy] * rd;
-        sy += dsy[dy] * rs;
+        const T ty_ = tn[n] * wy[dy];
+        f += ty_ * sx;
+        fx += ty_ * sd;
+        fy += tn[n] * dwy[dy] * sx;
+        fz += dtn[n] * wy[dy] * sx;
       }
-      const T tn = tnv[n], dn = dtn[n];
-      f += tn * s;
-      fx += tn * sx;
-      fy += tn * sy;
-      fz += dn * s;
+      f = warp_sum(f);
+      fx = warp_sum(fx);
+      fy = warp_sum(fy);
+      fz = warp_sum(fz);
+      if (lane == 0) {
+        const int o = perm[p0 + j];
+        phi_out[o] = (double)f;
+        grad_out[3 * o] = (double)fx * sc.x;
+        grad_out[3 * o + 1] = (double)fy * sc.y;
+        grad_out[3 * o + 2] = (double)fz * sc.z;
+      }
     }
-    f = warp_sum(f);
-    fx = warp_sum(fx);
-    fy = warp_sum(fy);
-    fz = warp_sum(fz);
-    if (lane == 0) {
-      const int o = perm[pi];
-      phi_out[o] = (double)f;
-      grad_out[3 * o] = (double)fx * sc.x;
-      grad_out[3 * o + 1] = (double)fy * sc.y;
-      grad_out[3 * o + 2] = (double)fz * sc.z;
-    }
-    __syncwarp();
   }
 }
 
@@ -1285,27 +1380,45 @@ __global__ void k_energy(const double* __restrict__ part, int nblk, double* __re
     }                                                                      \
   } while (0)
 
+// Opt a kernel in to the largest dynamic shared memory its static shared
+// memory leaves free.
+template <typename K>
+static cudaError_t allow_smem(K* kernel) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kMaxDynSmem - (int)a.sharedSizeBytes);
+}
+
 template <typename T, int PW>
 static cudaError_t allow_pw() {
-  cudaError_t e = cudaFuncSetAttribute(k_mid_spread<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mid_gather<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_long_spread<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_long_gather<T, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  cudaError_t e = allow_smem(k_mid_spread<T, PW>);
+  if (e == cudaSuccess) e = allow_smem(k_mid_gather<T, PW>);
+  if (e == cudaSuccess) e = allow_smem(k_long_spread<T, PW>);
+  if (e == cudaSuccess) e = allow_smem(k_long_gather<T, PW>);
   return e;
 }
 
 static size_t mid_smem(const sog_plan* p, size_t es, bool gather) {
   const TileGeom& g = p->gm;
-  return (size_t)g.W[0] * g.W[1] * g.W[2] * es + kMaxWin * kMaxWin * (sizeof(int) + 2) +
-         (size_t)8 * (gather ? 6 : 3) * kMaxWin * es;
+  const int P = p->wm.P;
+  const int rp = gather_row_pitch(g.W[0]);
+  const size_t tile = (size_t)g.W[2] * gather_plane_stride(rp, g.W[1], P);
+  if (gather) return kTileHeader + ((size_t)kTileBatch * 6 * kMaxWin + tile) * es;
+  // fixed-point tile: int32 for FP32, int64 for FP64 (same size as T)
+  return kTileHeader + ((size_t)kTileBatch * 3 * kMaxWin + tile) * es;
 }
 static size_t long_smem(const sog_plan* p, size_t es, bool gather) {
   const TileGeom& g = p->gl;
-  const size_t pl = (size_t)p->prm.P_cheb * (g.W[0] * g.W[1] + 1);
-  return (pl + 8 * (gather ? 4 * kMaxWin + 2 * kMaxCheb : 2 * kMaxWin + kMaxCheb)) * es;
+  const int P = p->prm.P_cheb;
+  if (gather) {
+    const int rp = gather_row_pitch(g.W[0]);
+    return kTileHeader + ((size_t)kTileBatch * (4 * kMaxWin + 2 * kMaxCheb) +
+                          (size_t)P * gather_plane_stride(rp, g.W[1], p->wl.P)) * es;
+  }
+  const size_t pl = (size_t)P * (g.W[0] * g.W[1] + 1);
+  return (pl + 8 * (2 * kMaxWin + kMaxCheb)) * es;
 }
 
 #define SOG_CK(x)                      \
