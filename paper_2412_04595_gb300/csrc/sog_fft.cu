@@ -2,17 +2,25 @@
 //
 // Algorithm 1 needs a forward 3D FFT, the scaling of Eq. (3.8) and a
 // backward 3D FFT on the real grid; Algorithm 2 needs forward and backward 2D
-// FFTs of every Chebyshev proxy plane with a z-contraction in between.  Both
-// are done as passes over lines:
-//   x pass:  real rows, two rows packed into one complex line (R2C / C2R),
-//            half spectrum written in place (row pitch Ix + 2 reals);
-//   y pass:  complex lines along y;
-//   z pass:  forward FFT along z, multiplication by the precomputed scaling
-//            factor, backward FFT along z, in one kernel (Algorithm 1 steps
-//            2-4 for the z direction without a round trip through memory).
-// Each CTA holds a batch of lines in shared memory and runs self-sorting
-// Stockham stages of radix 2, 3, 4, 5, 7 or 8.  Transforms are unnormalised;
-// the 1/n factors live in the scaling tables.
+// FFTs of every Chebyshev proxy plane with a z-contraction in between.
+//
+// Engine: a CTA of kFftThreads threads holds a set of lines in shared memory
+// and transforms them in place with self-sorting (Stockham) stages of radix
+// 2, 3, 4, 5, 7 or 8.  In a stage every thread reads the inputs of its
+// butterflies into registers, applies twiddles and the butterfly, waits at a
+// barrier and writes the outputs, so one buffer suffices; a thread holds at
+// most kFftCap complex values.  Index arithmetic uses exact float
+// reciprocals instead of integer division.  Transforms are unnormalised; the
+// 1/n factors live in the scaling tables.
+//
+// Kernels:
+//   k_fft_plane  one CTA per xy plane: real rows packed in pairs as complex
+//                lines, x FFT, split into half spectra, y FFT (forward), or
+//                the reverse; used when a plane fits one CTA.
+//   k_fft_rows   x pass alone (pairs of real rows), for planes that do not fit.
+//   k_fft_cols   complex lines with a stride (y pass), or the z pass of
+//                Algorithm 1: forward FFT, multiplication by the scaling
+//                factor, backward FFT without a round trip through memory.
 #include "sog_internal.h"
 
 namespace sogk {
@@ -20,6 +28,11 @@ namespace sogk {
 template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; };
 template <> struct C2<double> { using t = double2; };
+
+constexpr int kFftThreads = 512;
+template <typename T> struct FftCap;
+template <> struct FftCap<float> { static constexpr int v = 16; };
+template <> struct FftCap<double> { static constexpr int v = 8; };
 
 template <typename T2>
 __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return T2{a.x + b.x, a.y + b.y}; }
@@ -35,271 +48,482 @@ __device__ __forceinline__ T2 rot(T2 a, bool inv) {
   return inv ? T2{-a.y, a.x} : T2{a.y, -a.x};
 }
 
-// One Stockham stage of radix R on nl lines of length n stored with line
-// stride ls in a (input) and b (output).  L = product of earlier radices.
+// floor(a / b) for 0 <= a < 2^22 from rb = 1/b rounded to float: the
+// fractional part of (a + 1/2) / b is at least 1/(2b) away from an integer
+// and the relative error of the product is below 2^-23.
+__device__ __forceinline__ int fdiv(int a, float rb) { return (int)(((float)a + 0.5f) * rb); }
+
+// A set of nl lines of length n in shared memory: element i of line l at
+// l * ls + i * es.  line_fast: consecutive threads take consecutive lines
+// (lines adjacent in memory), else consecutive elements of one line.
+struct LineSet {
+  int n, nl, ls, es;
+  bool line_fast;
+};
+
 template <typename T2, int R>
-__device__ void stage(const T2* __restrict__ a, T2* __restrict__ b, int n, int L, int nl,
-                      int ls, const T2* __restrict__ tw, bool inv) {
-  const int nb = n / R;
-  const int m = nb / L;
-  const int tot = nl * nb;
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int line = idx / nb;
-    const int t = idx - line * nb;
-    const int j = t % L;
-    const int k = t / L;
-    const T2* al = a + line * ls;
-    T2* bl = b + line * ls;
-    T2 x[R];
-#pragma unroll
-    for (int p = 0; p < R; ++p) x[p] = al[(k + m * p) * L + j];
-#pragma unroll
-    for (int p = 1; p < R; ++p) {
-      T2 w = tw[j * p * m];
-      if (inv) w.y = -w.y;
-      x[p] = cmul(x[p], w);
-    }
+__device__ __forceinline__ void dft(T2* x, bool inv, const T2* tw, int n) {
+  if (R == 2) {
+    const T2 a = x[0], b = x[1];
+    x[0] = cadd(a, b);
+    x[1] = csub(a, b);
+  } else if (R == 4) {
+    const T2 s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
+    const T2 s13 = cadd(x[1], x[3]), d13 = rot(csub(x[1], x[3]), inv);
+    x[0] = cadd(s02, s13);
+    x[2] = csub(s02, s13);
+    x[1] = cadd(d02, d13);
+    x[3] = csub(d02, d13);
+  } else if (R == 8) {
+    // two DFT4 on even and odd samples, odd part rotated by w8^k
+    T2 e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
+    dft<T2, 4>(e, inv, tw, n);
+    dft<T2, 4>(o, inv, tw, n);
+    using T = decltype(e[0].x);
+    const T h = (T)0.70710678118654752440;
+    // w8^1 = (1 - i)/sqrt2 forward, (1 + i)/sqrt2 inverse; w8^2 = -i / +i
+    const T2 o1 = inv ? T2{h * (o[1].x - o[1].y), h * (o[1].x + o[1].y)}
+                      : T2{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};
+    const T2 o2 = rot(o[2], inv);
+    const T2 o3 = inv ? T2{-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y)}
+                      : T2{h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};
+    x[0] = cadd(e[0], o[0]);
+    x[4] = csub(e[0], o[0]);
+    x[1] = cadd(e[1], o1);
+    x[5] = csub(e[1], o1);
+    x[2] = cadd(e[2], o2);
+    x[6] = csub(e[2], o2);
+    x[3] = cadd(e[3], o3);
+    x[7] = csub(e[3], o3);
+  } else {
+    // odd radix: y_q = sum_p x_p w^(qp), w = exp(-+2 pi i / R) from the
+    // length-n table (entry (qp mod R) n / R)
+    const int step = n / R;
     T2 y[R];
-    if (R == 2) {
-      y[0] = cadd(x[0], x[1]);
-      y[1] = csub(x[0], x[1]);
-    } else if (R == 4) {
-      const T2 s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
-      const T2 s13 = cadd(x[1], x[3]), d13 = rot(csub(x[1], x[3]), inv);
-      y[0] = cadd(s02, s13);
-      y[2] = csub(s02, s13);
-      y[1] = cadd(d02, d13);
-      y[3] = csub(d02, d13);
-    } else {
-      const int step = n / R;
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        T2 s = x[0];
+    for (int q = 0; q < R; ++q) {
+      T2 s = x[0];
 #pragma unroll
-        for (int p = 1; p < R; ++p) {
-          T2 w = tw[((q * p) % R) * step];
-          if (inv) w.y = -w.y;
-          s = cadd(s, cmul(x[p], w));
-        }
-        y[q] = s;
+      for (int p = 1; p < R; ++p) {
+        T2 w = tw[((q * p) % R) * step];
+        if (inv) w.y = -w.y;
+        s = cadd(s, cmul(x[p], w));
       }
+      y[q] = s;
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q) bl[k * L * R + j + L * q] = y[q];
+    for (int q = 0; q < R; ++q) x[q] = y[q];
   }
 }
 
-// Runs all stages; returns the buffer holding the result (a or b).
-template <typename T2>
-__device__ T2* run_fft(T2* a, T2* b, const FftLen& f, int nl, int ls, const T2* tw, bool inv) {
+// One in-place Stockham stage of radix R; L = product of earlier radices.
+template <typename T2, int CAP, int R>
+__device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T2* tw, bool inv) {
+  constexpr int KB = CAP / R;
+  const int nb = s.n / R, m = nb / L;
+  const int tot = s.nl * nb;
+  const float rq = s.line_fast ? 1.f / (float)s.nl : 1.f / (float)nb;
+  const float rL = 1.f / (float)L;
+  T2 x[KB][R];
+  int wb[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int id = threadIdx.x + k * kFftThreads;
+    wb[k] = -1;
+    if (id < tot) {
+      int line, t;
+      if (s.line_fast) {
+        t = fdiv(id, rq);
+        line = id - t * s.nl;
+      } else {
+        line = fdiv(id, rq);
+        t = id - line * nb;
+      }
+      const int kk = fdiv(t, rL), j = t - kk * L;
+      const T2* a = buf + line * s.ls + (kk * L + j) * s.es;
+      const int st = m * L * s.es;
+#pragma unroll
+      for (int p = 0; p < R; ++p) x[k][p] = a[p * st];
+#pragma unroll
+      for (int p = 1; p < R; ++p) {
+        T2 w = tw[j * p * m];
+        if (inv) w.y = -w.y;
+        x[k][p] = cmul(x[k][p], w);
+      }
+      dft<T2, R>(x[k], inv, tw, s.n);
+      wb[k] = line * s.ls + (kk * L * R + j) * s.es;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    if (wb[k] >= 0) {
+      T2* b = buf + wb[k];
+      const int st = L * s.es;
+#pragma unroll
+      for (int q = 0; q < R; ++q) b[q * st] = x[k][q];
+    }
+  }
+  __syncthreads();
+}
+
+// All stages of one length.  The factorisation orders the radices 8..8, 4,
+// 2, 3..3, 5..5, 7..7; each group is a separate straight-line block so that
+// the registers of one stage are free for the next.
+template <typename T2, int CAP>
+__device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T2* tw, bool inv) {
+  const int n8 = f.n8, n4 = f.n4, n2 = f.n2, n3 = f.n3, n5 = f.n5, n7 = f.n7;
   int L = 1;
-  for (int s = 0; s < f.nst; ++s) {
-    const int R = f.radix[s];
-    switch (R) {
-      case 2: stage<T2, 2>(a, b, f.n, L, nl, ls, tw, inv); break;
-      case 3: stage<T2, 3>(a, b, f.n, L, nl, ls, tw, inv); break;
-      case 4: stage<T2, 4>(a, b, f.n, L, nl, ls, tw, inv); break;
-      case 5: stage<T2, 5>(a, b, f.n, L, nl, ls, tw, inv); break;
-      case 7: stage<T2, 7>(a, b, f.n, L, nl, ls, tw, inv); break;
-      default: stage<T2, 8>(a, b, f.n, L, nl, ls, tw, inv); break;
+  for (int i = 0; i < n8; ++i, L *= 8) stage<T2, CAP, 8>(buf, s, L, tw, inv);
+  if (n4) { stage<T2, CAP, 4>(buf, s, L, tw, inv); L *= 4; }
+  if (n2) { stage<T2, CAP, 2>(buf, s, L, tw, inv); L *= 2; }
+  for (int i = 0; i < n3; ++i, L *= 3) stage<T2, CAP, 3>(buf, s, L, tw, inv);
+  for (int i = 0; i < n5; ++i, L *= 5) stage<T2, CAP, 5>(buf, s, L, tw, inv);
+  for (int i = 0; i < n7; ++i, L *= 7) stage<T2, CAP, 7>(buf, s, L, tw, inv);
+}
+
+// Largest nl for which nl lines of length n fit the engine.
+static int max_lines(const FftLen& f, int cap) {
+  int best = 1 << 30;
+  for (int st = 0; st < f.nst; ++st) {
+    const int R = f.radix[st];
+    best = std::min(best, kFftThreads * (cap / R) / (f.n / R));
+  }
+  return best;
+}
+
+template <typename T2>
+__device__ __forceinline__ void load_tw(T2* dst, const T2* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+// Split Z = FFT(row 2p + i row 2p+1) into the half spectra of both rows,
+// in place: Z in [p][x] (pitch Ix) -> H in [y][k] (pitch C = Ix/2 + 1).
+template <typename T2, int CAP>
+__device__ __forceinline__ void split_pairs(T2* buf, int Ix, int npairs) {
+  using T = decltype(buf[0].x);
+  const int C = Ix / 2 + 1;
+  const int tot = npairs * C;
+  const float rC = 1.f / (float)C;
+  constexpr int KB = CAP / 2;
+  T2 a[KB], b[KB];
+  int pr[KB], fq[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int id = threadIdx.x + k * kFftThreads;
+    pr[k] = -1;
+    if (id < tot) {
+      const int p = fdiv(id, rC), f = id - p * C;
+      const T2 Z = buf[p * Ix + f], Zc = buf[p * Ix + (f == 0 ? 0 : Ix - f)];
+      const T h = T(0.5);
+      a[k] = T2{h * (Z.x + Zc.x), h * (Z.y - Zc.y)};
+      b[k] = T2{h * (Z.y + Zc.y), h * (Zc.x - Z.x)};
+      pr[k] = p;
+      fq[k] = f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+    if (pr[k] >= 0) {
+      buf[(2 * pr[k]) * C + fq[k]] = a[k];
+      buf[(2 * pr[k] + 1) * C + fq[k]] = b[k];
+    }
+  __syncthreads();
+}
+
+// Inverse of split_pairs: H [y][k] -> Z [p][x] with Z = X_2p + i X_2p+1 over
+// the full length (Hermitian symmetry for k > Ix/2).
+template <typename T2, int CAP>
+__device__ __forceinline__ void join_pairs(T2* buf, int Ix, int npairs) {
+  const int C = Ix / 2 + 1, nh = Ix / 2;
+  const int tot = npairs * C;
+  const float rC = 1.f / (float)C;
+  constexpr int KB = CAP / 2;
+  T2 a[KB], b[KB];
+  int pr[KB], fq[KB];
+#pragma unroll
+  for (int k = 0; k < KB; ++k) {
+    const int id = threadIdx.x + k * kFftThreads;
+    pr[k] = -1;
+    if (id < tot) {
+      const int p = fdiv(id, rC), f = id - p * C;
+      const T2 A = buf[(2 * p) * C + f], B = buf[(2 * p + 1) * C + f];
+      a[k] = T2{A.x - B.y, A.y + B.x};
+      b[k] = T2{A.x + B.y, B.x - A.y};
+      pr[k] = p;
+      fq[k] = f;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KB; ++k)
+    if (pr[k] >= 0) {
+      buf[pr[k] * Ix + fq[k]] = a[k];
+      if (fq[k] > 0 && fq[k] < nh) buf[pr[k] * Ix + Ix - fq[k]] = b[k];
+    }
+  __syncthreads();
+}
+
+// 2D real FFT of one plane per CTA.  Plane z: Iy rows of Ix reals with pitch
+// Ix + 2 at data + z * Iy * (Ix + 2); the half spectrum [ky][kx] (C complex
+// per row) is stored over the same memory.
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, 1)
+    k_fft_plane(T* __restrict__ data, FftLen fx, FftLen fy, const typename C2<T>::t* __restrict__ twg,
+                bool inv) {
+  using T2 = typename C2<T>::t;
+  constexpr int CAP = FftCap<T>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int Ix = fx.n, Iy = fy.n, C = Ix / 2 + 1, pitch = Ix + 2;
+  const int np = Iy / 2;
+  T2* twx = reinterpret_cast<T2*>(smraw);
+  T2* twy = twx + Ix;
+  T2* buf = twy + Iy;
+  load_tw(twx, twg + fx.tw_off, Ix);
+  load_tw(twy, twg + fy.tw_off, Iy);
+  T* pl = data + (size_t)blockIdx.x * Iy * pitch;
+  T2* plc = reinterpret_cast<T2*>(pl);
+  const LineSet xs{Ix, np, Ix, 1, false};
+  const LineSet ys{Iy, C, 1, C, true};
+  if (!inv) {
+    const float rI = 1.f / (float)Ix;
+    for (int id = threadIdx.x; id < np * Ix; id += kFftThreads) {
+      const int p = fdiv(id, rI), x = id - p * Ix;
+      const T* r0 = pl + (size_t)(2 * p) * pitch + x;
+      buf[id] = T2{r0[0], r0[pitch]};
     }
     __syncthreads();
-    T2* t = a;
-    a = b;
-    b = t;
-    L *= R;
+    fft_lines<T2, CAP>(buf, xs, fx, twx, false);
+    split_pairs<T2, CAP>(buf, Ix, np);
+    fft_lines<T2, CAP>(buf, ys, fy, twy, false);
+    for (int id = threadIdx.x; id < Iy * C; id += kFftThreads) plc[id] = buf[id];
+  } else {
+    for (int id = threadIdx.x; id < Iy * C; id += kFftThreads) buf[id] = plc[id];
+    __syncthreads();
+    fft_lines<T2, CAP>(buf, ys, fy, twy, true);
+    join_pairs<T2, CAP>(buf, Ix, np);
+    fft_lines<T2, CAP>(buf, xs, fx, twx, true);
+    const float rI = 1.f / (float)Ix;
+    for (int id = threadIdx.x; id < np * Ix; id += kFftThreads) {
+      const int p = fdiv(id, rI), x = id - p * Ix;
+      T* r0 = pl + (size_t)(2 * p) * pitch + x;
+      const T2 z = buf[id];
+      r0[0] = z.x;
+      r0[pitch] = z.y;
+    }
   }
-  return a;
 }
 
-// x pass.  Rows r = 0..nrows-1 (nrows even) of n reals with pitch n + 2;
-// rows 2p and 2p+1 travel as one complex line.  Forward: real rows in,
-// half spectra (n/2 + 1 complex) out, in place.  Inverse: the reverse.
+// x pass alone: rows 2p, 2p+1 (pitch Ix + 2) of pairs p0 .. p0 + B - 1.
 template <typename T>
-__global__ void k_fft_x(T* __restrict__ data, FftLen f, const typename C2<T>::t* __restrict__ twg,
-                        int npairs, int B, bool inv) {
+__global__ void __launch_bounds__(kFftThreads, 1)
+    k_fft_rows(T* __restrict__ data, FftLen fx, const typename C2<T>::t* __restrict__ twg,
+               int npairs, int B, bool inv) {
   using T2 = typename C2<T>::t;
-  extern __shared__ unsigned char smraw[];
-  const int n = f.n;
-  const int ls = n + 1;
-  T2* a = reinterpret_cast<T2*>(smraw);
-  T2* b = a + B * ls;
+  constexpr int CAP = FftCap<T>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int Ix = fx.n, C = Ix / 2 + 1, pitch = Ix + 2;
+  T2* twx = reinterpret_cast<T2*>(smraw);
+  T2* buf = twx + Ix;
+  load_tw(twx, twg + fx.tw_off, Ix);
   const int p0 = blockIdx.x * B;
   const int nl = min(B, npairs - p0);
-  const int pitch = n + 2;
-  const T2* tw = twg + f.tw_off;
+  T* base = data + (size_t)(2 * p0) * pitch;
+  const LineSet xs{Ix, nl, Ix, 1, false};
+  const float rI = 1.f / (float)Ix, rC = 1.f / (float)C;
   if (!inv) {
-    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-      const int l = idx / n, t = idx - l * n;
-      const T* r0 = data + (size_t)(2 * (p0 + l)) * pitch;
-      a[l * ls + t] = T2{r0[t], r0[pitch + t]};
-    }
-  } else {
-    const int nh = n / 2;
-    for (int idx = threadIdx.x; idx < nl * (nh + 1); idx += blockDim.x) {
-      const int l = idx / (nh + 1), fq = idx - l * (nh + 1);
-      const T2* ra = reinterpret_cast<const T2*>(data + (size_t)(2 * (p0 + l)) * pitch);
-      const T2* rb = reinterpret_cast<const T2*>(data + (size_t)(2 * (p0 + l) + 1) * pitch);
-      const T2 A = ra[fq], Bv = rb[fq];
-      a[l * ls + fq] = T2{A.x - Bv.y, A.y + Bv.x};
-      if (fq > 0 && fq < nh) a[l * ls + n - fq] = T2{A.x + Bv.y, Bv.x - A.y};
-    }
-  }
-  __syncthreads();
-  T2* res = run_fft<T2>(a, b, f, nl, ls, tw, inv);
-  if (!inv) {
-    const int nh = n / 2;
-    for (int idx = threadIdx.x; idx < nl * (nh + 1); idx += blockDim.x) {
-      const int l = idx / (nh + 1), fq = idx - l * (nh + 1);
-      const T2 Z = res[l * ls + fq];
-      const T2 Zc = res[l * ls + (fq == 0 ? 0 : n - fq)];
-      const T h = T(0.5);
-      T2* ra = reinterpret_cast<T2*>(data + (size_t)(2 * (p0 + l)) * pitch);
-      T2* rb = reinterpret_cast<T2*>(data + (size_t)(2 * (p0 + l) + 1) * pitch);
-      ra[fq] = T2{h * (Z.x + Zc.x), h * (Z.y - Zc.y)};
-      rb[fq] = T2{h * (Z.y + Zc.y), h * (Zc.x - Z.x)};
-    }
-  } else {
-    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-      const int l = idx / n, t = idx - l * n;
-      T* r0 = data + (size_t)(2 * (p0 + l)) * pitch;
-      const T2 z = res[l * ls + t];
-      r0[t] = z.x;
-      r0[pitch + t] = z.y;
-    }
-  }
-}
-
-// Complex line pass.  Line (o, c), o < O, c < C: element i at
-// o*os + c + i*es (complex units).  A CTA takes B consecutive c of one o.
-// With mult != nullptr (z pass of Algorithm 1): forward FFT, multiply element
-// (o, c, i) by mult[(i*O + o)*C + c], backward FFT.
-template <typename T>
-__global__ void k_fft_lines(typename C2<T>::t* __restrict__ data, FftLen f,
-                            const typename C2<T>::t* __restrict__ twg, int C, int O, long os,
-                            long es, int B, bool inv, const T* __restrict__ mult) {
-  using T2 = typename C2<T>::t;
-  extern __shared__ unsigned char smraw[];
-  const int n = f.n;
-  const int ls = n + 1;
-  T2* a = reinterpret_cast<T2*>(smraw);
-  T2* b = a + B * ls;
-  const int gpo = (C + B - 1) / B;
-  const int o = blockIdx.x / gpo;
-  const int c0 = (blockIdx.x - o * gpo) * B;
-  const int nl = min(B, C - c0);
-  const T2* tw = twg + f.tw_off;
-  T2* base = data + (size_t)o * os + c0;
-  for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-    const int i = idx / nl, c = idx - i * nl;
-    a[c * ls + i] = base[(size_t)i * es + c];
-  }
-  __syncthreads();
-  T2* res = run_fft<T2>(a, b, f, nl, ls, tw, mult ? false : inv);
-  if (mult) {
-    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-      const int i = idx / nl, c = idx - i * nl;
-      const T s = mult[((size_t)i * O + o) * C + c0 + c];
-      T2 v = res[c * ls + i];
-      res[c * ls + i] = T2{v.x * s, v.y * s};
+    for (int id = threadIdx.x; id < nl * Ix; id += kFftThreads) {
+      const int p = fdiv(id, rI), x = id - p * Ix;
+      const T* r0 = base + (size_t)(2 * p) * pitch + x;
+      buf[id] = T2{r0[0], r0[pitch]};
     }
     __syncthreads();
-    T2* other = (res == a) ? b : a;
-    res = run_fft<T2>(res, other, f, nl, ls, tw, true);
-  }
-  for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-    const int i = idx / nl, c = idx - i * nl;
-    base[(size_t)i * es + c] = res[c * ls + i];
+    fft_lines<T2, CAP>(buf, xs, fx, twx, false);
+    split_pairs<T2, CAP>(buf, Ix, nl);
+    for (int id = threadIdx.x; id < 2 * nl * C; id += kFftThreads) {
+      const int y = fdiv(id, rC), f = id - y * C;
+      reinterpret_cast<T2*>(base + (size_t)y * pitch)[f] = buf[id];
+    }
+  } else {
+    for (int id = threadIdx.x; id < 2 * nl * C; id += kFftThreads) {
+      const int y = fdiv(id, rC), f = id - y * C;
+      buf[id] = reinterpret_cast<const T2*>(base + (size_t)y * pitch)[f];
+    }
+    __syncthreads();
+    join_pairs<T2, CAP>(buf, Ix, nl);
+    fft_lines<T2, CAP>(buf, xs, fx, twx, true);
+    for (int id = threadIdx.x; id < nl * Ix; id += kFftThreads) {
+      const int p = fdiv(id, rI), x = id - p * Ix;
+      T* r0 = base + (size_t)(2 * p) * pitch + x;
+      const T2 z = buf[id];
+      r0[0] = z.x;
+      r0[pitch] = z.y;
+    }
   }
 }
 
-static int lines_per_cta(int n, size_t elem, int maxB) {
-  const size_t budget = 96 * 1024;
-  int B = (int)(budget / (2 * (size_t)(n + 1) * elem));
-  if (B > maxB) B = maxB;
-  if (B < 1) B = 1;
-  return B;
+// Complex lines (o, c), o < O, c < Cn: element i at o*os + c + i*es (complex
+// units).  A CTA takes B consecutive c of one o, held as [i][c].  With mult
+// (z pass of Algorithm 1): forward FFT, multiply element (o, c, i) by
+// mult[(i*O + o)*Cn + c], backward FFT.
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, 1)
+    k_fft_cols(typename C2<T>::t* __restrict__ data, FftLen f, const typename C2<T>::t* __restrict__ twg,
+               int Cn, int O, long os, long es, int B, bool inv, const T* __restrict__ mult) {
+  using T2 = typename C2<T>::t;
+  constexpr int CAP = FftCap<T>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int n = f.n;
+  T2* tw = reinterpret_cast<T2*>(smraw);
+  T2* buf = tw + n;
+  load_tw(tw, twg + f.tw_off, n);
+  const int gpo = (Cn + B - 1) / B;
+  const int o = blockIdx.x / gpo;
+  const int c0 = (blockIdx.x - o * gpo) * B;
+  const int nl = min(B, Cn - c0);
+  T2* base = data + (size_t)o * os + c0;
+  const float rl = 1.f / (float)nl;
+  for (int id = threadIdx.x; id < nl * n; id += kFftThreads) {
+    const int i = fdiv(id, rl), c = id - i * nl;
+    buf[id] = base[(size_t)i * es + c];
+  }
+  __syncthreads();
+  const LineSet cs{n, nl, 1, nl, true};
+  fft_lines<T2, CAP>(buf, cs, f, tw, mult ? false : inv);
+  if (mult) {
+    for (int id = threadIdx.x; id < nl * n; id += kFftThreads) {
+      const int i = fdiv(id, rl), c = id - i * nl;
+      const T sc = mult[((size_t)i * O + o) * Cn + c0 + c];
+      const T2 v = buf[id];
+      buf[id] = T2{v.x * sc, v.y * sc};
+    }
+    __syncthreads();
+    fft_lines<T2, CAP>(buf, cs, f, tw, true);
+  }
+  for (int id = threadIdx.x; id < nl * n; id += kFftThreads) {
+    const int i = fdiv(id, rl), c = id - i * nl;
+    base[(size_t)i * es + c] = buf[id];
+  }
+}
+
+// True when a whole Ix x Iy plane fits one CTA of k_fft_plane.
+template <typename T>
+static bool plane_fits(const FftLen& fx, const FftLen& fy) {
+  constexpr int CAP = FftCap<T>::v;
+  const int C = fx.n / 2 + 1;
+  const size_t smem = (size_t)(fx.n + fy.n + std::max((fy.n / 2) * fx.n, fy.n * C)) *
+                      sizeof(typename C2<T>::t);
+  return max_lines(fx, CAP) >= fy.n / 2 && max_lines(fy, CAP) >= C &&
+         (fy.n / 2) * C <= kFftThreads * (CAP / 2) && smem <= (size_t)kMaxDynSmem;
 }
 
 template <typename T>
-static cudaError_t launch_x(T* data, const FftLen& f, const void* tw, int nrows, bool inv,
-                            cudaStream_t s) {
+static cudaError_t launch_plane(T* data, const FftLen& fx, const FftLen& fy, const void* tw,
+                                int nplanes, bool inv, cudaStream_t s) {
   using T2 = typename C2<T>::t;
+  const int C = fx.n / 2 + 1;
+  const size_t sm = (size_t)(fx.n + fy.n + std::max((fy.n / 2) * fx.n, fy.n * C)) * sizeof(T2);
+  k_fft_plane<T><<<nplanes, kFftThreads, sm, s>>>(data, fx, fy, reinterpret_cast<const T2*>(tw),
+                                                  inv);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_rows(T* data, const FftLen& fx, const void* tw, int nrows, bool inv,
+                               cudaStream_t s) {
+  using T2 = typename C2<T>::t;
+  constexpr int CAP = FftCap<T>::v;
   const int npairs = nrows / 2;
-  const int B = lines_per_cta(f.n, sizeof(T2), 8);
-  const size_t sm = 2 * (size_t)B * (f.n + 1) * sizeof(T2);
+  const int C = fx.n / 2 + 1;
+  int B = std::min(max_lines(fx, CAP), kFftThreads * (CAP / 2) / C);
+  B = std::max(1, std::min(B, npairs));
+  const size_t sm = (size_t)(fx.n + B * std::max(fx.n, 2 * C)) * sizeof(T2);
   const int grid = (npairs + B - 1) / B;
-  k_fft_x<T><<<grid, 256, sm, s>>>(data, f, reinterpret_cast<const T2*>(tw), npairs, B, inv);
+  k_fft_rows<T><<<grid, kFftThreads, sm, s>>>(data, fx, reinterpret_cast<const T2*>(tw), npairs,
+                                              B, inv);
   return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t launch_lines(T* data, const FftLen& f, const void* tw, int C, int O, long os,
-                                long es, bool inv, const T* mult, cudaStream_t s) {
+static cudaError_t launch_cols(T* data, const FftLen& f, const void* tw, int Cn, int O, long os,
+                               long es, bool inv, const T* mult, cudaStream_t s) {
   using T2 = typename C2<T>::t;
-  const int B = lines_per_cta(f.n, sizeof(T2), 16);
-  const size_t sm = 2 * (size_t)B * (f.n + 1) * sizeof(T2);
-  const int grid = O * ((C + B - 1) / B);
-  k_fft_lines<T><<<grid, 256, sm, s>>>(reinterpret_cast<T2*>(data), f,
-                                       reinterpret_cast<const T2*>(tw), C, O, os, es, B, inv,
-                                       mult);
+  constexpr int CAP = FftCap<T>::v;
+  int B = std::max(1, std::min(max_lines(f, CAP), Cn));
+  // balance the groups of one o
+  const int groups = (Cn + B - 1) / B;
+  B = (Cn + groups - 1) / groups;
+  const size_t sm = (size_t)(f.n + B * f.n) * sizeof(T2);
+  const int grid = O * groups;
+  k_fft_cols<T><<<grid, kFftThreads, sm, s>>>(reinterpret_cast<T2*>(data), f,
+                                              reinterpret_cast<const T2*>(tw), Cn, O, os, es, B,
+                                              inv, mult);
   return cudaGetLastError();
+}
+
+// Forward 2D FFT of nplanes planes of Ix x Iy (pitch Ix + 2), or backward.
+template <typename T>
+static cudaError_t fft_planes(T* g, const FftLen& fx, const FftLen& fy, const void* tw,
+                              int nplanes, bool inv, cudaStream_t s, int& launches) {
+  const int Ix = fx.n, Iy = fy.n, C = Ix / 2 + 1;
+  if (plane_fits<T>(fx, fy)) {
+    launches += 1;
+    return launch_plane<T>(g, fx, fy, tw, nplanes, inv, s);
+  }
+  cudaError_t e;
+  launches += 2;
+  if (!inv) {
+    if ((e = launch_rows<T>(g, fx, tw, Iy * nplanes, false, s))) return e;
+    return launch_cols<T>(g, fy, tw, C, nplanes, (long)Iy * C, C, false, nullptr, s);
+  }
+  if ((e = launch_cols<T>(g, fy, tw, C, nplanes, (long)Iy * C, C, true, nullptr, s))) return e;
+  return launch_rows<T>(g, fx, tw, Iy * nplanes, true, s);
 }
 
 // Algorithm 1 steps 2-4 on the mid grid (layout [z][y][x], pitch Ix + 2).
 template <typename T>
-cudaError_t fft_mid_forward_conv_inverse(const sog_plan* p, cudaStream_t s) {
+cudaError_t fft_mid_forward_conv_inverse(const sog_plan* p, cudaStream_t s, int& launches) {
   T* g = reinterpret_cast<T*>(p->d_grid);
   const int Ix = p->prm.I[0], Iy = p->prm.I[1], Iz = p->prm.I[2];
   const int C = Ix / 2 + 1;
   cudaError_t e;
-  if ((e = launch_x<T>(g, p->fx, p->d_tw, Iy * Iz, false, s))) return e;
-  if ((e = launch_lines<T>(g, p->fy, p->d_tw, C, Iz, (long)Iy * C, C, false, nullptr, s))) return e;
-  if ((e = launch_lines<T>(g, p->fz, p->d_tw, C, Iy, C, (long)Iy * C, false,
-                           reinterpret_cast<const T*>(p->d_mult), s)))
+  if ((e = fft_planes<T>(g, p->fx, p->fy, p->d_tw, Iz, false, s, launches))) return e;
+  if ((e = launch_cols<T>(g, p->fz, p->d_tw, C, Iy, C, (long)Iy * C, false,
+                          reinterpret_cast<const T*>(p->d_mult), s)))
     return e;
-  if ((e = launch_lines<T>(g, p->fy, p->d_tw, C, Iz, (long)Iy * C, C, true, nullptr, s))) return e;
-  return launch_x<T>(g, p->fx, p->d_tw, Iy * Iz, true, s);
+  launches += 1;
+  return fft_planes<T>(g, p->fx, p->fy, p->d_tw, Iz, true, s, launches);
 }
+template cudaError_t fft_mid_forward_conv_inverse<float>(const sog_plan*, cudaStream_t, int&);
+template cudaError_t fft_mid_forward_conv_inverse<double>(const sog_plan*, cudaStream_t, int&);
 
 // Algorithm 2 steps 2 and 4: 2D FFTs of the Chebyshev proxy planes (layout
-// [n][y][x], pitch Ix_long + 2), forward (inv = false) or backward.
+// [n][y][x], pitch Ix_long + 2), forward on d_lA (inv = false) or backward
+// on d_lB.
 template <typename T>
-static cudaError_t fft_long_half(const sog_plan* p, T* g, bool inv, cudaStream_t s) {
-  const int Ix = p->prm.I_long[0], Iy = p->prm.I_long[1], P = p->prm.P_cheb;
-  const int C = Ix / 2 + 1;
-  cudaError_t e;
-  if (!inv) {
-    if ((e = launch_x<T>(g, p->flx, p->d_tw, Iy * P, false, s))) return e;
-    return launch_lines<T>(g, p->fly, p->d_tw, C, P, (long)Iy * C, C, false, nullptr, s);
-  }
-  if ((e = launch_lines<T>(g, p->fly, p->d_tw, C, P, (long)Iy * C, C, true, nullptr, s))) return e;
-  return launch_x<T>(g, p->flx, p->d_tw, Iy * P, true, s);
+cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s, int& launches) {
+  T* g = reinterpret_cast<T*>(inv ? p->d_lB : p->d_lA);
+  return fft_planes<T>(g, p->flx, p->fly, p->d_tw, p->prm.P_cheb, inv, s, launches);
 }
+template cudaError_t fft_long_pass<float>(const sog_plan*, bool, cudaStream_t, int&);
+template cudaError_t fft_long_pass<double>(const sog_plan*, bool, cudaStream_t, int&);
 
-// Allow the FFT kernels the full dynamic shared memory of an SM (set once per
+// Allow the FFT kernels the dynamic shared memory they may need (set once per
 // process before any launch or stream capture).
 template <typename T>
 cudaError_t fft_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_fft_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_fft_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kMaxDynSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fft_lines<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_fft_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kMaxDynSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kMaxDynSmem);
   return e;
 }
 template cudaError_t fft_prepare<float>();
 template cudaError_t fft_prepare<double>();
-
-template cudaError_t fft_mid_forward_conv_inverse<float>(const sog_plan*, cudaStream_t);
-template cudaError_t fft_mid_forward_conv_inverse<double>(const sog_plan*, cudaStream_t);
-
-// Exposed to the kernel driver: forward (inv = false) on d_lA, backward on d_lB.
-template <typename T>
-cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s) {
-  return fft_long_half<T>(p, reinterpret_cast<T*>(inv ? p->d_lB : p->d_lA), inv, s);
-}
-template cudaError_t fft_long_pass<float>(const sog_plan*, bool, cudaStream_t);
-template cudaError_t fft_long_pass<double>(const sog_plan*, bool, cudaStream_t);
 
 }  // namespace sogk

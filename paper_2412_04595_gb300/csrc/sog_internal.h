@@ -22,6 +22,7 @@ struct FftLen {
   int nst;
   int radix[kMaxFftStages];
   int tw_off;
+  int n8, n4, n2, n3, n5, n7;  // stages of each radix, in this order
 };
 
 // Particle record (x, y, z, q) or (local grid coordinates, q).
@@ -54,6 +55,8 @@ struct TileGeom {
 constexpr int kTileThreads = 256;  // 8 warps; the spread's row ownership relies on it
 constexpr int kTileBatch = 32;     // particles whose window weights are staged at once
 constexpr int kTileHeader = 896;   // bytes of row tables and per-particle offsets
+constexpr int kGatherBatch = 128;  // particles per batch of the gathers (two threads each)
+constexpr int kGatherHeader = 1280;
 
 __host__ __device__ inline int mod32(int a) { return ((a % 32) + 32) % 32; }
 // Shared-memory strides of the padded tile (in elements), chosen so that the
@@ -162,10 +165,11 @@ struct sog_plan {
 namespace sogk {
 
 // Host-side launchers (sog_fft.cu).
+// Each adds the number of kernels it launched to `launches`.
 template <typename T>
-cudaError_t fft_mid_forward_conv_inverse(const sog_plan* p, cudaStream_t s);
+cudaError_t fft_mid_forward_conv_inverse(const sog_plan* p, cudaStream_t s, int& launches);
 template <typename T>
-cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s);
+cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s, int& launches);
 template <typename T>
 cudaError_t fft_prepare();
 

@@ -24,9 +24,6 @@
 
 namespace sogk {
 
-template <typename T>
-cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s);
-
 // ---------------------------------------------------------------------------
 // geometry passed to the kernels
 // ---------------------------------------------------------------------------
@@ -790,9 +787,36 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
   }
 }
 
+// Copies a padded tile (W0 x W1 x nz elements) from the periodic grid into
+// shared memory (row pitch rp, plane stride ps), element by element with
+// cp.async: xoff, yoff, zoff give the grid offsets of tile column, row and
+// plane.
+template <typename T>
+__device__ __forceinline__ void tile_load(const T* __restrict__ grid, T* __restrict__ st, int W0,
+                                          int W1, int nz, int rp, int ps, const int* __restrict__ xoff,
+                                          const int* __restrict__ yoff,
+                                          const long long* __restrict__ zoff) {
+  const int tot = W0 * W1 * nz;
+  const int nt = blockDim.x;
+  int lx = threadIdx.x % W0, r = threadIdx.x / W0;
+  int ly = r % W1, lz = r / W1;
+  const int sx = nt % W0, sr = nt / W0, sy = sr % W1, sz = sr / W1;
+  for (int i = threadIdx.x; i < tot; i += nt) {
+    cp_async_elem(st + lz * ps + ly * rp + lx, grid + zoff[lz] + yoff[ly] + xoff[lx]);
+    lx += sx;
+    ly += sy;
+    lz += sz;
+    if (lx >= W0) { lx -= W0; ++ly; }
+    if (ly >= W1) { ly -= W1; ++lz; }
+  }
+  cp_async_wait_all();
+}
+
 // Gathering, Eq. (3.10): Phi^mid_i = sum_g u[g] W(r_i - r_g) and its gradient.
-// The padded tile is loaded into shared memory once; a warp per particle,
-// lanes over the (dz, dy) rows of its window, each lane summing along x.
+// The padded tile is loaded into shared memory once.  Window values and
+// derivatives are staged per batch of kGatherBatch particles; then two
+// threads per particle each sum half of the window's z-planes (x, then y,
+// then z contractions in registers) and combine with one shuffle.
 template <typename T, int PW>
 __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T> w,
                                                              const P4<T>* __restrict__ rec,
@@ -807,103 +831,96 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
   if (!chunk_range(b, e, g.chunks)) return;
   const int W0 = g.W[0], W1 = g.W[1], W2 = g.W[2];
   const int P = PW > 0 ? PW : w.P;
-  const int PP = P * P;
-  const int RP = gather_row_pitch(W0);
-  const int PS = gather_plane_stride(RP, W1, P);
+  const int PS = W0 * W1;
+  constexpr int PR = PW > 0 ? PW : kMaxWin;
   long long* zoff = reinterpret_cast<long long*>(smraw);
   int* yoff = reinterpret_cast<int*>(zoff + 64);
-  int* bofs = yoff + 32;
-  T* wgt = reinterpret_cast<T*>(smraw + kTileHeader);  // [j][6][k]: w, w' for x, y, z
-  T* st = wgt + kTileBatch * 6 * kMaxWin;
+  int* xoff = yoff + 32;
+  int* bofs = xoff + 32;
+  T* wgt = reinterpret_cast<T*>(smraw + kGatherHeader);  // [j][6][P]: w, w' for x, y, z
+  T* st = wgt + kGatherBatch * 6 * P;
   const int tz = tile / (g.nt[0] * g.nt[1]);
   const int ty = (tile / g.nt[0]) % g.nt[1];
   const int tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo, oz = tz * g.T[2] - g.pad_lo;
   tile_tables(g, oy, oz, W2, false, yoff, zoff);
+  for (int i = threadIdx.x; i < W0; i += blockDim.x) xoff[i] = pmod(ox + i, g.I[0]);
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int xw = lane < W0 ? pmod(ox + lane, g.I[0]) : 0;
-  tile_rows<T, true>(const_cast<T*>(grid), st, W0, W1, W2, RP, PS, yoff, zoff, xw);
-  constexpr int NIT = PW > 0 ? (PW * PW + 31) / 32 : (kMaxWin * kMaxWin) / 32;
-  constexpr int PR = PW > 0 ? PW : kMaxWin;
-  int roff[NIT], rdy[NIT], rdz[NIT];  // this lane's (dz, dy) rows
-#pragma unroll
-  for (int it = 0; it < NIT; ++it) {
-    const int s2 = lane + 32 * it;
-    const int dz = s2 / P, dy = s2 - dz * P;
-    const bool ok = s2 < PP;
-    roff[it] = ok ? dz * PS + dy * RP : -1;
-    rdy[it] = ok ? dy : 0;
-    rdz[it] = ok ? dz : 0;
-  }
-  for (int p0 = b; p0 < e; p0 += kTileBatch) {
-    const int nb = min(kTileBatch, e - p0);
+  tile_load(grid, st, W0, W1, W2, W0, PS, xoff, yoff, zoff);
+  const int j = threadIdx.x >> 1, sl = threadIdx.x & 1;
+  const int z0 = sl ? (P + 1) / 2 : 0, z1 = sl ? P : (P + 1) / 2;
+  for (int p0 = b; p0 < e; p0 += kGatherBatch) {
+    const int nb = min(kGatherBatch, e - p0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * 3 * kMaxWin; idx += blockDim.x) {
-      const int j = idx / (3 * kMaxWin);
-      const int r = idx - j * 3 * kMaxWin;
-      const int ax = r / kMaxWin, k = r - ax * kMaxWin;
-      if (k < P) {
-        const P4<T> a = rec[p0 + j];
-        const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
-        const int g0 = (int)dceil(c - w.half);
-        T v, dv;
-        // d/dt of phi((g - t)/half) = -phi'/half
-        win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
-        T* wj = wgt + (j * 6 + 2 * ax) * kMaxWin;
-        wj[k] = v;
-        wj[kMaxWin + k] = -dv * w.inv_half;
-        if (r == 0) {
-          const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
-          bofs[j] = (gz0 + g.pad_lo) * PS + (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
-        }
+    for (int idx = threadIdx.x; idx < nb * 3 * P; idx += blockDim.x) {
+      const int jj = idx / (3 * P);
+      const int r = idx - jj * 3 * P;
+      const int ax = r / P, k = r - ax * P;
+      const P4<T> a = rec[p0 + jj];
+      const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
+      const int g0 = (int)dceil(c - w.half);
+      T v, dv;
+      // d/dt of phi((g - t)/half) = -phi'/half
+      win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
+      T* wj = wgt + jj * 6 * P + 2 * ax * P;
+      wj[k] = v;
+      wj[P + k] = -dv * w.inv_half;
+      if (r == 0) {
+        const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
+        bofs[jj] = (gz0 + g.pad_lo) * PS + (gy0 + g.pad_lo) * W0 + g0 + g.pad_lo;
       }
     }
     __syncthreads();
-    for (int j = warp; j < nb; j += nw) {
-      const T* wj = wgt + j * 6 * kMaxWin;
-      const T *wx = wj, *dwx = wj + kMaxWin, *wy = wj + 2 * kMaxWin, *dwy = wj + 3 * kMaxWin;
-      const T *wz = wj + 4 * kMaxWin, *dwz = wj + 5 * kMaxWin;
-      T rwx[PR], rdx[PR];
+    T f = 0, fx = 0, fy = 0, fz = 0;
+    if (j < nb) {
+      const T* wj = wgt + j * 6 * P;
+      T wx[PR], dwx[PR], wy[PR], dwy[PR];
 #pragma unroll
-      for (int dx = 0; dx < PR; ++dx) {
-        rwx[dx] = dx < P ? wx[dx] : T(0);
-        rdx[dx] = dx < P ? dwx[dx] : T(0);
+      for (int k = 0; k < PR; ++k) {
+        wx[k] = k < P ? wj[k] : T(0);
+        dwx[k] = k < P ? wj[P + k] : T(0);
+        wy[k] = k < P ? wj[2 * P + k] : T(0);
+        dwy[k] = k < P ? wj[3 * P + k] : T(0);
       }
       const T* bj = st + bofs[j];
-      T f = 0, fx = 0, fy = 0, fz = 0;
+      for (int dz = z0; dz < z1; ++dz) {
+        const T* pl = bj + dz * PS;
+        T Sx = 0, Sd = 0, Sy = 0;
 #pragma unroll
-      for (int it = 0; it < NIT; ++it) {
-        if (roff[it] >= 0) {
-          const T* rp = bj + roff[it];
-          T sx = 0, sd = 0;
+        for (int dy = 0; dy < PR; ++dy) {
+          if (dy < P) {
+            const T* rp = pl + dy * W0;
+            T sx = 0, sd = 0;
 #pragma unroll
-          for (int dx = 0; dx < PR; ++dx) {
-            if (dx < P) {
-              const T u = rp[dx];
-              sx += u * rwx[dx];
-              sd += u * rdx[dx];
+            for (int dx = 0; dx < PR; ++dx) {
+              if (dx < P) {
+                const T u = rp[dx];
+                sx += u * wx[dx];
+                sd += u * dwx[dx];
+              }
             }
+            Sx += wy[dy] * sx;
+            Sd += wy[dy] * sd;
+            Sy += dwy[dy] * sx;
           }
-          const T wyv = wy[rdy[it]], wzv = wz[rdz[it]];
-          const T wyz = wyv * wzv;
-          f += wyz * sx;
-          fx += wyz * sd;
-          fy += dwy[rdy[it]] * wzv * sx;
-          fz += wyv * dwz[rdz[it]] * sx;
         }
+        const T wzv = wj[4 * P + dz], dwzv = wj[5 * P + dz];
+        f += wzv * Sx;
+        fx += wzv * Sd;
+        fy += wzv * Sy;
+        fz += dwzv * Sx;
       }
-      f = warp_sum(f);
-      fx = warp_sum(fx);
-      fy = warp_sum(fy);
-      fz = warp_sum(fz);
-      if (lane == 0) {
-        const int o = perm[p0 + j];
-        phi_out[o] = (double)f;
-        grad_out[3 * o] = (double)fx * invh.x;
-        grad_out[3 * o + 1] = (double)fy * invh.y;
-        grad_out[3 * o + 2] = (double)fz * invh.z;
-      }
+    }
+    f += __shfl_xor_sync(0xffffffffu, f, 1);
+    fx += __shfl_xor_sync(0xffffffffu, fx, 1);
+    fy += __shfl_xor_sync(0xffffffffu, fy, 1);
+    fz += __shfl_xor_sync(0xffffffffu, fz, 1);
+    if (j < nb && sl == 0) {
+      const int o = perm[p0 + j];
+      phi_out[o] = (double)f;
+      grad_out[3 * o] = (double)fx * invh.x;
+      grad_out[3 * o + 1] = (double)fy * invh.y;
+      grad_out[3 * o + 2] = (double)fz * invh.z;
     }
   }
 }
@@ -1107,9 +1124,10 @@ __global__ void k_long_contract(const T* __restrict__ A, T* __restrict__ B, cons
 }
 
 // Gathering, Eq. (3.19) discretised: Phi_i = sum_n T_n(x_i) sum_g W2 u_n[g].
-// The padded tile of all P proxy planes is loaded into shared memory; window
-// weights and Chebyshev values are staged per batch of particles; a warp per
-// particle, lanes over the (n, dy) rows of its window, each summing along x.
+// The padded tile of all P proxy planes is loaded into shared memory; 2D
+// window values are staged per batch of particles; two threads per particle
+// each take half of the planes n, with T_n and T_n' from the Chebyshev
+// recurrence, and combine with one shuffle.
 template <typename T, int PW>
 __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T> w, int P,
                                                               const P4<T>* __restrict__ rec,
@@ -1124,92 +1142,103 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
   if (!chunk_range(b, e, g.chunks)) return;
   const int W0 = g.W[0], W1 = g.W[1];
   const int Pw = PW > 0 ? PW : w.P;
-  const int RP = gather_row_pitch(W0);
-  const int PS = gather_plane_stride(RP, W1, Pw);
-  const int nrow = P * Pw;
+  const int PS = W0 * W1;
+  constexpr int PR = PW > 0 ? PW : kMaxWin;
   long long* zoff = reinterpret_cast<long long*>(smraw);
   int* yoff = reinterpret_cast<int*>(zoff + 64);
-  int* bofs = yoff + 32;
-  // per particle: wx, w'x, wy, w'y [kMaxWin each], T_n, T'_n [kMaxCheb each]
-  constexpr int kRec = 4 * kMaxWin + 2 * kMaxCheb;
-  T* wgt = reinterpret_cast<T*>(smraw + kTileHeader);
-  T* st = wgt + kTileBatch * kRec;
+  int* xoff = yoff + 32;
+  int* bofs = xoff + 32;
+  T* wgt = reinterpret_cast<T*>(smraw + kGatherHeader);  // [j][4][Pw]: w, w' for x, y
+  T* st = wgt + kGatherBatch * 4 * Pw;
   const int ty = tile / g.nt[0], tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
   tile_tables(g, oy, 0, P, true, yoff, zoff);
+  for (int i = threadIdx.x; i < W0; i += blockDim.x) xoff[i] = pmod(ox + i, g.I[0]);
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int xw = lane < W0 ? pmod(ox + lane, g.I[0]) : 0;
-  tile_rows<T, true>(const_cast<T*>(planes), st, W0, W1, P, RP, PS, yoff, zoff, xw);
-  constexpr int PR = PW > 0 ? PW : kMaxWin;
-  for (int p0 = b; p0 < e; p0 += kTileBatch) {
-    const int nb = min(kTileBatch, e - p0);
+  tile_load(planes, st, W0, W1, P, W0, PS, xoff, yoff, zoff);
+  const int j = threadIdx.x >> 1, sl = threadIdx.x & 1;
+  const int n0 = sl ? (P + 1) / 2 : 0, n1 = sl ? P : (P + 1) / 2;
+  for (int p0 = b; p0 < e; p0 += kGatherBatch) {
+    const int nb = min(kGatherBatch, e - p0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * 2 * kMaxWin; idx += blockDim.x) {
-      const int j = idx / (2 * kMaxWin);
-      const int r = idx - j * 2 * kMaxWin;
-      const int ax = r / kMaxWin, k = r - ax * kMaxWin;
-      if (k < Pw) {
-        const P4<T> a = rec[p0 + j];
-        const T c = ax == 0 ? a.x : a.y;
-        const int g0 = (int)dceil(c - w.half);
-        T v, dv;
-        win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
-        T* wj = wgt + j * kRec + 2 * ax * kMaxWin;
-        wj[k] = v;
-        wj[kMaxWin + k] = -dv * w.inv_half;
-        if (r == 0) {
-          const int gy0 = (int)dceil(a.y - w.half);
-          bofs[j] = (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
-        }
+    for (int idx = threadIdx.x; idx < nb * 2 * Pw; idx += blockDim.x) {
+      const int jj = idx / (2 * Pw);
+      const int r = idx - jj * 2 * Pw;
+      const int ax = r / Pw, k = r - ax * Pw;
+      const P4<T> a = rec[p0 + jj];
+      const T c = ax == 0 ? a.x : a.y;
+      const int g0 = (int)dceil(c - w.half);
+      T v, dv;
+      win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
+      T* wj = wgt + jj * 4 * Pw + 2 * ax * Pw;
+      wj[k] = v;
+      wj[Pw + k] = -dv * w.inv_half;
+      if (r == 0) {
+        const int gy0 = (int)dceil(a.y - w.half);
+        bofs[jj] = (gy0 + g.pad_lo) * W0 + g0 + g.pad_lo;
       }
     }
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-      T* wj = wgt + j * kRec + 4 * kMaxWin;
-      cheb_all_d(rec[p0 + j].z, P, wj, wj + kMaxCheb);
-    }
     __syncthreads();
-    for (int j = warp; j < nb; j += nw) {
-      const T* wj = wgt + j * kRec;
-      const T *wy = wj + 2 * kMaxWin, *dwy = wj + 3 * kMaxWin;
-      const T *tn = wj + 4 * kMaxWin, *dtn = tn + kMaxCheb;
-      T rwx[PR], rdx[PR];
+    T f = 0, fx = 0, fy = 0, fz = 0;
+    if (j < nb) {
+      const T* wj = wgt + j * 4 * Pw;
+      T wx[PR], dwx[PR], wy[PR], dwy[PR];
 #pragma unroll
-      for (int dx = 0; dx < PR; ++dx) {
-        rwx[dx] = dx < Pw ? wj[dx] : T(0);
-        rdx[dx] = dx < Pw ? wj[kMaxWin + dx] : T(0);
+      for (int k = 0; k < PR; ++k) {
+        wx[k] = k < Pw ? wj[k] : T(0);
+        dwx[k] = k < Pw ? wj[Pw + k] : T(0);
+        wy[k] = k < Pw ? wj[2 * Pw + k] : T(0);
+        dwy[k] = k < Pw ? wj[3 * Pw + k] : T(0);
       }
       const T* bj = st + bofs[j];
-      T f = 0, fx = 0, fy = 0, fz = 0;
-      for (int rr = lane; rr < nrow; rr += 32) {
-        const int n = rr / Pw, dy = rr - n * Pw;
-        const T* rp = bj + n * PS + dy * RP;
-        T sx = 0, sd = 0;
+      const T x = rec[p0 + j].z;
+      // T_n(x), T_n'(x) by the three-term recurrence
+      T tm1 = 0, tc = 1, dm1 = 0, dc = 0;
+      for (int n = 0; n < n1; ++n) {
+        if (n >= n0) {
+          const T* pl = bj + n * PS;
+          T Sx = 0, Sd = 0, Sy = 0;
 #pragma unroll
-        for (int dx = 0; dx < PR; ++dx) {
-          if (dx < Pw) {
-            const T u = rp[dx];
-            sx += u * rwx[dx];
-            sd += u * rdx[dx];
+          for (int dy = 0; dy < PR; ++dy) {
+            if (dy < Pw) {
+              const T* rp = pl + dy * W0;
+              T sx = 0, sd = 0;
+#pragma unroll
+              for (int dx = 0; dx < PR; ++dx) {
+                if (dx < Pw) {
+                  const T u = rp[dx];
+                  sx += u * wx[dx];
+                  sd += u * dwx[dx];
+                }
+              }
+              Sx += wy[dy] * sx;
+              Sd += wy[dy] * sd;
+              Sy += dwy[dy] * sx;
+            }
           }
+          f += tc * Sx;
+          fx += tc * Sd;
+          fy += tc * Sy;
+          fz += dc * Sx;
         }
-        const T ty_ = tn[n] * wy[dy];
-        f += ty_ * sx;
-        fx += ty_ * sd;
-        fy += tn[n] * dwy[dy] * sx;
-        fz += dtn[n] * wy[dy] * sx;
+        const T tn = n == 0 ? x : T(2) * x * tc - tm1;
+        const T dn = n == 0 ? T(1) : T(2) * tc + T(2) * x * dc - dm1;
+        tm1 = tc;
+        tc = tn;
+        dm1 = dc;
+        dc = dn;
       }
-      f = warp_sum(f);
-      fx = warp_sum(fx);
-      fy = warp_sum(fy);
-      fz = warp_sum(fz);
-      if (lane == 0) {
-        const int o = perm[p0 + j];
-        phi_out[o] = (double)f;
-        grad_out[3 * o] = (double)fx * sc.x;
-        grad_out[3 * o + 1] = (double)fy * sc.y;
-        grad_out[3 * o + 2] = (double)fz * sc.z;
-      }
+    }
+    f += __shfl_xor_sync(0xffffffffu, f, 1);
+    fx += __shfl_xor_sync(0xffffffffu, fx, 1);
+    fy += __shfl_xor_sync(0xffffffffu, fy, 1);
+    fz += __shfl_xor_sync(0xffffffffu, fz, 1);
+    if (j < nb && sl == 0) {
+      const int o = perm[p0 + j];
+      phi_out[o] = (double)f;
+      grad_out[3 * o] = (double)fx * sc.x;
+      grad_out[3 * o + 1] = (double)fy * sc.y;
+      grad_out[3 * o + 2] = (double)fz * sc.z;
     }
   }
 }
@@ -1403,20 +1432,18 @@ static cudaError_t allow_pw() {
 static size_t mid_smem(const sog_plan* p, size_t es, bool gather) {
   const TileGeom& g = p->gm;
   const int P = p->wm.P;
+  if (gather)
+    return kGatherHeader + ((size_t)kGatherBatch * 6 * P + (size_t)g.W[0] * g.W[1] * g.W[2]) * es;
+  // fixed-point tile: int32 for FP32, int64 for FP64 (same size as T)
   const int rp = gather_row_pitch(g.W[0]);
   const size_t tile = (size_t)g.W[2] * gather_plane_stride(rp, g.W[1], P);
-  if (gather) return kTileHeader + ((size_t)kTileBatch * 6 * kMaxWin + tile) * es;
-  // fixed-point tile: int32 for FP32, int64 for FP64 (same size as T)
   return kTileHeader + ((size_t)kTileBatch * 3 * kMaxWin + tile) * es;
 }
 static size_t long_smem(const sog_plan* p, size_t es, bool gather) {
   const TileGeom& g = p->gl;
   const int P = p->prm.P_cheb;
-  if (gather) {
-    const int rp = gather_row_pitch(g.W[0]);
-    return kTileHeader + ((size_t)kTileBatch * (4 * kMaxWin + 2 * kMaxCheb) +
-                          (size_t)P * gather_plane_stride(rp, g.W[1], p->wl.P)) * es;
-  }
+  if (gather)
+    return kGatherHeader + ((size_t)kGatherBatch * 4 * p->wl.P + (size_t)P * g.W[0] * g.W[1]) * es;
   const size_t pl = (size_t)P * (g.W[0] * g.W[1] + 1);
   return (pl + 8 * (2 * kMaxWin + kMaxCheb)) * es;
 }
@@ -1534,8 +1561,9 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     LAUNCH_CHECK();
     mark_end(p, 2, s);
     mark_begin(p, 3, s);
-    SOG_CK(fft_mid_forward_conv_inverse<T>(p, s));
-    p->launches += 5;
+    int nl = 0;
+    SOG_CK(fft_mid_forward_conv_inverse<T>(p, s, nl));
+    p->launches += nl;
     mark_end(p, 3, s);
     mark_begin(p, 4, s);
     const size_t sm2 = mid_smem(p, sizeof(T), true);
@@ -1580,16 +1608,16 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     }
     mark_end(p, 5, s);
     mark_begin(p, 6, s);
-    SOG_CK(fft_long_pass<T>(p, false, s));
-    p->launches += 2;
+    int nl = 0;
+    SOG_CK(fft_long_pass<T>(p, false, s, nl));
     const int C = m.I_long[0] / 2 + 1;
     const int modes = m.I_long[1] * C;
     const int per = 256 / P;
     k_long_contract<T><<<(modes + per - 1) / per, 256, 0, s>>>(
         A, B, reinterpret_cast<const T*>(p->d_kmat), P, m.I_long[1], C);
     LAUNCH_CHECK();
-    SOG_CK(fft_long_pass<T>(p, true, s));
-    p->launches += 2;
+    SOG_CK(fft_long_pass<T>(p, true, s, nl));
+    p->launches += nl;
     mark_end(p, 6, s);
     mark_begin(p, 7, s);
     const size_t sm2 = long_smem(p, sizeof(T), true);

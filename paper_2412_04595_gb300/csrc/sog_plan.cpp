@@ -255,6 +255,16 @@ void factorize(int n, sogk::FftLen& f) {
   while (k % 2 == 0) { f.radix[f.nst++] = 2; k /= 2; }
   for (int p : {3, 5, 7})
     while (k % p == 0) { f.radix[f.nst++] = p; k /= p; }
+  f.n8 = f.n4 = f.n2 = f.n3 = f.n5 = f.n7 = 0;
+  for (int st = 0; st < f.nst; ++st) {
+    const int R = f.radix[st];
+    f.n8 += R == 8;
+    f.n4 += R == 4;
+    f.n2 += R == 2;
+    f.n3 += R == 3;
+    f.n5 += R == 5;
+    f.n7 += R == 7;
+  }
 }
 
 // Gauss-Legendre nodes and weights on [-1, 1].
