@@ -14,6 +14,7 @@ namespace sogk {
 constexpr int kMaxFftStages = 16;
 constexpr int kMaxCheb = 64;
 constexpr int kMaxWin = 16;
+constexpr int kNearD = 8;  // degree of the near-field table polynomials
 
 // One FFT length: radix sequence of the Stockham stages and the offset of its
 // n roots of unity exp(-2 pi i t / n) in the twiddle table.

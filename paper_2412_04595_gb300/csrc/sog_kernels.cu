@@ -327,7 +327,6 @@ struct Acc {
 };
 
 constexpr int kNearThreads = 256;
-constexpr int kNearQ = 64;       // per-warp queue of accepted pairs
 // source particles staged per pass and table entries kept in shared memory
 // (static shared memory stays under 48 KB for both element types)
 template <typename T> struct NearCfg;
@@ -345,51 +344,64 @@ __device__ __forceinline__ void inv_dist(double r2, double& rr, double& rinv) {
   rinv = 1.0 / rr;
 }
 
-// One warp, one target: test the staged sources 32 at a time, queue the
-// pairs inside r_c (ballot + prefix count) and evaluate every full batch of
-// 32 queued pairs with all lanes busy.  SHIFT: sources carry a periodic
-// shift s (dx = (x_i + s) - (x_j - s), both brackets exact).
+// Position of the k-th (from 0) set bit of m; k < popc(m).
+__device__ __forceinline__ int nth_bit(unsigned m, int k) {
+  int pos = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const int c = __popc(m & ((1u << w) - 1u));
+    if (k >= c) {
+      k -= c;
+      m >>= w;
+      pos += w;
+    }
+  }
+  return pos;
+}
+
+// Near kernel g(r)/r and its radial derivative from the piecewise
+// polynomial table (degree kNearD in u on each of the K intervals).
+template <typename T>
+__device__ __forceinline__ void near_pair(T r2, T q, T dx, T dy, T dz, const T* __restrict__ tab,
+                                          int K, T hK, T ihK, Acc<T>& phi, T& gx, T& gy, T& gz) {
+  T rr, rinv;
+  inv_dist(r2, rr, rinv);
+  int kk = (int)(rr * ihK);
+  kk = kk < K ? kk : K - 1;
+  const T ihK2 = T(2) * ihK;
+  const T u = (rr - (T)kk * hK) * ihK2 - T(1);
+  const T* cf = tab + kk * (kNearD + 1);
+  T p = cf[kNearD], dp = T(0);
+#pragma unroll
+  for (int jj = kNearD - 1; jj >= 0; --jj) {
+    dp = dp * u + p;
+    p = p * u + cf[jj];
+  }
+  // g(r) = 1 - r F_M(r) = p; near kernel G = g/r; dG/dr = (g' - g/r)/r
+  const T gp = dp * ihK2;
+  phi.add(q * p * rinv);
+  const T f = q * (gp - p * rinv) * rinv * rinv;
+  gx += f * dx;
+  gy += f * dy;
+  gz += f * dz;
+}
+
+// One warp, one target.  Pass 1 tests the staged sources 32 at a time and
+// keeps one bit per source inside r_c (a ballot per step).  Pass 2 hands the
+// accepted sources to the lanes in order, 32 at a time (prefix counts of the
+// step masks, binary search, k-th set bit), and evaluates them with all
+// lanes busy.  SHIFT: sources carry a periodic shift s
+// (dx = (x_i + s) - (x_j - s), both brackets exact).
 template <typename T, bool SHIFT>
 __device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restrict__ src,
                                             const float2* __restrict__ sh, int nsteps, T rc2,
-                                            const T* __restrict__ tab, int K, int D, T hK, T ihK,
-                                            P4<T>* __restrict__ myq, T* __restrict__ myr,
-                                            T& o_phi, T& o_gx, T& o_gy, T& o_gz) {
+                                            const T* __restrict__ tab, int K, T hK, T ihK,
+                                            unsigned* __restrict__ msk, T& o_phi, T& o_gx, T& o_gy,
+                                            T& o_gz) {
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  const T ihK2 = T(2) * ihK;
-  Acc<T> phi{0, 0};
-  T gx = 0, gy = 0, gz = 0;
-  int qn = 0, qh = 0;
-  auto eval_batch = [&](int cnt) {
-    if (lane < cnt) {
-      const int e = (qh + lane) & (kNearQ - 1);
-      const P4<T> d = myq[e];
-      T rr, rinv;
-      inv_dist(myr[e], rr, rinv);
-      int kk = (int)(rr * ihK);
-      kk = kk < K ? kk : K - 1;
-      const T u = (rr - (T)kk * hK) * ihK2 - T(1);
-      const T* cf = tab + kk * (D + 1);
-      T p = cf[D], dp = T(0);
-      for (int jj = D - 1; jj >= 0; --jj) {
-        dp = dp * u + p;
-        p = p * u + cf[jj];
-      }
-      // g(r) = 1 - r F_M(r) = p; near kernel G = g/r; dG/dr = (g' - g/r)/r
-      const T gp = dp * ihK2;
-      phi.add(d.q * p * rinv);
-      const T f = d.q * (gp - p * rinv) * rinv * rinv;
-      gx += f * d.x;
-      gy += f * d.y;
-      gz += f * d.z;
-    }
-    qh += cnt;
-  };
-  for (int st = 0; st < nsteps; ++st) {
-    const int k = st * 32 + lane;
+  auto diff = [&](int k, T& dx, T& dy, T& dz, T& q) {
     const P4<T> b = src[k];
-    T dx, dy;
     if (SHIFT) {
       const float2 s2 = sh[k];
       dx = (a.x + (T)s2.x) - b.x;
@@ -398,25 +410,48 @@ __device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restr
       dx = a.x - b.x;
       dy = a.y - b.y;
     }
-    const T dz = a.z - b.z;
+    dz = a.z - b.z;
+    q = b.q;
+  };
+  for (int st = 0; st < nsteps; ++st) {
+    T dx, dy, dz, q;
+    diff(st * 32 + lane, dx, dy, dz, q);
     const T r2 = dx * dx + dy * dy + dz * dz;
     // r2 == 0 only for the target itself (coincident charges are invalid input)
-    const bool in = r2 < rc2 && r2 > T(0);
-    const unsigned m = __ballot_sync(0xffffffffu, in);
-    if (in) {
-      const int e = (qn + __popc(m & lt)) & (kNearQ - 1);
-      myq[e] = P4<T>{dx, dy, dz, b.q};
-      myr[e] = r2;
+    const unsigned m = __ballot_sync(full, r2 < rc2 && r2 > T(0));
+    if (lane == 0) msk[st] = m;
+  }
+  __syncwarp();
+  Acc<T> phi{0, 0};
+  T gx = 0, gy = 0, gz = 0;
+  for (int c0 = 0; c0 < nsteps; c0 += 32) {
+    const unsigned ms = c0 + lane < nsteps ? msk[c0 + lane] : 0u;
+    const int cnt = __popc(ms);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += v;
     }
-    qn += __popc(m);
-    __syncwarp();
-    if (qn - qh >= 32) {
-      eval_batch(32);
-      __syncwarp();
+    const int total = __shfl_sync(full, incl, 31);
+    for (int h0 = 0; h0 < total; h0 += 32) {
+      const int h = min(h0 + lane, total - 1);
+      int sidx = 0;  // number of steps whose inclusive count is <= h
+#pragma unroll
+      for (int stp = 16; stp >= 1; stp >>= 1) {
+        const int v = __shfl_sync(full, incl, sidx + stp - 1);
+        if (v <= h) sidx += stp;
+      }
+      const int ex = __shfl_sync(full, incl, sidx) - __shfl_sync(full, cnt, sidx);
+      const unsigned mk = __shfl_sync(full, ms, sidx);
+      if (h0 + lane < total) {
+        const int k = (c0 + sidx) * 32 + nth_bit(mk, h - ex);
+        T dx, dy, dz, q;
+        diff(k, dx, dy, dz, q);
+        near_pair(dx * dx + dy * dy + dz * dz, q, dx, dy, dz, tab, K, hK, ihK, phi, gx, gy, gz);
+      }
     }
   }
-  if (qn - qh > 0) eval_batch(qn - qh);
-  __syncwarp();
   o_phi = phi.get();
   o_gx = gx;
   o_gy = gy;
@@ -439,8 +474,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
   constexpr int kNearSrc = NearCfg<T>::src, kNearTab = NearCfg<T>::tab;
   __shared__ P4<T> src[kNearSrc];                  // x - s, y - s, z, q
   __shared__ float2 shs[kNearSrc];                 // s (periodic shift) per source
-  __shared__ P4<T> qd[kNearThreads / 32][kNearQ];  // dx, dy, dz, q_j
-  __shared__ T qr[kNearThreads / 32][kNearQ];      // r^2
+  __shared__ unsigned msk[kNearThreads / 32][kNearSrc / 32];  // accepted sources per step
   __shared__ T stab[kNearTab];
   __shared__ int cb[27], coff[28];
   __shared__ float csx[27], csy[27];
@@ -448,7 +482,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
   const int c = blockIdx.x;
   const int tb = cstart[c], te = cstart[c + 1];
   if (tb == te) return;
-  const int ntab = g.K * (g.D + 1);
+  const int ntab = g.K * (kNearD + 1);
   const bool tab_sm = ntab <= kNearTab;
   if (tab_sm)
     for (int i = threadIdx.x; i < ntab; i += blockDim.x) stab[i] = tab[i];
@@ -492,8 +526,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
   const T rc = (T)g.rc, rc2 = rc * rc;
   const T hK = rc / (T)g.K, ihK = (T)g.K / rc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNearThreads / 32;
-  P4<T>* myq = qd[warp];
-  T* myr = qr[warp];
+  unsigned* mymsk = msk[warp];
   const int ntg = te - tb;
   const int nsrc = coff[ncell];
   const bool shifted = any_shift != 0;
@@ -531,7 +564,6 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
         // few cells: minimum image per pair (sources unshifted)
         Acc<T> phi{0, 0};
         T gx = 0, gy = 0, gz = 0;
-        const T ihK2 = T(2) * ihK;
         for (int k = lane; k < ns; k += 32) {  // padding excluded: rounding would fold it back
           const P4<T> b = src[k];
           T dx = a.x - b.x, dy = a.y - b.y;
@@ -539,33 +571,16 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
           dx -= Lx * drint(dx * iLx);
           dy -= Ly * drint(dy * iLy);
           const T r2 = dx * dx + dy * dy + dz * dz;
-          if (!(r2 < rc2 && r2 > T(0))) continue;
-          T rr, rinv;
-          inv_dist(r2, rr, rinv);
-          int kk = (int)(rr * ihK);
-          kk = kk < g.K ? kk : g.K - 1;
-          const T u = (rr - (T)kk * hK) * ihK2 - T(1);
-          const T* cf = tb_ + kk * (g.D + 1);
-          T p = cf[g.D], dp = T(0);
-          for (int jj = g.D - 1; jj >= 0; --jj) {
-            dp = dp * u + p;
-            p = p * u + cf[jj];
-          }
-          const T gp = dp * ihK2;
-          phi.add(b.q * p * rinv);
-          const T f = b.q * (gp - p * rinv) * rinv * rinv;
-          gx += f * dx;
-          gy += f * dy;
-          gz += f * dz;
+          if (r2 < rc2 && r2 > T(0)) near_pair(r2, b.q, dx, dy, dz, tb_, g.K, hK, ihK, phi, gx, gy, gz);
         }
         v0 = phi.get();
         v1 = gx;
         v2 = gy;
         v3 = gz;
       } else if (shifted) {
-        near_target<T, true>(a, src, shs, nsteps, rc2, tb_, g.K, g.D, hK, ihK, myq, myr, v0, v1, v2, v3);
+        near_target<T, true>(a, src, shs, nsteps, rc2, tb_, g.K, hK, ihK, mymsk, v0, v1, v2, v3);
       } else {
-        near_target<T, false>(a, src, shs, nsteps, rc2, tb_, g.K, g.D, hK, ihK, myq, myr, v0, v1, v2, v3);
+        near_target<T, false>(a, src, shs, nsteps, rc2, tb_, g.K, hK, ihK, mymsk, v0, v1, v2, v3);
       }
       v0 = warp_sum(v0);
       v1 = warp_sum(v1);

@@ -589,7 +589,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   if (tw.empty()) tw.assign(2, 0.0);
 
   // near table
-  p->near_D = 8;
+  p->near_D = sogk::kNearD;
   std::vector<double> ntab;
   if (!near_table(w, s, prm.rc, p->near_D, prec == SOG_PREC_FP64 ? 3e-15 : 1e-9, p->near_K, ntab)) {
     delete p;
