@@ -1032,51 +1032,57 @@ __global__ void __launch_bounds__(256) k_long_spread(TileGeom g, WinT<T> w, int 
   tile_rows<T, false>(planes, st, W0, W1, P, W0, ps, yoff, zoff, xw);
 }
 
-// Small long-range grids (cubic boxes: I_long of order 16): each CTA takes a
-// slice of the particles; every thread owns grid points of all P planes in
+// Small long-range grids (I_long <= 16, one tile): each CTA takes a slice
+// of the particles; every thread owns grid points of all P planes in
 // registers and adds q_j W2 T_n(x_j) for the particles whose window covers
-// them (no atomics).  The per-CTA planes go to scratch and k_long_reduce adds
-// them in a fixed order.
+// them (no atomics).  Window values on every grid line (nearest image) and
+// the Chebyshev values are staged per batch by all threads.  The per-CTA
+// planes go to scratch and k_long_reduce adds them in a fixed order.
 constexpr int kSmallBatch = 32;
 
 template <typename T, int PMAX>
 __global__ void __launch_bounds__(256) k_long_spread_small(int I0, int I1, WinT<T> w, int P,
                                                            const P4<T>* __restrict__ rec, int N,
                                                            T* __restrict__ partial) {
-  __shared__ T wx[kSmallBatch][16], wy[kSmallBatch][16], tn[kSmallBatch][PMAX];
+  __shared__ T wx[kSmallBatch][16], wy[kSmallBatch][16];
+  __shared__ __align__(16) T tn[kSmallBatch][PMAX];
   const int G = I0 * I1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int per = (N + gridDim.x - 1) / gridDim.x;
   const int b = blockIdx.x * per, e = min(N, b + per);
   const T iI0 = T(1) / (T)I0, iI1 = T(1) / (T)I1;
   for (int g0 = 0; g0 < G; g0 += blockDim.x) {
     const int gpt = g0 + threadIdx.x;
-    const int gx = gpt % I0, gy = gpt / I0;
+    const int gy = gpt / I0, gx = gpt - gy * I0;
     T acc[PMAX];
 #pragma unroll
     for (int n = 0; n < PMAX; ++n) acc[n] = T(0);
     for (int p0 = b; p0 < e; p0 += kSmallBatch) {
       const int nb = min(kSmallBatch, e - p0);
       __syncthreads();
-      // one warp per particle: weights over the whole (periodic) grid lines
-      for (int j = warp; j < nb; j += nw) {
-        const P4<T> a = rec[p0 + j];
-        for (int k = lane; k < I0; k += 32) {
+      for (int idx = threadIdx.x; idx < nb * 32; idx += blockDim.x) {
+        const int j = idx >> 5, ax = (idx >> 4) & 1, k = idx & 15;
+        const int Id = ax ? I1 : I0;
+        if (k < Id) {
+          const P4<T> a = rec[p0 + j];
           // nearest image of grid index k relative to the particle
-          T d = (T)k - a.x;
-          d -= (T)I0 * drint(d * iI0);
+          T d = (T)k - (ax ? a.y : a.x);
+          d -= (T)Id * drint(d * (ax ? iI1 : iI0));
           T v, dv;
           win_eval(w, d * w.inv_half, v, dv);
-          wx[j][k] = v * a.q;
+          if (ax) wy[j][k] = v;
+          else wx[j][k] = v * a.q;
         }
-        for (int k = lane; k < I1; k += 32) {
-          T d = (T)k - a.y;
-          d -= (T)I1 * drint(d * iI1);
-          T v, dv;
-          win_eval(w, d * w.inv_half, v, dv);
-          wy[j][k] = v;
+      }
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        const T x = rec[p0 + j].z;
+        T t0 = T(1), t1 = x;
+#pragma unroll
+        for (int n = 0; n < PMAX; ++n) {
+          tn[j][n] = n < P ? t0 : T(0);
+          const T t2 = T(2) * x * t1 - t0;
+          t0 = t1;
+          t1 = t2;
         }
-        if (lane == 0) cheb_all(a.z, P, tn[j]);
       }
       __syncthreads();
       if (gpt < G) {
@@ -1084,8 +1090,7 @@ __global__ void __launch_bounds__(256) k_long_spread_small(int I0, int I1, WinT<
           const T c = wx[j][gx] * wy[j][gy];
           if (c != T(0)) {
 #pragma unroll
-            for (int n = 0; n < PMAX; ++n)
-              if (n < P) acc[n] += c * tn[j][n];
+            for (int n = 0; n < PMAX; ++n) acc[n] += c * tn[j][n];
           }
         }
       }
@@ -1099,17 +1104,30 @@ __global__ void __launch_bounds__(256) k_long_spread_small(int I0, int I1, WinT<
   }
 }
 
+// planes[n][y][x] = sum over the CTAs b of partial[b][n][y][x], in the
+// order b = 0, 1, ...: eight threads per value each sum a contiguous eighth,
+// then the eight sums are added in a fixed order.
 template <typename T>
 __global__ void k_long_reduce(const T* __restrict__ partial, int nblk, int I0, int I1, int P,
                               T* __restrict__ planes) {
   const int G = I0 * I1;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P * G) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = t >> 3, part = t & 7;
+  const int len = (nblk + 7) / 8;
+  const int b0 = part * len, b1 = min(nblk, b0 + len);
   T acc = 0;
-  for (int b = 0; b < nblk; ++b) acc += partial[(size_t)b * P * G + i];
-  const int n = i / G, gg = i - n * G;
-  const int y = gg / I0, x = gg - y * I0;
-  planes[((size_t)n * I1 + y) * (I0 + 2) + x] = acc;
+  if (i < P * G)
+    for (int bb = b0; bb < b1; ++bb) acc += partial[(size_t)bb * P * G + i];
+  // fixed-order combination of the eight partial sums (lanes 8k .. 8k+7)
+  const int base = threadIdx.x & 24;
+  T tot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) tot += __shfl_sync(0xffffffffu, acc, base + k);
+  if (part == 0 && i < P * G) {
+    const int n = i / G, gg = i - n * G;
+    const int y = gg / I0, x = gg - y * I0;
+    planes[((size_t)n * I1 + y) * (I0 + 2) + x] = tot;
+  }
 }
 
 // Per-mode z-contraction (Eq. 3.17 in the Chebyshev basis): for every 2D
@@ -1263,17 +1281,22 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
 // ---------------------------------------------------------------------------
 
 // Per-block partial Chebyshev moments sum_j q_j T_n(x_j), n < P: T_n by the
-// recurrence in the element type (|T_n| <= 1 on [-1, 1]), products summed in
-// FP64 per thread, then per block.
+// recurrence in the element type (|T_n| <= 1 on [-1, 1]); each thread sums
+// its few particles (about N / 19,456) in the element type, warps and blocks
+// sum in FP64.  The moments are then combined with the FP64 kernel matrix
+// and the k = 0 potential is evaluated in FP64 (Clenshaw).
+constexpr int kK0Blocks = 152, kK0Threads = 128;
+
 template <typename T, int PMAX>
-__global__ void __launch_bounds__(256) k_k0_moments(const T* __restrict__ q,
-                                                    const T* __restrict__ r, int N, int P,
-                                                    double halfLz, double* __restrict__ part) {
-  __shared__ double wsum[8][PMAX];
+__global__ void __launch_bounds__(kK0Threads) k_k0_moments(const T* __restrict__ q,
+                                                           const T* __restrict__ r, int N, int P,
+                                                           double halfLz, double* __restrict__ part) {
+  __shared__ double wsum[kK0Threads / 32][PMAX];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double mom[PMAX];
+  // a thread sums its few particles in T, the block sums in double
+  T mom[PMAX];
 #pragma unroll
-  for (int n = 0; n < PMAX; ++n) mom[n] = 0.0;
+  for (int n = 0; n < PMAX; ++n) mom[n] = T(0);
   const double ih = 1.0 / halfLz;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     double z = (double)r[3 * i + 2];
@@ -1284,30 +1307,23 @@ __global__ void __launch_bounds__(256) k_k0_moments(const T* __restrict__ q,
     T t0 = T(1), t1 = x;
 #pragma unroll
     for (int n = 0; n < PMAX; ++n) {
-      if (n < P) {
-        T tn;
-        if (n == 0) tn = T(1);
-        else if (n == 1) tn = x;
-        else {
-          tn = T(2) * x * t1 - t0;
-          t0 = t1;
-          t1 = tn;
-        }
-        mom[n] += (double)(qi * tn);
-      }
+      mom[n] += qi * t0;
+      const T t2 = T(2) * x * t1 - t0;
+      t0 = t1;
+      t1 = t2;
     }
   }
 #pragma unroll
   for (int n = 0; n < PMAX; ++n) {
     if (n < P) {
-      const double v = warp_sum(mom[n]);
+      const double v = warp_sum((double)mom[n]);
       if (lane == 0) wsum[warp][n] = v;
     }
   }
   __syncthreads();
   for (int n = threadIdx.x; n < P; n += blockDim.x) {
     double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w][n];
+    for (int w = 0; w < kK0Threads / 32; ++w) t += wsum[w][n];
     part[(size_t)blockIdx.x * P + n] = t;
   }
 }
@@ -1325,7 +1341,7 @@ __device__ __forceinline__ double warp_sum_partials(const double* __restrict__ p
 // check of Eq. (2.4) from the binning partials.  One warp per entry.
 __global__ void k_k0_finalize(const double* __restrict__ part, int nblk, int P,
                               const double* __restrict__ K0, double* __restrict__ nu,
-                              const double* __restrict__ qred, int* __restrict__ status) {
+                              const double* __restrict__ qred, int nblk_q, int* __restrict__ status) {
   __shared__ double mu[kMaxCheb];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int n = warp; n < P; n += nw) {
@@ -1333,8 +1349,8 @@ __global__ void k_k0_finalize(const double* __restrict__ part, int nblk, int P,
     if (lane == 0) mu[n] = v;
   }
   if (warp == nw - 1 && qred) {
-    const double sq = warp_sum_partials(qred, nblk, 2, 0);
-    const double sa = warp_sum_partials(qred, nblk, 2, 1);
+    const double sq = warp_sum_partials(qred, nblk_q, 2, 0);
+    const double sa = warp_sum_partials(qred, nblk_q, 2, 1);
     if (lane == 0 && fabs(sq) > 1e-10 * sa) atomicOr(status, 1);
   }
   __syncthreads();
@@ -1349,28 +1365,32 @@ template <typename T>
 __global__ void k_k0_eval(const T* __restrict__ r, int N, int P, double halfLz,
                           const double* __restrict__ nu, double* __restrict__ phi_out,
                           double* __restrict__ grad_out) {
+  __shared__ double snu[kMaxCheb], scd[kMaxCheb];
+  for (int n = threadIdx.x; n < P; n += blockDim.x) {
+    snu[n] = nu[n];
+    scd[n] = n + 1 < P ? (double)(n + 1) * nu[n + 1] : 0.0;  // T_n' = n U_(n-1)
+  }
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double z = (double)r[3 * i + 2];
   if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
-  const double x = z / halfLz;
-  double t0 = 1.0, t1 = x, d0 = 0.0, d1 = 1.0;
-  double f = nu[0], fz = 0.0;
-  if (P > 1) {
-    f += nu[1] * x;
-    fz += nu[1];
+  const double ih = 1.0 / halfLz;
+  const double x = z * ih, x2 = 2.0 * x;
+  // Clenshaw: sum nu_n T_n(x) and sum (n+1) nu_(n+1) U_n(x)
+  double b1 = 0.0, b2 = 0.0, d1 = 0.0, d2 = 0.0;
+  for (int k = P - 1; k >= 1; --k) {
+    const double b0 = fma(x2, b1, snu[k] - b2);
+    b2 = b1;
+    b1 = b0;
+    const double d0 = fma(x2, d1, scd[k - 1] - d2);
+    d2 = d1;
+    d1 = d0;
   }
-  for (int n = 2; n < P; ++n) {
-    const double t2 = 2.0 * x * t1 - t0;
-    const double d2 = 2.0 * t1 + 2.0 * x * d1 - d0;
-    f += nu[n] * t2;
-    fz += nu[n] * d2;
-    t0 = t1; t1 = t2; d0 = d1; d1 = d2;
-  }
-  phi_out[i] = f;
+  phi_out[i] = fma(x, b1, snu[0] - b2);
   grad_out[3 * i] = 0.0;
   grad_out[3 * i + 1] = 0.0;
-  grad_out[3 * i + 2] = fz / halfLz;
+  grad_out[3 * i + 2] = d1 * ih;
 }
 
 // ---------------------------------------------------------------------------
@@ -1610,7 +1630,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
         k_long_spread_small<T, 64><<<p->long_small_blocks, 256, 0, s>>>(I0, I1, w, P, rl, N, part);
       LAUNCH_CHECK();
       const int tot = P * I0 * I1;
-      k_long_reduce<T><<<(tot + 255) / 256, 256, 0, s>>>(
+      k_long_reduce<T><<<(8 * tot + 255) / 256, 256, 0, s>>>(
           reinterpret_cast<const T*>(p->d_long_partial), p->long_small_blocks, I0, I1, P, A);
       LAUNCH_CHECK();
     } else {
@@ -1645,14 +1665,14 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     mark_begin(p, 8, s);
     double* mpart = p->d_red + 2 * kRedBlocks;
     if (P <= 16)
-      k_k0_moments<T, 16><<<kRedBlocks, 256, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+      k_k0_moments<T, 16><<<kK0Blocks, kK0Threads, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
     else if (P <= 32)
-      k_k0_moments<T, 32><<<kRedBlocks, 256, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+      k_k0_moments<T, 32><<<kK0Blocks, kK0Threads, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
     else
-      k_k0_moments<T, 64><<<kRedBlocks, 256, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+      k_k0_moments<T, 64><<<kK0Blocks, kK0Threads, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
     LAUNCH_CHECK();
-    k_k0_finalize<<<1, 1024, 0, s>>>(p->d_red + 2 * kRedBlocks, kRedBlocks, P, p->d_k0mat,
-                                     p->d_k0nu, p->d_red, p->d_status);
+    k_k0_finalize<<<1, 1024, 0, s>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, P, p->d_k0mat,
+                                     p->d_k0nu, p->d_red, kRedBlocks, p->d_status);
     LAUNCH_CHECK();
     k_k0_eval<T><<<(N + 255) / 256, 256, 0, s>>>(r, N, P, 0.5 * m.L[2], p->d_k0nu,
                                                 pp + 3 * (size_t)N, pg + 9 * (size_t)N);
@@ -1661,8 +1681,8 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   } else {
     SOG_CK(cudaMemsetAsync(pp + 2 * (size_t)N, 0, sizeof(double) * 2 * N, s));
     SOG_CK(cudaMemsetAsync(pg + 6 * (size_t)N, 0, sizeof(double) * 6 * N, s));
-    k_k0_finalize<<<1, 1024, 0, s>>>(p->d_red + 2 * kRedBlocks, kRedBlocks, 0, p->d_k0mat,
-                                     p->d_k0nu, p->d_red, p->d_status);
+    k_k0_finalize<<<1, 1024, 0, s>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, 0, p->d_k0mat,
+                                     p->d_k0nu, p->d_red, kRedBlocks, p->d_status);
     LAUNCH_CHECK();
   }
 
