@@ -38,7 +38,13 @@ WORKLOADS = {
                desc="uniform neutral +-1 charges, N=1e3, box 10x10x10, tol 1e-6"),
 }
 FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2, written between steps
-PAIR_FLOP = 50                   # FP32 operations per near-field pair
+# FP32 operations of the near field: 8 per candidate of the 27-cell
+# neighbourhood (3 differences, squared distance, comparison) and 60 per pair
+# inside r_c (distance again, reciprocal square root, degree-8 table
+# polynomial with its derivative, compensated potential sum, force).
+CAND_FLOP = 8
+PAIR_FLOP = 60
+DOMINANT = "near"   # largest share of GPU time in the kernel launch list
 
 
 def peaks():
@@ -97,21 +103,66 @@ class ClockSampler:
 
 
 def stage_units(prm, N, stage):
-    """Algorithmic work of one stage launch and its bound."""
+    """Algorithmic work of one launch of a stage and the resource bounding it:
+    ("alu", FP32 operations) or ("hbm", bytes), with a description."""
     Ix, Iy, Iz = prm["I"]
     P = prm["P_win"]
-    rho = N / (prm["L"][0] * prm["L"][1] * prm["L"][2])
+    L = prm["L"]
+    rho = N / (L[0] * L[1] * L[2])
     pairs = N * 4.0 / 3.0 * math.pi * prm["rc"] ** 3 * rho
+    ncell = [max(1, int(math.floor(L[d] / prm["rc"]))) for d in range(3)]
+    cand = N * 27.0 * N / (ncell[0] * ncell[1] * ncell[2])
     if stage == "near":
-        return "alu", pairs * PAIR_FLOP, "FP32 flop: %.3g pairs x %d" % (pairs, PAIR_FLOP)
+        return ("alu", cand * CAND_FLOP + pairs * PAIR_FLOP,
+                "FP32 flop: %.3g candidates x %d + %.3g pairs x %d" % (cand, CAND_FLOP, pairs, PAIR_FLOP))
     if stage == "mid_spread":
         return "alu", N * P ** 3 * 2.0, "FP32 flop: N x P^3 x 2"
     if stage == "mid_gather":
-        return "alu", N * P ** 3 * 4.0, "FP32 flop: N x P^3 x 4"
+        return "alu", N * P ** 3 * 4.0, "FP32 flop: N x P^3 x 4 (value and x-derivative sums)"
     if stage == "mid_fft":
-        cplx = Iz * Iy * (Ix // 2 + 1) * 8
-        return "hbm", 5 * 2 * cplx, "bytes: 5 passes x (read + write) of the half spectrum"
+        half = Iz * Iy * (Ix // 2 + 1)
+        return ("hbm", 3 * 2 * half * 8 + half * 4,
+                "bytes: 3 passes x (read + write) of the complex half spectrum + scaling table")
+    if stage == "long_gather":
+        Pl, Pc = prm["P_long"], prm["P_cheb"]
+        return "alu", N * Pc * Pl ** 2 * 4.0, "FP32 flop: N x P_cheb x P_long^2 x 4"
+    if stage == "long_spread":
+        Pc = prm["P_cheb"]
+        Ilx, Ily = prm["I_long"]
+        return "alu", N * Pc * Ilx * Ily * 2.0, "FP32 flop: N x P_cheb x I_long^2 x 2 (dense planes)"
     return None, None, None
+
+
+def roofline_entry(prm, N, stage, t_s, hbm, fp32_peak, smax, src):
+    bound, work, desc = stage_units(prm, N, stage)
+    if bound == "alu":
+        ach = work / t_s / 1e12
+        return {"bound": "alu", "kernel": stage, "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "work_per_launch": desc,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
+    if bound == "hbm":
+        ach = work / t_s / 1e9
+        return {"bound": "hbm", "kernel": stage, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "work_per_launch": desc, "peak_source": src}
+    return None
+
+
+def recorded_traffic(stage):
+    """DRAM bytes per launch recorded by an ncu capture of the current kernel
+    source (profiles/<stage>_traffic.txt: 'source_sha256 <hex>' and
+    'dram_bytes <n>'); None when absent or taken on another version."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "%s_traffic.txt" % stage)
+    try:
+        rec = dict(line.split(None, 1) for line in open(path).read().splitlines() if line.strip()
+                   and not line.startswith("#"))
+        src = os.path.join(ROOT, "paper_2412_04595_gb300", "csrc", "sog_kernels.cu")
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256", "").strip() != sha:
+            return None
+        return float(rec["dram_bytes"])
+    except Exception:
+        return None
 
 
 def run_ours(args, wl, rank, world):
@@ -185,12 +236,15 @@ def run_ours(args, wl, rank, world):
     plan.set_timing(False)
     for _ in range(2):
         plan.eval_host(qh, rh, phih, Eh, Fh)
-    t0 = time.perf_counter()
+    e2e_s = 0.0
     for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         st = plan.eval_host(qh, rh, phih, Eh, Fh)
+        e2e_s += time.perf_counter() - t0
         if st != 0:
             raise RuntimeError("sog_eval_host status %d" % st)
-    e2e_s = time.perf_counter() - t0
     es = q.dtype.itemsize
     e2e = {"value": N * args.steps / e2e_s, "unit": "particles/s",
            "h2d_bytes_per_step": int(N * 4 * es), "d2h_bytes_per_step": int(N * 4 * es + 8)}
@@ -217,8 +271,8 @@ def emit(d):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
@@ -277,20 +331,12 @@ def main():
     N = wl["N"]
     hbm, smax, src = peaks()
     fp32_peak = 152 * 128 * 2 * smax * 1e6 / 1e12          # TFLOP/s at the max SM clock
-    dom = max(res["stage_ms"], key=res["stage_ms"].get)
-    bound, work, work_desc = stage_units(prm, N, dom)
-    t_dom = res["stage_ms"][dom] * 1e-3
-    roof = None
-    if bound == "alu":
-        ach = work / t_dom / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None, "work_per_launch": work_desc,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
-    elif bound == "hbm":
-        ach = work / t_dom / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "work_per_launch": work_desc,
-                "peak_source": src}
+    dom = DOMINANT if DOMINANT in res["stage_ms"] else max(res["stage_ms"], key=res["stage_ms"].get)
+    roof = roofline_entry(prm, N, dom, res["stage_ms"][dom] * 1e-3, hbm, fp32_peak, smax, src)
+    if roof is not None:
+        roof["traffic"] = recorded_traffic(dom)
+    others = [roofline_entry(prm, N, k, v * 1e-3, hbm, fp32_peak, smax, src)
+              for k, v in res["stage_ms"].items() if k != dom and v > 0]
     line = {"metric": METRIC, "value": res["value"], "unit": "particles/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
@@ -298,6 +344,7 @@ def main():
             "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic", "config": config, "e2e": res["e2e"],
             "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": roof,
+            "roofline_stages": [o for o in others if o is not None],
             "stage_ms": {k: round(v, 5) for k, v in res["stage_ms"].items()},
             "params": {k: prm[k] for k in ("rc", "M", "m", "I", "P_win", "I_long", "P_cheb")}}
     if not args.no_cpu_baseline:
