@@ -61,6 +61,14 @@ struct LineSet {
   bool line_fast;
 };
 
+// a / sqrt(2) to within the rounding of the result
+__device__ __forceinline__ float div_sqrt2(float a) {
+  return fmaf(a, 0.70710676908493042f, a * 1.2101617e-8f);
+}
+__device__ __forceinline__ double div_sqrt2(double a) {
+  return fma(a, 0.70710678118654746, a * 6.2685835895251089e-17);
+}
+
 template <typename T2, int R>
 __device__ __forceinline__ void dft(T2* x, bool inv, const T2* tw, int n) {
   if (R == 2) {
@@ -79,14 +87,15 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T2* tw, int n) {
     T2 e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
     dft<T2, 4>(e, inv, tw, n);
     dft<T2, 4>(o, inv, tw, n);
-    using T = decltype(e[0].x);
-    const T h = (T)0.70710678118654752440;
-    // w8^1 = (1 - i)/sqrt2 forward, (1 + i)/sqrt2 inverse; w8^2 = -i / +i
-    const T2 o1 = inv ? T2{h * (o[1].x - o[1].y), h * (o[1].x + o[1].y)}
-                      : T2{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};
+    // w8^1 = (1 - i)/sqrt2 forward, (1 + i)/sqrt2 inverse; w8^2 = -i / +i.
+    // 1/sqrt2 is applied as a rounded value plus its rounding error (no
+    // floating-point number h has 2 h^2 = 1, and a biased rotation would
+    // shrink every transform by a few 1e-8).
+    const T2 o1 = inv ? T2{div_sqrt2(o[1].x - o[1].y), div_sqrt2(o[1].x + o[1].y)}
+                      : T2{div_sqrt2(o[1].x + o[1].y), div_sqrt2(o[1].y - o[1].x)};
     const T2 o2 = rot(o[2], inv);
-    const T2 o3 = inv ? T2{-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y)}
-                      : T2{h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};
+    const T2 o3 = inv ? T2{-div_sqrt2(o[3].x + o[3].y), div_sqrt2(o[3].x - o[3].y)}
+                      : T2{div_sqrt2(o[3].y - o[3].x), -div_sqrt2(o[3].x + o[3].y)};
     x[0] = cadd(e[0], o[0]);
     x[4] = csub(e[0], o[0]);
     x[1] = cadd(e[1], o1);

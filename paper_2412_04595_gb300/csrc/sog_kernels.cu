@@ -68,8 +68,6 @@ __device__ __forceinline__ double dceil(double x) { return ceil(x); }
 __device__ __forceinline__ float drint(float x) { return rintf(x); }
 __device__ __forceinline__ double drint(double x) { return rint(x); }
 __device__ __forceinline__ float drsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ float ddiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double ddiv(double a, double b) { return a / b; }
 __device__ __forceinline__ double drsqrt(double x) { return rsqrt(x); }
 
 // Window phi(v) (v = offset / half-width) and d phi / dv; zero outside |v| <= 1.
@@ -84,7 +82,7 @@ __device__ __forceinline__ void win_eval(const WinT<T>& w, T v, T& val, T& dval)
     // no cancellation near the window centre, where the weights are largest
     const T a2 = (one - v) * (one + v);
     const T a = dsqrt(a2);
-    val = dexp(-w.shape * ddiv(v * v, one + a));
+    val = dexp(-w.shape * (v * v / (one + a)));
     if (a2 > T(0)) dval = -val * w.shape * v * drsqrt(a2);
   } else {
     val = dexp(-w.shape * v * v);

@@ -319,6 +319,17 @@ struct WinFT {
   }
 };
 
+// The window the kernels apply, phi((g - x) / half) with the shape and
+// 1/half rounded to the element type: its transform (which the scaling
+// tables divide by) is taken with the same rounded values, so that a plan
+// in FP32 deconvolves exactly the window it spreads with.
+double eff_shape(double shape, int prec) {
+  return prec == SOG_PREC_MIXED ? (double)(float)shape : shape;
+}
+double eff_half(double half, int prec) {
+  return prec == SOG_PREC_MIXED ? 1.0 / (double)(float)(1.0 / half) : half;
+}
+
 // Near kernel table: g(r) = 1 - r F_M(r) on [0, rc], K intervals, degree D
 // monomials in u = 2 (r - r_k)/(rc/K) - 1 (fitted at Chebyshev points).
 bool near_table(const std::vector<double>& w, const std::vector<double>& s, double rc, int D,
@@ -600,9 +611,10 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   std::vector<double> mult;
   if (p->has_mid) {
     const int C = Ix / 2 + 1;
-    WinFT fx(prm.window, prm.shape, p->wm.half * p->h[0]);
-    WinFT fy(prm.window, prm.shape, p->wm.half * p->h[1]);
-    WinFT fz(prm.window, prm.shape, p->wm.half * p->h[2]);
+    const double shp = eff_shape(prm.shape, prec), hw = eff_half(p->wm.half, prec);
+    WinFT fx(prm.window, shp, hw * p->h[0]);
+    WinFT fy(prm.window, shp, hw * p->h[1]);
+    WinFT fz(prm.window, shp, hw * p->h[2]);
     std::vector<double> kx(C), ky(Iy), kz(Iz), Wx(C), Wy(Iy), Wz(Iz);
     for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
     for (int f = 0; f < Iy; ++f) { ky[f] = 2.0 * kPi * std::min(f, Iy - f) / L[1]; Wy[f] = fy(ky[f]); }
@@ -670,8 +682,9 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
       delete p;
       return SOG_ERR_PARAMS;
     }
-    WinFT fx(prm.window, prm.shape_long, p->wl.half * p->hl[0]);
-    WinFT fy(prm.window, prm.shape_long, p->wl.half * p->hl[1]);
+    const double shp = eff_shape(prm.shape_long, prec), hw = eff_half(p->wl.half, prec);
+    WinFT fx(prm.window, shp, hw * p->hl[0]);
+    WinFT fy(prm.window, shp, hw * p->hl[1]);
     std::vector<double> Wx(C), Wy(Ily), kx(C), ky(Ily);
     for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
     for (int f = 0; f < Ily; ++f) { ky[f] = 2.0 * kPi * std::min(f, Ily - f) / L[1]; Wy[f] = fy(ky[f]); }
