@@ -486,38 +486,51 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
     for (int i = threadIdx.x; i < ntab; i += blockDim.x) stab[i] = tab[i];
   const bool periodic_cells = g.nc[0] >= 3 && g.nc[1] >= 3;
   const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
-  if (threadIdx.x == 0) {
-    int lo[3], hi[3];
+  if (threadIdx.x < 32) {
+    // warp 0: one lane per neighbouring cell (x fastest, then y, then z)
+    const int lane = threadIdx.x;
     const int cc[3] = {cx, cy, cz};
+    int lo[3], ext[3];
     for (int d = 0; d < 2; ++d) {
-      if (g.nc[d] >= 3) { lo[d] = cc[d] - 1; hi[d] = cc[d] + 1; }
-      else { lo[d] = 0; hi[d] = g.nc[d] - 1; }
+      if (g.nc[d] >= 3) { lo[d] = cc[d] - 1; ext[d] = 3; }
+      else { lo[d] = 0; ext[d] = g.nc[d]; }
     }
     lo[2] = max(cz - 1, 0);
-    hi[2] = min(cz + 1, g.nc[2] - 1);
-    int n = 0, off = 0, anys = 0;
-    for (int z = lo[2]; z <= hi[2]; ++z)
-      for (int y0 = lo[1]; y0 <= hi[1]; ++y0)
-        for (int x0 = lo[0]; x0 <= hi[0]; ++x0) {
-          const int y = (y0 + g.nc[1]) % g.nc[1], x = (x0 + g.nc[0]) % g.nc[0];
-          const int k = (z * g.nc[1] + y) * g.nc[0] + x;
-          cb[n] = cstart[k];
-          coff[n] = off;
-          // source beyond the -L/2 edge sits near +L/2: s = +L/2, and vice versa
-          float sx = 0.f, sy = 0.f;
-          if (periodic_cells) {
-            sx = x0 < 0 ? (float)g.halfL[0] : (x0 >= g.nc[0] ? (float)(-g.halfL[0]) : 0.f);
-            sy = y0 < 0 ? (float)g.halfL[1] : (y0 >= g.nc[1] ? (float)(-g.halfL[1]) : 0.f);
-          }
-          csx[n] = sx;
-          csy[n] = sy;
-          anys |= (sx != 0.f || sy != 0.f);
-          off += cstart[k + 1] - cstart[k];
-          ++n;
-        }
-    coff[n] = off;
-    ncell = n;
-    any_shift = anys;
+    ext[2] = min(cz + 1, g.nc[2] - 1) - lo[2] + 1;
+    const int n = ext[0] * ext[1] * ext[2];
+    int cnt = 0, st = 0;
+    float sx = 0.f, sy = 0.f;
+    if (lane < n) {
+      const int ix = lane % ext[0], iy = (lane / ext[0]) % ext[1], iz = lane / (ext[0] * ext[1]);
+      const int x0 = lo[0] + ix, y0 = lo[1] + iy, z = lo[2] + iz;
+      const int y = (y0 + g.nc[1]) % g.nc[1], x = (x0 + g.nc[0]) % g.nc[0];
+      const int k = (z * g.nc[1] + y) * g.nc[0] + x;
+      st = cstart[k];
+      cnt = cstart[k + 1] - st;
+      // source beyond the -L/2 edge sits near +L/2: s = +L/2, and vice versa
+      if (periodic_cells) {
+        sx = x0 < 0 ? (float)g.halfL[0] : (x0 >= g.nc[0] ? (float)(-g.halfL[0]) : 0.f);
+        sy = y0 < 0 ? (float)g.halfL[1] : (y0 >= g.nc[1] ? (float)(-g.halfL[1]) : 0.f);
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const bool anys = __any_sync(0xffffffffu, sx != 0.f || sy != 0.f);
+    if (lane < n) {
+      cb[lane] = st;
+      coff[lane] = incl - cnt;
+      csx[lane] = sx;
+      csy[lane] = sy;
+    }
+    if (lane == n - 1) coff[n] = incl;
+    if (lane == 0) {
+      ncell = n;
+      any_shift = anys;
+    }
   }
   __syncthreads();
   const T* tb_ = tab_sm ? stab : tab;
@@ -535,21 +548,22 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
     const int ns = min(kNearSrc, nsrc - s0);
     const int nsteps = (ns + 31) >> 5;
     __syncthreads();
-    for (int k = threadIdx.x; k < nsteps * 32; k += blockDim.x) {
-      if (k < ns) {
-        const int gk = s0 + k;
-        int cc = 0;
-        while (coff[cc + 1] <= gk) ++cc;
-        P4<T> b = rec[cb[cc] + gk - coff[cc]];
-        const float sx = csx[cc], sy = csy[cc];
+    // a warp per neighbouring cell copies the part of it inside this pass
+    for (int cc = warp; cc < ncell; cc += nw) {
+      const int a0 = max(coff[cc], s0), a1 = min(coff[cc + 1], s0 + ns);
+      const float sx = csx[cc], sy = csy[cc];
+      const int shift = cb[cc] - coff[cc];
+      for (int gk = a0 + lane; gk < a1; gk += 32) {
+        P4<T> b = rec[gk + shift];
         b.x = b.x - (T)sx;
         b.y = b.y - (T)sy;
-        src[k] = b;
-        shs[k] = make_float2(sx, sy);
-      } else {
-        src[k] = P4<T>{T(1e30), T(1e30), T(1e30), T(0)};
-        shs[k] = make_float2(0.f, 0.f);
+        src[gk - s0] = b;
+        shs[gk - s0] = make_float2(sx, sy);
       }
+    }
+    for (int k = ns + threadIdx.x; k < nsteps * 32; k += blockDim.x) {
+      src[k] = P4<T>{T(1e30), T(1e30), T(1e30), T(0)};
+      shs[k] = make_float2(0.f, 0.f);
     }
     __syncthreads();
     for (int t0 = 0; t0 < ntg; t0 += nw) {
