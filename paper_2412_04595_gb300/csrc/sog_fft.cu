@@ -29,9 +29,9 @@ template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; };
 template <> struct C2<double> { using t = double2; };
 
-constexpr int kFftThreads = 512;
+constexpr int kFftThreads = 1024;
 template <typename T> struct FftCap;
-template <> struct FftCap<float> { static constexpr int v = 16; };
+template <> struct FftCap<float> { static constexpr int v = 10; };
 template <> struct FftCap<double> { static constexpr int v = 8; };
 
 template <typename T2>
