@@ -152,11 +152,12 @@ struct sog_plan {
   cudaEvent_t ev[2 * SOG_NSTAGES];   // start and end of each stage
   int ev_used[2 * SOG_NSTAGES];
   int64_t launches;
-  // captured evaluations replayed with one cudaGraphLaunch; the near field
-  // runs on side_stream concurrently with the mid and long ranges
+  // captured evaluations replayed with one cudaGraphLaunch; after the
+  // binning the near field (side_stream) and the long range (long_stream)
+  // run concurrently with the mid range
   cudaStream_t cap_stream;
-  cudaStream_t side_stream;
-  cudaEvent_t ev_fork, ev_join;
+  cudaStream_t side_stream, long_stream;
+  cudaEvent_t ev_fork, ev_join, ev_join_long;
   sogk::GraphEntry graphs[sogk::kMaxGraphs];
   int n_graphs;
   uint64_t use_clock;

@@ -1624,9 +1624,11 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     SOG_CK(cudaMemsetAsync(pg + 3 * (size_t)N, 0, sizeof(double) * 3 * N, s));
   }
 
-  // 4-5. long range and its k = 0 mode
+  // 4-5. long range and its k = 0 mode, on long_stream
+  const cudaStream_t sl = p->long_stream;
+  SOG_CK(cudaStreamWaitEvent(sl, p->ev_fork, 0));
   if (p->has_long) {
-    mark_begin(p, 5, s);
+    mark_begin(p, 5, sl);
     const int P = m.P_cheb;
     T* A = reinterpret_cast<T*>(p->d_lA);
     T* B = reinterpret_cast<T*>(p->d_lB);
@@ -1635,71 +1637,74 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
       const int I0 = m.I_long[0], I1 = m.I_long[1];
       T* part = reinterpret_cast<T*>(p->d_long_partial);
       if (P <= 16)
-        k_long_spread_small<T, 16><<<p->long_small_blocks, 256, 0, s>>>(I0, I1, w, P, rl, N, part);
+        k_long_spread_small<T, 16><<<p->long_small_blocks, 256, 0, sl>>>(I0, I1, w, P, rl, N, part);
       else if (P <= 32)
-        k_long_spread_small<T, 32><<<p->long_small_blocks, 256, 0, s>>>(I0, I1, w, P, rl, N, part);
+        k_long_spread_small<T, 32><<<p->long_small_blocks, 256, 0, sl>>>(I0, I1, w, P, rl, N, part);
       else
-        k_long_spread_small<T, 64><<<p->long_small_blocks, 256, 0, s>>>(I0, I1, w, P, rl, N, part);
+        k_long_spread_small<T, 64><<<p->long_small_blocks, 256, 0, sl>>>(I0, I1, w, P, rl, N, part);
       LAUNCH_CHECK();
       const int tot = P * I0 * I1;
-      k_long_reduce<T><<<(8 * tot + 255) / 256, 256, 0, s>>>(
+      k_long_reduce<T><<<(8 * tot + 255) / 256, 256, 0, sl>>>(
           reinterpret_cast<const T*>(p->d_long_partial), p->long_small_blocks, I0, I1, P, A);
       LAUNCH_CHECK();
     } else {
       const size_t pbytes = (size_t)P * m.I_long[1] * (m.I_long[0] + 2) * sizeof(T);
-      SOG_CK(cudaMemsetAsync(A, 0, pbytes, s));
+      SOG_CK(cudaMemsetAsync(A, 0, pbytes, sl));
       const size_t sm = long_smem(p, sizeof(T), false);
       const dim3 lgrid(p->n_tiles_long, p->gl.chunks);
-      SOG_DISPATCH_PW(p->wl.P, k_long_spread, lgrid, sm, s, p->gl, w, P, rl, p->d_cnt + off.z, A);
+      SOG_DISPATCH_PW(p->wl.P, k_long_spread, lgrid, sm, sl, p->gl, w, P, rl, p->d_cnt + off.z, A);
       LAUNCH_CHECK();
     }
-    mark_end(p, 5, s);
-    mark_begin(p, 6, s);
+    mark_end(p, 5, sl);
+    mark_begin(p, 6, sl);
     int nl = 0;
-    SOG_CK(fft_long_pass<T>(p, false, s, nl));
+    SOG_CK(fft_long_pass<T>(p, false, sl, nl));
     const int C = m.I_long[0] / 2 + 1;
     const int modes = m.I_long[1] * C;
     const int per = 256 / P;
-    k_long_contract<T><<<(modes + per - 1) / per, 256, 0, s>>>(
+    k_long_contract<T><<<(modes + per - 1) / per, 256, 0, sl>>>(
         A, B, reinterpret_cast<const T*>(p->d_kmat), P, m.I_long[1], C);
     LAUNCH_CHECK();
-    SOG_CK(fft_long_pass<T>(p, true, s, nl));
+    SOG_CK(fft_long_pass<T>(p, true, sl, nl));
     p->launches += nl;
-    mark_end(p, 6, s);
-    mark_begin(p, 7, s);
+    mark_end(p, 6, sl);
+    mark_begin(p, 7, sl);
     const size_t sm2 = long_smem(p, sizeof(T), true);
     const double3 sc = make_double3(1.0 / p->hl[0], 1.0 / p->hl[1], 2.0 / m.L[2]);
     const dim3 lgrid2(p->n_tiles_long, p->gl.chunks);
-    SOG_DISPATCH_PW(p->wl.P, k_long_gather, lgrid2, sm2, s, p->gl, w, P, rl, p->d_cnt + off.z,
+    SOG_DISPATCH_PW(p->wl.P, k_long_gather, lgrid2, sm2, sl, p->gl, w, P, rl, p->d_cnt + off.z,
                     p->d_perm + 2 * (size_t)N, B, sc, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     LAUNCH_CHECK();
-    mark_end(p, 7, s);
-    mark_begin(p, 8, s);
+    mark_end(p, 7, sl);
+    mark_begin(p, 8, sl);
     double* mpart = p->d_red + 2 * kRedBlocks;
     if (P <= 16)
-      k_k0_moments<T, 16><<<kK0Blocks, kK0Threads, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+      k_k0_moments<T, 16><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, 0.5 * m.L[2], mpart);
     else if (P <= 32)
-      k_k0_moments<T, 32><<<kK0Blocks, kK0Threads, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+      k_k0_moments<T, 32><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, 0.5 * m.L[2], mpart);
     else
-      k_k0_moments<T, 64><<<kK0Blocks, kK0Threads, 0, s>>>(q, r, N, P, 0.5 * m.L[2], mpart);
+      k_k0_moments<T, 64><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, 0.5 * m.L[2], mpart);
     LAUNCH_CHECK();
-    k_k0_finalize<<<1, 1024, 0, s>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, P, p->d_k0mat,
+    k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, P, p->d_k0mat,
                                      p->d_k0nu, p->d_red, kRedBlocks, p->d_status);
     LAUNCH_CHECK();
-    k_k0_eval<T><<<(N + 255) / 256, 256, 0, s>>>(r, N, P, 0.5 * m.L[2], p->d_k0nu,
+    k_k0_eval<T><<<(N + 255) / 256, 256, 0, sl>>>(r, N, P, 0.5 * m.L[2], p->d_k0nu,
                                                 pp + 3 * (size_t)N, pg + 9 * (size_t)N);
     LAUNCH_CHECK();
-    mark_end(p, 8, s);
+    mark_end(p, 8, sl);
   } else {
-    SOG_CK(cudaMemsetAsync(pp + 2 * (size_t)N, 0, sizeof(double) * 2 * N, s));
-    SOG_CK(cudaMemsetAsync(pg + 6 * (size_t)N, 0, sizeof(double) * 6 * N, s));
-    k_k0_finalize<<<1, 1024, 0, s>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, 0, p->d_k0mat,
+    SOG_CK(cudaMemsetAsync(pp + 2 * (size_t)N, 0, sizeof(double) * 2 * N, sl));
+    SOG_CK(cudaMemsetAsync(pg + 6 * (size_t)N, 0, sizeof(double) * 6 * N, sl));
+    k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, 0, p->d_k0mat,
                                      p->d_k0nu, p->d_red, kRedBlocks, p->d_status);
     LAUNCH_CHECK();
   }
 
-  // join the near field, then 6. assembly
+  SOG_CK(cudaEventRecord(p->ev_join_long, sl));
+
+  // join the near field and the long range, then 6. assembly
   SOG_CK(cudaStreamWaitEvent(s, p->ev_join, 0));
+  SOG_CK(cudaStreamWaitEvent(s, p->ev_join_long, 0));
   mark_begin(p, 9, s);
   if (phi || F || E) {
     double* epart = p->d_red + 2 * kRedBlocks + (size_t)kRedBlocks * kMaxCheb;

@@ -820,8 +820,10 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   }
   if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&p->long_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_join_long, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(base);
     delete p;
@@ -939,8 +941,10 @@ void sog_plan_destroy(sog_plan* plan) {
   sogk::release_graphs(plan);
   cudaStreamDestroy(plan->cap_stream);
   cudaStreamDestroy(plan->side_stream);
+  cudaStreamDestroy(plan->long_stream);
   cudaEventDestroy(plan->ev_fork);
   cudaEventDestroy(plan->ev_join);
+  cudaEventDestroy(plan->ev_join_long);
   cudaFree(plan->arena);
   delete plan;
 }
