@@ -193,6 +193,37 @@ sog_status sog_plan_get_timing(sog_plan* plan, float* ms);
 int64_t sog_plan_launches(const sog_plan* plan);
 
 /*
+ * Batches of independent systems (row "batching" of the hot path; the paper
+ * evaluates one system at a time).  Each system i has its own plan, with
+ * parameters selected for (N[i], L[3i..3i+2], tol[i]); one sog_batch_eval
+ * replays all systems' evaluations as one CUDA graph, the systems running
+ * concurrently.
+ *   sog_batch_create: nsys >= 1; N [nsys], L [nsys x 3], tol [nsys] host
+ *     arrays; opts as for sog_plan_create (opts->manual must be NULL).
+ *     Returns the first failing plan's status.  *batch owned by the caller.
+ *   sog_batch_eval: q, r, phi, F are host arrays of nsys device pointers
+ *     (each as in sog_eval for its system; phi and F may be NULL arrays, or
+ *     hold NULL entries only if all systems do the same across calls); E is
+ *     a device array of nsys doubles or NULL.  Enqueued on `stream`.  The
+ *     graph is captured on the first call and reused while the pointers stay
+ *     the same (a change of pointers re-captures it).
+ *   sog_batch_check: waits, returns the first data status of any system (as
+ *     sog_plan_check) and its index in *first_bad (-1 if none; may be NULL).
+ *   sog_batch_plan: the plan of system i (owned by the batch), e.g. for
+ *     sog_plan_get_params; NULL if out of range.
+ */
+typedef struct sog_batch sog_batch;
+sog_status sog_batch_create(sog_batch** batch, int32_t nsys, const int64_t* N, const double* L,
+                            const double* tol, const sog_opts* opts);
+sog_status sog_batch_eval(sog_batch* batch, const void* const* q, const void* const* r,
+                          void* const* phi, double* E, void* const* F, void* stream);
+sog_status sog_batch_check(sog_batch* batch, int32_t* first_bad);
+int32_t sog_batch_size(const sog_batch* batch);
+sog_plan* sog_batch_plan(sog_batch* batch, int32_t i);
+int64_t sog_batch_launches(const sog_batch* batch);
+void sog_batch_destroy(sog_batch* batch);
+
+/*
  * Assembly of Phi, F and U from the four parts that sog_eval_components
  * returns, with no plan and no memory allocation.  The paper has no
  * counterpart: it is a library convenience for callers that must not allocate

@@ -94,9 +94,23 @@ def load(build_if_missing: bool = False):
     L.sog_status_str.restype = ctypes.c_char_p
     L.sog_assemble_noalloc.argtypes = [i64, i32, ctypes.POINTER(SogParams), vp, vp, vp, vp, vp,
                                        vp, vp]
+    pa = ctypes.POINTER(vp)
+    L.sog_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i64),
+                                   ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(SogOpts)]
+    L.sog_batch_eval.argtypes = [vp, pa, pa, pa, vp, pa, vp]
+    L.sog_batch_check.argtypes = [vp, ctypes.POINTER(i32)]
+    L.sog_batch_size.argtypes = [vp]
+    L.sog_batch_size.restype = i32
+    L.sog_batch_plan.argtypes = [vp, i32]
+    L.sog_batch_plan.restype = vp
+    L.sog_batch_launches.argtypes = [vp]
+    L.sog_batch_launches.restype = i64
+    L.sog_batch_destroy.argtypes = [vp]
+    L.sog_batch_destroy.restype = None
     for f in ("sog_select_params", "sog_plan_create", "sog_plan_get_params", "sog_eval",
               "sog_eval_components", "sog_eval_host", "sog_plan_check", "sog_plan_set_timing",
-              "sog_plan_get_timing", "sog_assemble_noalloc"):
+              "sog_plan_get_timing", "sog_assemble_noalloc", "sog_batch_create", "sog_batch_eval",
+              "sog_batch_check"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -249,6 +263,75 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.sog_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns one ``sog_batch``: independent systems evaluated by one graph
+    launch.  ``systems`` is a list of (N, (Lx, Ly, Lz)); ``tol`` a float or a
+    list.  Tensors are contiguous CUDA tensors of the batch's dtype."""
+
+    def __init__(self, systems, tol, precision=SOG_PREC_MIXED, window=SOG_WIN_ES, n_nb=None):
+        self._lib = load()
+        n = len(systems)
+        tols = list(tol) if hasattr(tol, "__len__") else [float(tol)] * n
+        Ns = (ctypes.c_int64 * n)(*[int(s[0]) for s in systems])
+        Ls = (ctypes.c_double * (3 * n))(*[float(x) for s in systems for x in s[1]])
+        Ts = (ctypes.c_double * n)(*tols)
+        o = _opts(precision, window, n_nb, None)
+        h = ctypes.c_void_p()
+        _check(self._lib.sog_batch_create(ctypes.byref(h), n, Ns, Ls, Ts, ctypes.byref(o)),
+               "sog_batch_create")
+        self._h = h
+        self.size = n
+        self.precision = precision
+        self.params = []
+        for i in range(n):
+            out = SogParams()
+            _check(self._lib.sog_plan_get_params(self._lib.sog_batch_plan(h, i), ctypes.byref(out)),
+                   "sog_plan_get_params")
+            self.params.append(out.to_dict())
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == SOG_PREC_FP64 else torch.float32
+
+    def eval(self, q, r, phi=None, E=None, F=None, stream=None):
+        """sog_batch_eval: q, r, phi, F are lists of per-system tensors; E one
+        float64 CUDA tensor of size nsys (or None)."""
+        n = self.size
+
+        def arr(ts):
+            if ts is None:
+                return None
+            for t in ts:
+                if t is not None and (not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous()):
+                    raise ValueError("expected contiguous CUDA %s tensors" % self.dtype)
+            return (ctypes.c_void_p * n)(*[t.data_ptr() if t is not None else None for t in ts])
+
+        if E is not None and (not E.is_cuda or E.dtype.itemsize != 8 or E.numel() < n):
+            raise ValueError("E must be a CUDA float64 tensor of size nsys")
+        _check(self._lib.sog_batch_eval(self._h, arr(q), arr(r), arr(phi), _ptr(E), arr(F),
+                                        _stream_ptr(stream)), "sog_batch_eval")
+
+    def check(self):
+        bad = ctypes.c_int32(-1)
+        st = int(self._lib.sog_batch_check(self._h, ctypes.byref(bad)))
+        return st, int(bad.value)
+
+    def launches(self) -> int:
+        return int(self._lib.sog_batch_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sog_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -518,6 +518,15 @@ cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s, int& laun
 template cudaError_t fft_long_pass<float>(const sog_plan*, bool, cudaStream_t, int&);
 template cudaError_t fft_long_pass<double>(const sog_plan*, bool, cudaStream_t, int&);
 
+// True when transforms of this length fit the engine (at least one line per
+// CTA; the x pass also needs its half spectrum to fit one CTA).
+bool fft_len_ok(int prec, const FftLen& f) {
+  const int cap = prec == SOG_PREC_FP64 ? FftCap<double>::v : FftCap<float>::v;
+  const size_t elem = prec == SOG_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  return f.n >= 2 && max_lines(f, cap) >= 1 && (f.n / 2 + 1) <= kFftThreads * (cap / 2) &&
+         (size_t)(f.n + std::max(f.n, f.n + 2)) * elem <= (size_t)kMaxDynSmem;
+}
+
 // Allow the FFT kernels the dynamic shared memory they may need (set once per
 // process before any launch or stream capture).
 template <typename T>

@@ -174,10 +174,15 @@ template <typename T>
 cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s, int& launches);
 template <typename T>
 cudaError_t fft_prepare();
+bool fft_len_ok(int prec, const FftLen& f);
 
 // One-time kernel attributes for the plan's element type (sog_kernels.cu).
 cudaError_t prepare_kernels(int prec);
 void release_graphs(sog_plan* p);
+// Enqueue one evaluation's kernels on s without a graph of the plan's own
+// (used while a batch of plans is being captured into one graph).
+cudaError_t enqueue_eval(sog_plan* p, const void* q, const void* r, void* phi, double* E, void* F,
+                         cudaStream_t s);
 
 // Evaluation driver (sog_kernels.cu).
 sog_status eval_device(sog_plan* p, const void* q, const void* r, void* phi, double* E, void* F,

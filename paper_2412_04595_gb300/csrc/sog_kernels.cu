@@ -342,6 +342,13 @@ __device__ __forceinline__ void inv_dist(double r2, double& rr, double& rinv) {
   rinv = 1.0 / rr;
 }
 
+// Periodic shift (x, y) of a staged source, in the element type (half box
+// lengths are exact in FP64, and rounded like the positions in FP32).
+template <typename T>
+struct alignas(2 * sizeof(T)) S2 {
+  T x, y;
+};
+
 // Position of the k-th (from 0) set bit of m; k < popc(m).
 __device__ __forceinline__ int nth_bit(unsigned m, int k) {
   int pos = 0;
@@ -392,7 +399,7 @@ __device__ __forceinline__ void near_pair(T r2, T q, T dx, T dy, T dz, const T* 
 // (dx = (x_i + s) - (x_j - s), both brackets exact).
 template <typename T, bool SHIFT>
 __device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restrict__ src,
-                                            const float2* __restrict__ sh, int nsteps, T rc2,
+                                            const S2<T>* __restrict__ sh, int nsteps, T rc2,
                                             const T* __restrict__ tab, int K, T hK, T ihK,
                                             unsigned* __restrict__ msk, T& o_phi, T& o_gx, T& o_gy,
                                             T& o_gz) {
@@ -401,9 +408,9 @@ __device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restr
   auto diff = [&](int k, T& dx, T& dy, T& dz, T& q) {
     const P4<T> b = src[k];
     if (SHIFT) {
-      const float2 s2 = sh[k];
-      dx = (a.x + (T)s2.x) - b.x;
-      dy = (a.y + (T)s2.y) - b.y;
+      const S2<T> s2 = sh[k];
+      dx = (a.x + s2.x) - b.x;
+      dy = (a.y + s2.y) - b.y;
     } else {
       dx = a.x - b.x;
       dy = a.y - b.y;
@@ -471,11 +478,11 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
                                                       double* __restrict__ grad_out) {
   constexpr int kNearSrc = NearCfg<T>::src, kNearTab = NearCfg<T>::tab;
   __shared__ P4<T> src[kNearSrc];                  // x - s, y - s, z, q
-  __shared__ float2 shs[kNearSrc];                 // s (periodic shift) per source
+  __shared__ S2<T> shs[kNearSrc];                  // s (periodic shift) per source
   __shared__ unsigned msk[kNearThreads / 32][kNearSrc / 32];  // accepted sources per step
   __shared__ T stab[kNearTab];
   __shared__ int cb[27], coff[28];
-  __shared__ float csx[27], csy[27];
+  __shared__ T csx[27], csy[27];
   __shared__ int ncell, any_shift;
   const int c = blockIdx.x;
   const int tb = cstart[c], te = cstart[c + 1];
@@ -499,7 +506,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
     ext[2] = min(cz + 1, g.nc[2] - 1) - lo[2] + 1;
     const int n = ext[0] * ext[1] * ext[2];
     int cnt = 0, st = 0;
-    float sx = 0.f, sy = 0.f;
+    T sx = T(0), sy = T(0);
     if (lane < n) {
       const int ix = lane % ext[0], iy = (lane / ext[0]) % ext[1], iz = lane / (ext[0] * ext[1]);
       const int x0 = lo[0] + ix, y0 = lo[1] + iy, z = lo[2] + iz;
@@ -509,8 +516,8 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
       cnt = cstart[k + 1] - st;
       // source beyond the -L/2 edge sits near +L/2: s = +L/2, and vice versa
       if (periodic_cells) {
-        sx = x0 < 0 ? (float)g.halfL[0] : (x0 >= g.nc[0] ? (float)(-g.halfL[0]) : 0.f);
-        sy = y0 < 0 ? (float)g.halfL[1] : (y0 >= g.nc[1] ? (float)(-g.halfL[1]) : 0.f);
+        sx = x0 < 0 ? (T)g.halfL[0] : (x0 >= g.nc[0] ? (T)(-g.halfL[0]) : T(0));
+        sy = y0 < 0 ? (T)g.halfL[1] : (y0 >= g.nc[1] ? (T)(-g.halfL[1]) : T(0));
       }
     }
     int incl = cnt;
@@ -519,7 +526,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
       const int v = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += v;
     }
-    const bool anys = __any_sync(0xffffffffu, sx != 0.f || sy != 0.f);
+    const bool anys = __any_sync(0xffffffffu, sx != T(0) || sy != T(0));
     if (lane < n) {
       cb[lane] = st;
       coff[lane] = incl - cnt;
@@ -551,19 +558,19 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
     // a warp per neighbouring cell copies the part of it inside this pass
     for (int cc = warp; cc < ncell; cc += nw) {
       const int a0 = max(coff[cc], s0), a1 = min(coff[cc + 1], s0 + ns);
-      const float sx = csx[cc], sy = csy[cc];
+      const T sx = csx[cc], sy = csy[cc];
       const int shift = cb[cc] - coff[cc];
       for (int gk = a0 + lane; gk < a1; gk += 32) {
         P4<T> b = rec[gk + shift];
         b.x = b.x - (T)sx;
         b.y = b.y - (T)sy;
         src[gk - s0] = b;
-        shs[gk - s0] = make_float2(sx, sy);
+        shs[gk - s0] = S2<T>{sx, sy};
       }
     }
     for (int k = ns + threadIdx.x; k < nsteps * 32; k += blockDim.x) {
       src[k] = P4<T>{T(1e30), T(1e30), T(1e30), T(0)};
-      shs[k] = make_float2(0.f, 0.f);
+      shs[k] = S2<T>{T(0), T(0)};
     }
     __syncthreads();
     for (int t0 = 0; t0 < ntg; t0 += nw) {
@@ -1740,6 +1747,13 @@ static cudaError_t eval_direct(sog_plan* p, const void* q, const void* r, void* 
     return eval_t<double>(p, (const double*)q, (const double*)r, (double*)phi, E, (double*)F, pp,
                           pg, s);
   return eval_t<float>(p, (const float*)q, (const float*)r, (float*)phi, E, (float*)F, pp, pg, s);
+}
+
+cudaError_t enqueue_eval(sog_plan* p, const void* q, const void* r, void* phi, double* E, void* F,
+                         cudaStream_t s) {
+  const cudaError_t e = eval_direct(p, q, r, phi, E, F, p->d_parts_phi, p->d_parts_grad, s);
+  p->last_stream = s;
+  return e;
 }
 
 void release_graphs(sog_plan* p) {

@@ -598,6 +598,12 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     add_len(Ily, p->fly);
   }
   if (tw.empty()) tw.assign(2, 0.0);
+  if ((p->has_mid && !(sogk::fft_len_ok(prec, p->fx) && sogk::fft_len_ok(prec, p->fy) &&
+                       sogk::fft_len_ok(prec, p->fz))) ||
+      (p->has_long && !(sogk::fft_len_ok(prec, p->flx) && sogk::fft_len_ok(prec, p->fly)))) {
+    delete p;
+    return SOG_ERR_PARAMS;  // a grid dimension too long for the shared-memory FFT
+  }
 
   // near table
   p->near_D = sogk::kNearD;
