@@ -25,9 +25,18 @@
 
 namespace sogk {
 
+// Twiddle table entry: FP32 (cos, sin) and the parts lost to their
+// rounding; FP64 (cos, sin).
+struct alignas(16) TwF {
+  float x, y, z, w;
+};
+struct alignas(16) TwD {
+  double x, y;
+};
+
 template <typename T> struct C2;
-template <> struct C2<float> { using t = float2; };
-template <> struct C2<double> { using t = double2; };
+template <> struct C2<float> { using t = float2; using tw = TwF; };
+template <> struct C2<double> { using t = double2; using tw = TwD; };
 
 constexpr int kFftThreads = 1024;
 template <typename T> struct FftCap;
@@ -46,6 +55,20 @@ __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
 template <typename T2>
 __device__ __forceinline__ T2 rot(T2 a, bool inv) {
   return inv ? T2{-a.y, a.x} : T2{a.y, -a.x};
+}
+
+// a times the twiddle w = (cos, sin) + (cos_lo, sin_lo) (its conjugate for
+// the inverse): the rounding-error parts are applied first
+__device__ __forceinline__ float2 cmul_tw(float2 a, TwF w, bool inv) {
+  const float sh = inv ? -w.y : w.y;
+  const float sl = inv ? -w.w : w.w;
+  const float re_lo = a.x * w.z - a.y * sl;
+  const float im_lo = a.x * sl + a.y * w.z;
+  return float2{fmaf(a.x, w.x, fmaf(-a.y, sh, re_lo)), fmaf(a.x, sh, fmaf(a.y, w.x, im_lo))};
+}
+__device__ __forceinline__ double2 cmul_tw(double2 a, TwD w, bool inv) {
+  const double sh = inv ? -w.y : w.y;
+  return double2{a.x * w.x - a.y * sh, a.x * sh + a.y * w.x};
 }
 
 // floor(a / b) for 0 <= a < 2^22 from rb = 1/b rounded to float: the
@@ -69,8 +92,8 @@ __device__ __forceinline__ double div_sqrt2(double a) {
   return fma(a, 0.70710678118654746, a * 6.2685835895251089e-17);
 }
 
-template <typename T2, int R>
-__device__ __forceinline__ void dft(T2* x, bool inv, const T2* tw, int n) {
+template <typename T2, int R, typename T4>
+__device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
   if (R == 2) {
     const T2 a = x[0], b = x[1];
     x[0] = cadd(a, b);
@@ -114,9 +137,7 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T2* tw, int n) {
       T2 s = x[0];
 #pragma unroll
       for (int p = 1; p < R; ++p) {
-        T2 w = tw[((q * p) % R) * step];
-        if (inv) w.y = -w.y;
-        s = cadd(s, cmul(x[p], w));
+        s = cadd(s, cmul_tw(x[p], tw[((q * p) % R) * step], inv));
       }
       y[q] = s;
     }
@@ -126,8 +147,8 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T2* tw, int n) {
 }
 
 // One in-place Stockham stage of radix R; L = product of earlier radices.
-template <typename T2, int CAP, int R>
-__device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T2* tw, bool inv) {
+template <typename T2, int CAP, int R, typename T4>
+__device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T4* tw, bool inv) {
   constexpr int KB = CAP / R;
   const int nb = s.n / R, m = nb / L;
   const int tot = s.nl * nb;
@@ -154,11 +175,7 @@ __device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T2*
 #pragma unroll
       for (int p = 0; p < R; ++p) x[k][p] = a[p * st];
 #pragma unroll
-      for (int p = 1; p < R; ++p) {
-        T2 w = tw[j * p * m];
-        if (inv) w.y = -w.y;
-        x[k][p] = cmul(x[k][p], w);
-      }
+      for (int p = 1; p < R; ++p) x[k][p] = cmul_tw(x[k][p], tw[j * p * m], inv);
       dft<T2, R>(x[k], inv, tw, s.n);
       wb[k] = line * s.ls + (kk * L * R + j) * s.es;
     }
@@ -179,8 +196,8 @@ __device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T2*
 // All stages of one length.  The factorisation orders the radices 8..8, 4,
 // 2, 3..3, 5..5, 7..7; each group is a separate straight-line block so that
 // the registers of one stage are free for the next.
-template <typename T2, int CAP>
-__device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T2* tw, bool inv) {
+template <typename T2, int CAP, typename T4>
+__device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T4* tw, bool inv) {
   const int n8 = f.n8, n4 = f.n4, n2 = f.n2, n3 = f.n3, n5 = f.n5, n7 = f.n7;
   int L = 1;
   for (int i = 0; i < n8; ++i, L *= 8) stage<T2, CAP, 8>(buf, s, L, tw, inv);
@@ -201,8 +218,8 @@ static int max_lines(const FftLen& f, int cap) {
   return best;
 }
 
-template <typename T2>
-__device__ __forceinline__ void load_tw(T2* dst, const T2* src, int n) {
+template <typename T4>
+__device__ __forceinline__ void load_tw(T4* dst, const T4* src, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
@@ -279,16 +296,17 @@ __device__ __forceinline__ void join_pairs(T2* buf, int Ix, int npairs) {
 // per row) is stored over the same memory.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1)
-    k_fft_plane(T* __restrict__ data, FftLen fx, FftLen fy, const typename C2<T>::t* __restrict__ twg,
+    k_fft_plane(T* __restrict__ data, FftLen fx, FftLen fy, const typename C2<T>::tw* __restrict__ twg,
                 bool inv) {
   using T2 = typename C2<T>::t;
+  using T4 = typename C2<T>::tw;
   constexpr int CAP = FftCap<T>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Ix = fx.n, Iy = fy.n, C = Ix / 2 + 1, pitch = Ix + 2;
   const int np = Iy / 2;
-  T2* twx = reinterpret_cast<T2*>(smraw);
-  T2* twy = twx + Ix;
-  T2* buf = twy + Iy;
+  T4* twx = reinterpret_cast<T4*>(smraw);
+  T4* twy = twx + Ix;
+  T2* buf = reinterpret_cast<T2*>(twy + Iy);
   load_tw(twx, twg + fx.tw_off, Ix);
   load_tw(twy, twg + fy.tw_off, Iy);
   T* pl = data + (size_t)blockIdx.x * Iy * pitch;
@@ -327,14 +345,15 @@ __global__ void __launch_bounds__(kFftThreads, 1)
 // x pass alone: rows 2p, 2p+1 (pitch Ix + 2) of pairs p0 .. p0 + B - 1.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1)
-    k_fft_rows(T* __restrict__ data, FftLen fx, const typename C2<T>::t* __restrict__ twg,
+    k_fft_rows(T* __restrict__ data, FftLen fx, const typename C2<T>::tw* __restrict__ twg,
                int npairs, int B, bool inv) {
   using T2 = typename C2<T>::t;
   constexpr int CAP = FftCap<T>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Ix = fx.n, C = Ix / 2 + 1, pitch = Ix + 2;
-  T2* twx = reinterpret_cast<T2*>(smraw);
-  T2* buf = twx + Ix;
+  using T4 = typename C2<T>::tw;
+  T4* twx = reinterpret_cast<T4*>(smraw);
+  T2* buf = reinterpret_cast<T2*>(twx + Ix);
   load_tw(twx, twg + fx.tw_off, Ix);
   const int p0 = blockIdx.x * B;
   const int nl = min(B, npairs - p0);
@@ -378,14 +397,15 @@ __global__ void __launch_bounds__(kFftThreads, 1)
 // mult[(i*O + o)*Cn + c], backward FFT.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, 1)
-    k_fft_cols(typename C2<T>::t* __restrict__ data, FftLen f, const typename C2<T>::t* __restrict__ twg,
+    k_fft_cols(typename C2<T>::t* __restrict__ data, FftLen f, const typename C2<T>::tw* __restrict__ twg,
                int Cn, int O, long os, long es, int B, bool inv, const T* __restrict__ mult) {
   using T2 = typename C2<T>::t;
   constexpr int CAP = FftCap<T>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n = f.n;
-  T2* tw = reinterpret_cast<T2*>(smraw);
-  T2* buf = tw + n;
+  using T4 = typename C2<T>::tw;
+  T4* tw = reinterpret_cast<T4*>(smraw);
+  T2* buf = reinterpret_cast<T2*>(tw + n);
   load_tw(tw, twg + f.tw_off, n);
   const int gpo = (Cn + B - 1) / B;
   const int o = blockIdx.x / gpo;
@@ -421,8 +441,8 @@ template <typename T>
 static bool plane_fits(const FftLen& fx, const FftLen& fy) {
   constexpr int CAP = FftCap<T>::v;
   const int C = fx.n / 2 + 1;
-  const size_t smem = (size_t)(fx.n + fy.n + std::max((fy.n / 2) * fx.n, fy.n * C)) *
-                      sizeof(typename C2<T>::t);
+  const size_t smem = (size_t)(fx.n + fy.n) * sizeof(typename C2<T>::tw) +
+                      (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(typename C2<T>::t);
   return max_lines(fx, CAP) >= fy.n / 2 && max_lines(fy, CAP) >= C &&
          (fy.n / 2) * C <= kFftThreads * (CAP / 2) && smem <= (size_t)kMaxDynSmem;
 }
@@ -432,8 +452,10 @@ static cudaError_t launch_plane(T* data, const FftLen& fx, const FftLen& fy, con
                                 int nplanes, bool inv, cudaStream_t s) {
   using T2 = typename C2<T>::t;
   const int C = fx.n / 2 + 1;
-  const size_t sm = (size_t)(fx.n + fy.n + std::max((fy.n / 2) * fx.n, fy.n * C)) * sizeof(T2);
-  k_fft_plane<T><<<nplanes, kFftThreads, sm, s>>>(data, fx, fy, reinterpret_cast<const T2*>(tw),
+  using T4 = typename C2<T>::tw;
+  const size_t sm = (size_t)(fx.n + fy.n) * sizeof(T4) +
+                    (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(T2);
+  k_fft_plane<T><<<nplanes, kFftThreads, sm, s>>>(data, fx, fy, reinterpret_cast<const T4*>(tw),
                                                   inv);
   return cudaGetLastError();
 }
@@ -447,9 +469,10 @@ static cudaError_t launch_rows(T* data, const FftLen& fx, const void* tw, int nr
   const int C = fx.n / 2 + 1;
   int B = std::min(max_lines(fx, CAP), kFftThreads * (CAP / 2) / C);
   B = std::max(1, std::min(B, npairs));
-  const size_t sm = (size_t)(fx.n + B * std::max(fx.n, 2 * C)) * sizeof(T2);
+  using T4 = typename C2<T>::tw;
+  const size_t sm = (size_t)fx.n * sizeof(T4) + (size_t)B * std::max(fx.n, 2 * C) * sizeof(T2);
   const int grid = (npairs + B - 1) / B;
-  k_fft_rows<T><<<grid, kFftThreads, sm, s>>>(data, fx, reinterpret_cast<const T2*>(tw), npairs,
+  k_fft_rows<T><<<grid, kFftThreads, sm, s>>>(data, fx, reinterpret_cast<const T4*>(tw), npairs,
                                               B, inv);
   return cudaGetLastError();
 }
@@ -463,10 +486,11 @@ static cudaError_t launch_cols(T* data, const FftLen& f, const void* tw, int Cn,
   // balance the groups of one o
   const int groups = (Cn + B - 1) / B;
   B = (Cn + groups - 1) / groups;
-  const size_t sm = (size_t)(f.n + B * f.n) * sizeof(T2);
+  using T4 = typename C2<T>::tw;
+  const size_t sm = (size_t)f.n * sizeof(T4) + (size_t)B * f.n * sizeof(T2);
   const int grid = O * groups;
   k_fft_cols<T><<<grid, kFftThreads, sm, s>>>(reinterpret_cast<T2*>(data), f,
-                                              reinterpret_cast<const T2*>(tw), Cn, O, os, es, B,
+                                              reinterpret_cast<const T4*>(tw), Cn, O, os, es, B,
                                               inv, mult);
   return cudaGetLastError();
 }
@@ -523,8 +547,9 @@ template cudaError_t fft_long_pass<double>(const sog_plan*, bool, cudaStream_t, 
 bool fft_len_ok(int prec, const FftLen& f) {
   const int cap = prec == SOG_PREC_FP64 ? FftCap<double>::v : FftCap<float>::v;
   const size_t elem = prec == SOG_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+  const size_t twe = prec == SOG_PREC_FP64 ? sizeof(TwD) : sizeof(TwF);
   return f.n >= 2 && max_lines(f, cap) >= 1 && (f.n / 2 + 1) <= kFftThreads * (cap / 2) &&
-         (size_t)(f.n + std::max(f.n, f.n + 2)) * elem <= (size_t)kMaxDynSmem;
+         (size_t)f.n * twe + (size_t)(f.n + 2) * elem <= (size_t)kMaxDynSmem;
 }
 
 // Allow the FFT kernels the dynamic shared memory they may need (set once per

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "sog_internal.h"
@@ -388,35 +389,6 @@ bool near_table(const std::vector<double>& w, const std::vector<double>& s, doub
   return false;
 }
 
-// Float32 twiddle (c, s) near (cos, sin) whose norm c^2 + s^2 is closest to
-// 1: independently rounded cosines and sines leave every butterfly of a given
-// radix with the same small gain error, which a forward/backward pair turns
-// into a bias of the particles' self-interaction (and of the energy).
-// Candidates are the float32 values within two ulps of each rounded value.
-void unit_norm_f32(double& c, double& s) {
-  const float c0 = (float)c, s0 = (float)s;
-  float bc = c0, bs = s0;
-  double best = fabs((double)c0 * c0 + (double)s0 * s0 - 1.0);
-  double bang = fabs((double)c0 - c) + fabs((double)s0 - s);
-  float cc = c0;
-  for (int i = 0; i < 2; ++i) cc = nextafterf(cc, -2.0f);
-  for (int i = -2; i <= 2; ++i, cc = nextafterf(cc, 2.0f)) {
-    float ss = s0;
-    for (int k = 0; k < 2; ++k) ss = nextafterf(ss, -2.0f);
-    for (int j = -2; j <= 2; ++j, ss = nextafterf(ss, 2.0f)) {
-      const double nrm = fabs((double)cc * cc + (double)ss * ss - 1.0);
-      const double ang = fabs((double)cc - c) + fabs((double)ss - s);
-      if (nrm < best - 1e-18 || (fabs(nrm - best) <= 1e-18 && ang < bang)) {
-        best = nrm;
-        bang = ang;
-        bc = cc;
-        bs = ss;
-      }
-    }
-  }
-  c = bc;
-  s = bs;
-}
 
 template <typename T>
 void put(std::vector<unsigned char>& buf, size_t off, const std::vector<double>& v) {
@@ -576,16 +548,23 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     g.chunks = std::max(1, ch);
   }
 
-  // FFT lengths and twiddles exp(-2 pi i t/n)
+  // FFT lengths and twiddles exp(-2 pi i t/n): FP64 (cos, sin); FP32
+  // (cos, sin) rounded and their rounding errors, so that FP32 transforms
+  // apply twiddles of ~48-bit precision and no FP32-rounded root of unity
+  // biases the transform's gain.
   std::vector<double> tw;
+  const int tw_vals = prec == SOG_PREC_MIXED ? 4 : 2;
   auto add_len = [&](int n, sogk::FftLen& f) {
     factorize(n, f);
-    f.tw_off = (int)(tw.size() / 2);
+    f.tw_off = (int)(tw.size() / tw_vals);
     for (int t = 0; t < n; ++t) {
-      double c = cos(2.0 * kPi * t / n), sn = -sin(2.0 * kPi * t / n);
-      if (prec == SOG_PREC_MIXED) unit_norm_f32(c, sn);
-      tw.push_back(c);
-      tw.push_back(sn);
+      const double c = cos(2.0 * kPi * t / n), sn = -sin(2.0 * kPi * t / n);
+      if (prec == SOG_PREC_MIXED) {
+        const double ch = (double)(float)c, sh = (double)(float)sn;
+        tw.insert(tw.end(), {ch, sh, c - ch, sn - sh});
+      } else {
+        tw.insert(tw.end(), {c, sn});
+      }
     }
   };
   if (p->has_mid) {
@@ -597,7 +576,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     add_len(Ilx, p->flx);
     add_len(Ily, p->fly);
   }
-  if (tw.empty()) tw.assign(2, 0.0);
+  if (tw.empty()) tw.assign(4, 0.0);
   if ((p->has_mid && !(sogk::fft_len_ok(prec, p->fx) && sogk::fft_len_ok(prec, p->fy) &&
                        sogk::fft_len_ok(prec, p->fz))) ||
       (p->has_long && !(sogk::fft_len_ok(prec, p->flx) && sogk::fft_len_ok(prec, p->fly)))) {
@@ -684,7 +663,9 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     }
     const int C = Ilx / 2 + 1;
     const size_t kbytes = (size_t)Ily * C * P * P * es;
-    if (kbytes > ((size_t)1 << 30)) {
+    // per-mode P x P kernels: up to 32 GB (a 1176^2 long grid with P = 24,
+    // the 1000 x 1000 x 10 slab at 1e6 particles, needs 1.6 GB in FP32)
+    if (kbytes > ((size_t)32 << 30)) {
       delete p;
       return SOG_ERR_PARAMS;
     }
@@ -695,21 +676,31 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
     for (int f = 0; f < Ily; ++f) { ky[f] = 2.0 * kPi * std::min(f, Ily - f) / L[1]; Wy[f] = fy(ky[f]); }
     kmat.assign((size_t)Ily * C * P * P, 0.0);
-    std::vector<double> a(nl);
-    for (int y = 0; y < Ily; ++y)
-      for (int x = 0; x < C; ++x) {
-        if (x == 0 && y == 0) continue;
-        const double k2 = kx[x] * kx[x] + ky[y] * ky[y];
-        const double fac = kPi / A * pow(p->hl[0] * p->hl[1], 2) / pow(Wx[x] * Wy[y], 2);
-        double* K = &kmat[((size_t)y * C + x) * P * P];
-        for (int li = 0; li < nl; ++li) {
-          const int l = prm.m + 1 + li;
-          const double al = w[l] * s[l] * s[l] * exp(-s[l] * s[l] * k2 / 4.0);
-          if (al == 0.0) continue;
-          const double* B = &Bl[(size_t)li * P * P];
-          for (int i = 0; i < P * P; ++i) K[i] += fac * al * B[i];
+    // rows of modes on host threads; s_l grows with l, so once
+    // s_l^2 k^2 / 4 > 80 this and every later term is below e^-80 of the
+    // earlier ones and the sum stops
+    auto rows = [&](int y0, int ystep) {
+      for (int y = y0; y < Ily; y += ystep)
+        for (int x = 0; x < C; ++x) {
+          if (x == 0 && y == 0) continue;
+          const double k2 = kx[x] * kx[x] + ky[y] * ky[y];
+          const double fac = kPi / A * pow(p->hl[0] * p->hl[1], 2) / pow(Wx[x] * Wy[y], 2);
+          double* K = &kmat[((size_t)y * C + x) * P * P];
+          for (int li = 0; li < nl; ++li) {
+            const int l = prm.m + 1 + li;
+            const double ex = s[l] * s[l] * k2 / 4.0;
+            if (ex > 80.0) break;
+            const double al = w[l] * s[l] * s[l] * exp(-ex);
+            const double* B = &Bl[(size_t)li * P * P];
+            for (int i = 0; i < P * P; ++i) K[i] += fac * al * B[i];
+          }
         }
-      }
+    };
+    const int nthr = std::max(1, std::min(Ily, (int)std::min(16u, std::thread::hardware_concurrency())));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthr; ++t) pool.emplace_back(rows, t, nthr);
+    rows(0, nthr);
+    for (auto& th : pool) th.join();
     // k = 0: (pi/A) C^T K0 C, K0(d) = -sum_{l>m} w_l d^2 phi1(d^2/s_l^2)
     std::vector<double> K0((size_t)P * P, 0.0);
     for (int c = 0; c < P; ++c)
