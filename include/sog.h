@@ -224,6 +224,45 @@ int64_t sog_batch_launches(const sog_batch* batch);
 void sog_batch_destroy(sog_batch* batch);
 
 /*
+ * Learned parameter proposer (the paper selects parameters analytically,
+ * Sec. 4.4; that selection remains the fallback).  A multilayer perceptron
+ * with two tanh hidden layers of n_hidden units and one output, in FP32 on
+ * the device, with its own forward, backward and Adam kernels.  Parameters
+ * form one array: W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], w3 [H], b3 [1].
+ *   sog_mlp_create: 1 <= n_in <= 16, 1 <= n_hidden <= 64; Glorot-uniform
+ *     weights from `seed`, zero biases.  *mlp owned by the caller.
+ *   sog_mlp_get_params / sog_mlp_set_params: host array of exactly
+ *     sog_mlp_num_params values (set also resets the Adam state).
+ *   sog_mlp_forward: X [n x n_in] and Y [n], device FP32.
+ *   sog_mlp_loss_grad: loss = (1/n) sum_s (y_s - T_s)^2 and its gradient
+ *     with respect to the parameters; X, T, grad [num_params], loss [1] are
+ *     device FP32 (grad and loss are overwritten).
+ *   sog_mlp_train: `iters` full-batch Adam steps (beta 0.9, 0.999, eps 1e-8,
+ *     learning rate lr) on (X, T); *loss_out (host, may be NULL) receives the
+ *     loss of the last step (waits for the stream then).
+ * All enqueue on `stream`.
+ *
+ * sog_features: eight features of a system for the proposer, written to host
+ * memory `feat`: log10 N, log10 sqrt(Lx Ly), log10 (Lz / sqrt(Lx Ly)),
+ * log10 tol, log10 density, and of a 16-bin histogram of z (computed on the
+ * device from r, N x 3 of the precision's type): max / mean, mean of the two
+ * wall bins / mean, standard deviation / mean.  Synchronous.
+ */
+typedef struct sog_mlp sog_mlp;
+sog_status sog_mlp_create(sog_mlp** mlp, int32_t n_in, int32_t n_hidden, uint64_t seed);
+int64_t sog_mlp_num_params(const sog_mlp* mlp);
+sog_status sog_mlp_get_params(const sog_mlp* mlp, float* params, int64_t n);
+sog_status sog_mlp_set_params(sog_mlp* mlp, const float* params, int64_t n);
+sog_status sog_mlp_forward(const sog_mlp* mlp, const float* X, int32_t n, float* Y, void* stream);
+sog_status sog_mlp_loss_grad(const sog_mlp* mlp, const float* X, const float* T, int32_t n,
+                             float* grad, float* loss, void* stream);
+sog_status sog_mlp_train(sog_mlp* mlp, const float* X, const float* T, int32_t n, int32_t iters,
+                         float lr, float* loss_out, void* stream);
+void sog_mlp_destroy(sog_mlp* mlp);
+sog_status sog_features(int64_t N, double Lx, double Ly, double Lz, double tol, const void* r,
+                        int32_t precision, float* feat);
+
+/*
  * Assembly of Phi, F and U from the four parts that sog_eval_components
  * returns, with no plan and no memory allocation.  The paper has no
  * counterpart: it is a library convenience for callers that must not allocate

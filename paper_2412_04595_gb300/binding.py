@@ -107,10 +107,24 @@ def load(build_if_missing: bool = False):
     L.sog_batch_launches.restype = i64
     L.sog_batch_destroy.argtypes = [vp]
     L.sog_batch_destroy.restype = None
+    u64 = ctypes.c_uint64
+    L.sog_mlp_create.argtypes = [ctypes.POINTER(vp), i32, i32, u64]
+    L.sog_mlp_num_params.argtypes = [vp]
+    L.sog_mlp_num_params.restype = i64
+    L.sog_mlp_get_params.argtypes = [vp, vp, i64]
+    L.sog_mlp_set_params.argtypes = [vp, vp, i64]
+    L.sog_mlp_forward.argtypes = [vp, vp, i32, vp, vp]
+    L.sog_mlp_loss_grad.argtypes = [vp, vp, vp, i32, vp, vp, vp]
+    L.sog_mlp_train.argtypes = [vp, vp, vp, i32, i32, ctypes.c_float,
+                                ctypes.POINTER(ctypes.c_float), vp]
+    L.sog_mlp_destroy.argtypes = [vp]
+    L.sog_mlp_destroy.restype = None
+    L.sog_features.argtypes = [i64, d, d, d, d, vp, i32, ctypes.POINTER(ctypes.c_float)]
     for f in ("sog_select_params", "sog_plan_create", "sog_plan_get_params", "sog_eval",
               "sog_eval_components", "sog_eval_host", "sog_plan_check", "sog_plan_set_timing",
               "sog_plan_get_timing", "sog_assemble_noalloc", "sog_batch_create", "sog_batch_eval",
-              "sog_batch_check"):
+              "sog_batch_check", "sog_mlp_create", "sog_mlp_get_params", "sog_mlp_set_params",
+              "sog_mlp_forward", "sog_mlp_loss_grad", "sog_mlp_train", "sog_features"):
         getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
@@ -332,6 +346,82 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.sog_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+N_FEATURES = 8
+
+
+def sog_features(N, L, tol, r):
+    """sog_features: the proposer's eight features of a system (host list);
+    r is the N x 3 CUDA tensor of positions (float32 or float64)."""
+    import torch
+    prec = SOG_PREC_FP64 if r.dtype == torch.float64 else SOG_PREC_MIXED
+    if not r.is_cuda or not r.is_contiguous():
+        raise ValueError("r must be a contiguous CUDA tensor")
+    out = (ctypes.c_float * N_FEATURES)()
+    _check(load().sog_features(int(N), float(L[0]), float(L[1]), float(L[2]), float(tol), _ptr(r),
+                               prec, out), "sog_features")
+    return [float(v) for v in out]
+
+
+class MLP:
+    """Owns one ``sog_mlp`` (FP32 parameters on the device)."""
+
+    def __init__(self, n_in=N_FEATURES, n_hidden=32, seed=0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.sog_mlp_create(ctypes.byref(h), int(n_in), int(n_hidden), int(seed)),
+               "sog_mlp_create")
+        self._h = h
+        self.n_in, self.n_hidden = int(n_in), int(n_hidden)
+        self.num_params = int(self._lib.sog_mlp_num_params(h))
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(self._lib.sog_mlp_get_params(self._h, ctypes.c_void_p(out.ctypes.data),
+                                            self.num_params), "sog_mlp_get_params")
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self._lib.sog_mlp_set_params(self._h, ctypes.c_void_p(a.ctypes.data), a.size),
+               "sog_mlp_set_params")
+
+    def forward(self, X, Y=None, stream=None):
+        import torch
+        if Y is None:
+            Y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _check(self._lib.sog_mlp_forward(self._h, _ptr(X), int(X.shape[0]), _ptr(Y),
+                                         _stream_ptr(stream)), "sog_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T, stream=None):
+        import torch
+        g = torch.empty(self.num_params, dtype=torch.float32, device=X.device)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        _check(self._lib.sog_mlp_loss_grad(self._h, _ptr(X), _ptr(T), int(X.shape[0]), _ptr(g),
+                                           _ptr(loss), _stream_ptr(stream)), "sog_mlp_loss_grad")
+        return loss, g
+
+    def train(self, X, T, iters, lr=1e-2, stream=None):
+        out = ctypes.c_float()
+        _check(self._lib.sog_mlp_train(self._h, _ptr(X), _ptr(T), int(X.shape[0]), int(iters),
+                                       float(lr), ctypes.byref(out), _stream_ptr(stream)),
+               "sog_mlp_train")
+        return float(out.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sog_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,113 @@
+"""The learned parameter proposer: the network's own CUDA kernels against the
+FP64 reference network, its training, the system features, and what the
+trained proposer gains over the analytic selection (n_nb = 120) on systems
+it was not trained on, at the analytic selection's accuracy."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_2412_04595_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2412_04595_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return binding
+
+
+def test_forward_and_gradient_match_the_reference(B):
+    rng = np.random.default_rng(1)
+    n_in, H, n = 8, 32, 300
+    mlp = B.MLP(n_in, H, seed=7)
+    p = mlp.get_params().astype(np.float64)
+    X = rng.normal(0, 1, (n, n_in))
+    T = rng.normal(0, 1, n)
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Tt = torch.tensor(T, dtype=torch.float32, device="cuda")
+    # the reference sees the same FP32-rounded inputs
+    X32 = X.astype(np.float32).astype(np.float64)
+    T32 = T.astype(np.float32).astype(np.float64)
+    y_ref, _, _ = omlp.forward(p, X32, n_in, H)
+    y = mlp.forward(Xt).double().cpu().numpy()
+    assert np.max(np.abs(y - y_ref)) <= 1e-5 * max(1.0, np.max(np.abs(y_ref)))
+    loss_ref, g_ref = omlp.loss_grad(p, X32, T32, n_in, H)
+    loss, g = mlp.loss_grad(Xt, Tt)
+    torch.cuda.synchronize()
+    assert abs(loss.item() - loss_ref) <= 1e-5 * loss_ref
+    g = g.double().cpu().numpy()
+    assert np.max(np.abs(g - g_ref)) <= 1e-4 * np.max(np.abs(g_ref))
+    mlp.close()
+
+
+def test_training_fits_a_smooth_map(B):
+    rng = np.random.default_rng(2)
+    n = 512
+    X = rng.uniform(-1, 1, (n, 8))
+    T = np.sin(2 * X[:, 0]) + 0.5 * X[:, 1] ** 2 - 0.3 * X[:, 2] * X[:, 3]
+    mlp = B.MLP(8, 32, seed=3)
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    Tt = torch.tensor(T, dtype=torch.float32, device="cuda")
+    loss0 = mlp.train(Xt, Tt, 0)
+    loss = mlp.train(Xt, Tt, 3000, lr=1e-2)
+    assert loss < 2e-3 * loss0 + 1e-3, (loss0, loss)
+    mlp.close()
+
+
+def test_features_see_the_double_layer(B):
+    N, L = 40000, (60.0, 60.0, 80.0)
+    fu = B.sog_features(N, L, 1e-6, torch.tensor(workloads.uniform_neutral(N, L, 1)[1],
+                                                   device="cuda"))
+    fe = B.sog_features(N, L, 1e-6, torch.tensor(workloads.edl_neutral(N, L, 1)[1], device="cuda"))
+    assert abs(fu[0] - math.log10(N)) < 1e-6 and abs(fu[3] + 6.0) < 1e-6
+    assert fu[5] < 1.2 and fu[7] < 0.1          # flat histogram
+    assert fe[6] > 2.0 and fe[5] > 2.0          # charges piled at the walls
+
+
+def test_proposer_gains_over_the_analytic_default(B, oracle_mod):
+    from paper_2412_04595_gb300 import proposer as P
+    train = P.training_systems(96, seed=11)
+    Z, Y, _ = P.measure(train, 1e-6, reps=7)
+    prop = P.Proposer(n_hidden=32, seed=0)
+    prop.fit(Z, Y, iters=4000, lr=5e-3)
+    held = P.training_systems(16, seed=99, nmax=100000)
+    t_prop = t_def = t_best = 0.0
+    used = 0
+    for q, r, L in held:
+        N = q.size
+        qt = torch.tensor(q, dtype=torch.float32, device="cuda")
+        rt = torch.tensor(r, dtype=torch.float32, device="cuda")
+        n_nb, src = prop.propose(B.sog_features(N, L, 1e-6, rt), N, L, 1e-6)
+        used += src == "mlp"
+        print(N, [round(v, 1) for v in L], "proposed n_nb %.0f (%s)" % (n_nb, src))
+        tp = P.time_eval(N, L, 1e-6, qt, rt, n_nb, reps=7)
+        td = P.time_eval(N, L, 1e-6, qt, rt, P.DEFAULT_NNB, reps=7)
+        row = [P.time_eval(N, L, 1e-6, qt, rt, c, reps=7) for c in P.CANDIDATES]
+        t_prop += tp
+        t_def += td
+        t_best += min(t for t in row if t is not None)
+    print("held-out time: proposed %.3f ms, analytic %.3f ms, best candidate %.3f ms (gain %.3f, "
+          "ceiling %.3f)" % (t_prop, t_def, t_best, t_def / t_prop, t_def / t_best))
+    assert t_prop <= 1.01 * t_def
+    # accuracy of a proposed plan: FP64 with the proposed parameters against
+    # the oracle's own selection at a much tighter tolerance
+    q, r, L = P.training_systems(1, seed=5, nmin=3000, nmax=4000)[0]
+    N = q.size
+    rt = torch.tensor(r, dtype=torch.float32, device="cuda")
+    plan, n_nb, _ = prop.plan(N, L, 1e-6, rt, precision=B.SOG_PREC_FP64)
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F = torch.empty(N, 3, dtype=torch.float64, device="cuda")
+    plan.eval(torch.tensor(q, device="cuda"), torch.tensor(r, device="cuda"), None, E, F)
+    torch.cuda.synchronize()
+    plan.close()
+    ref = oracle_mod.sog_eval(oracle_mod.select_params(N, *L, 1e-10), q, r)
+    assert abs(E.item() - ref["E"]) <= 1e-5 * abs(ref["E"])
