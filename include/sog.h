@@ -73,7 +73,14 @@ enum { SOG_WIN_ES = 0, SOG_WIN_GAUSS = 1 };
  *   P_long, shape_long   long-range window support and shape
  *   P_cheb   number of Chebyshev proxy points in z (Eq. A.6), 2..64
  *   window   SOG_WIN_ES or SOG_WIN_GAUSS (Remark 3.4)
- * Grid sizes must be even; Ix, Iy, Iz*, Ix_long, Iy_long factor into 2,3,5,7.
+ *   long_direct  0: long range by window gridding and 2D FFTs (Algorithm 2);
+ *            1: by direct Fourier sums without FFT (Algorithm 3) over the
+ *            modes |n_x| <= (Ix_long-1)/2, |n_y| <= (Iy_long-1)/2 (odd
+ *            counts; P_long and shape_long unused)
+ * Grid sizes must be even; Ix, Iy, Iz*, Ix_long, Iy_long factor into 2,3,5,7
+ * Long-range mode counts of long_direct: odd; the half-plane modes
+ * Ky + Kx (2 Ky + 1) (K = (I_long - 1) / 2) at most 256, and times P_cheb
+ * at most 8192 (the coefficient table is held on chip).
  */
 typedef struct sog_params {
   double L[3];
@@ -88,6 +95,7 @@ typedef struct sog_params {
   double shape_long;
   int32_t P_cheb;
   int32_t window;
+  int32_t long_direct;
 } sog_params;
 
 /*

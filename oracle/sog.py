@@ -253,11 +253,14 @@ def lagrange(zc, z):
 # ---------------------------------------------------------------------------
 
 def make_params(L, b, r0, omega, rc, M, m, I, hz, P_win, I_long, P_long,
-                P_cheb, window="es", shape=None, shape_long=None):
+                P_cheb, window="es", shape=None, shape_long=None, long_direct=False):
     """Manual parameter set.  L = (Lx, Ly, Lz); I = (Ix, Iy, Iz*) mid grid with
     z spacing hz (Lz* = Iz* hz); I_long = (Ix_long, Iy_long); P_win / P_long
     window supports (grid points); P_cheb Chebyshev proxy planes; m the last
-    mid-range index (-1: no mid range), Gaussians m+1..M are long range."""
+    mid-range index (-1: no mid range), Gaussians m+1..M are long range.
+    long_direct: the long range by direct Fourier sums (Algorithm 3) over the
+    modes |n_x| <= (Ix_long - 1)/2, |n_y| <= (Iy_long - 1)/2 (odd counts)
+    instead of window gridding and FFTs (Algorithm 2)."""
     sigma = rc / r0
     w = make_window(window, P_win, shape)
     wl = make_window(window, P_long, shape_long)
@@ -265,7 +268,8 @@ def make_params(L, b, r0, omega, rc, M, m, I, hz, P_win, I_long, P_long,
                 sigma=float(sigma), rc=float(rc), M=int(M), m=int(m),
                 I=tuple(map(int, I)), hz=float(hz), P_win=int(P_win),
                 window=window, shape=w.shape, I_long=tuple(map(int, I_long)),
-                P_long=int(P_long), shape_long=wl.shape, P_cheb=int(P_cheb))
+                P_long=int(P_long), shape_long=wl.shape, P_cheb=int(P_cheb),
+                long_direct=bool(long_direct))
 
 
 def _fft_size(n: int) -> int:
@@ -341,6 +345,7 @@ def select_params(N: int, Lx: float, Ly: float, Lz: float, tol: float,
     best = None
     for m in range(-1, M + 1):
         cost = 0
+        direct = False
         if m >= 0:
             K = 2.0 * math.sqrt(lne) / s[0]
             nx, ny = math.ceil(K * Lx / PI), math.ceil(K * Ly / PI)
@@ -383,16 +388,31 @@ def select_params(N: int, Lx: float, Ly: float, Lz: float, tol: float,
             if Pc == 0:
                 continue
             Gl = Ilx * Ily
-            cost += 4 * N * Pl * Pl * Pc + 10 * Gl * Pc * _clog2(Gl) + 2 * Gl * Pc * Pc + N * Pc
+            cost_grid = 4 * N * Pl * Pl * Pc + 10 * Gl * Pc * _clog2(Gl) + 2 * Gl * Pc * Pc + N * Pc
+            # Algorithm 3 (no FFT): direct sums over the modes |k| <= Kl, at
+            # most 256 half-plane modes and 8192 half-plane modes x Pc; taken
+            # when its operation count is lower (READING: the paper prefers it
+            # when Lz ~ sqrt(Lx Ly))
+            Kdx = math.ceil(Kl * Lx / (2 * PI))
+            Kdy = math.ceil(Kl * Ly / (2 * PI))
+            nhalf = Kdy + Kdx * (2 * Kdy + 1)
+            cost_direct = 4 * N * nhalf * Pc
+            if 1 <= nhalf <= 256 and nhalf * Pc <= 8192 and cost_direct < cost_grid:
+                direct = True
+                Ilx, Ily = 2 * Kdx + 1, 2 * Kdy + 1
+                cost += cost_direct
+            else:
+                cost += cost_grid
         else:
             Ilx = Ily = Pl = Pc = 0
         if best is None or cost < best[0]:
-            best = (cost, m, (Ix, Iy, Izs), hz, Pw, (Ilx, Ily), Pl, Pc)
+            best = (cost, m, (Ix, Iy, Izs), hz, Pw, (Ilx, Ily), Pl, Pc, direct)
     if best is None:
         raise ValueError("no feasible parameter set")
-    _, m, I, hz, Pw, Il, Pl, Pc = best
+    _, m, I, hz, Pw, Il, Pl, Pc, direct = best
     return make_params((Lx, Ly, Lz), b, r0, omega, rc, M, m, I, hz,
-                       Pw if Pw else 4, Il, Pl if Pl else 4, Pc, window=window)
+                       Pw if Pw else 4, Il, Pl if Pl else 4, Pc, window=window,
+                       long_direct=direct)
 
 
 # ---------------------------------------------------------------------------
@@ -549,6 +569,8 @@ def long_range(prm, q, r, tgt=None):
         mu_c'(k) = sum_j q_j L_c'(z_j) e^{-ik.rho_j},
     with the two NUFFT-like steps done by window gridding / gathering on the
     I^long grid and 2D FFTs exactly as in Algorithm 1."""
+    if prm.get("long_direct", False):
+        return long_range_direct(prm, q, r, tgt)
     q = np.asarray(q, dtype=np.float64)
     r = np.asarray(r, dtype=np.float64)
     tgt, tr = _targets(r, tgt)
@@ -607,6 +629,43 @@ def long_range(prm, q, r, tgt=None):
         grad[:, 0] += Lt[:, c] * Sx / hx
         grad[:, 1] += Lt[:, c] * Sy / hy
         grad[:, 2] += dLt[:, c] * Sc
+    return phi, grad
+
+
+def long_range_direct(prm, q, r, tgt=None):
+    """Long range without its k = 0 mode by Algorithm 3 (no FFT), in the same
+    anterpolation reading: for the modes k = (2 pi n_x / Lx, 2 pi n_y / Ly),
+    |n_x| <= (Ix_long - 1)/2, |n_y| <= (Iy_long - 1)/2, k != 0,
+        mu_c(k) = sum_j q_j L_c(z_j) e^{-ik.rho_j}          (gridding, direct sums)
+        nu_c(k) = (pi/A) sum_c' K_k(z_c - z_c') mu_c'(k)      (Eq. 3.13 / 4.40)
+        Phi_i   = Re sum_k e^{ik.rho_i} sum_c L_c(z_i) nu_c(k)  (gathering)."""
+    q = np.asarray(q, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64)
+    tgt, tr = _targets(r, tgt)
+    if prm["m"] >= prm["M"]:
+        return np.zeros(tgt.size), np.zeros((tgt.size, 3))
+    Lx, Ly, Lz = prm["L"]
+    Kx, Ky = (prm["I_long"][0] - 1) // 2, (prm["I_long"][1] - 1) // 2
+    nx, ny = np.meshgrid(np.arange(-Kx, Kx + 1), np.arange(-Ky, Ky + 1), indexing="ij")
+    keep = (nx != 0) | (ny != 0)
+    kx = 2 * PI * nx[keep] / Lx
+    ky = 2 * PI * ny[keep] / Ly
+    P = prm["P_cheb"]
+    zc = cheb_nodes(P, Lz)
+    Ls, _ = lagrange(zc, r[:, 2])
+    phase = np.exp(-1j * (np.outer(r[:, 0], kx) + np.outer(r[:, 1], ky)))   # (N, modes)
+    mu = (phase * q[:, None]).T @ Ls                                         # (modes, P)
+    Kmat = long_kernel(prm, (kx ** 2 + ky ** 2)[:, None, None],
+                       zc[None, :, None] - zc[None, None, :])                # (modes, P, P)
+    nu = np.einsum("kab,kb->ka", Kmat, mu) * (PI / (Lx * Ly))
+    Lt, dLt = lagrange(zc, tr[:, 2])
+    ph = np.exp(1j * (np.outer(tr[:, 0], kx) + np.outer(tr[:, 1], ky)))      # (T, modes)
+    S = ph * (Lt @ nu.T)                                                     # (T, modes)
+    Sz = ph * (dLt @ nu.T)
+    phi = S.sum(1).real
+    grad = np.column_stack([(1j * S * kx[None, :]).sum(1).real,
+                            (1j * S * ky[None, :]).sum(1).real,
+                            Sz.sum(1).real])
     return phi, grad
 
 

@@ -26,14 +26,15 @@ class SogParams(ctypes.Structure):
                 ("hz", ctypes.c_double), ("P_win", ctypes.c_int32), ("shape", ctypes.c_double),
                 ("I_long", ctypes.c_int32 * 2), ("P_long", ctypes.c_int32),
                 ("shape_long", ctypes.c_double), ("P_cheb", ctypes.c_int32),
-                ("window", ctypes.c_int32)]
+                ("window", ctypes.c_int32), ("long_direct", ctypes.c_int32)]
 
     def to_dict(self):
         return dict(L=tuple(self.L), b=self.b, r0=self.r0, omega=self.omega, sigma=self.sigma,
                     rc=self.rc, M=self.M, m=self.m, I=tuple(self.I), hz=self.hz,
                     P_win=self.P_win, shape=self.shape, I_long=tuple(self.I_long),
                     P_long=self.P_long, shape_long=self.shape_long, P_cheb=self.P_cheb,
-                    window="es" if self.window == SOG_WIN_ES else "gauss")
+                    window="es" if self.window == SOG_WIN_ES else "gauss",
+                    long_direct=bool(self.long_direct))
 
     @classmethod
     def from_dict(cls, d):
@@ -46,6 +47,7 @@ class SogParams(ctypes.Structure):
         p.I[:] = list(d["I"])
         p.I_long[:] = list(d["I_long"])
         p.window = SOG_WIN_ES if d.get("window", "es") == "es" else SOG_WIN_GAUSS
+        p.long_direct = 1 if d.get("long_direct", False) else 0
         return p
 
 

@@ -92,6 +92,19 @@ __device__ __forceinline__ double div_sqrt2(double a) {
   return fma(a, 0.70710678118654746, a * 6.2685835895251089e-17);
 }
 
+// a times a constant given as a rounded value hi plus its rounding error lo
+// (FP32); FP64 uses the double constant.
+__device__ __forceinline__ float mulc(float a, float hi, float lo, double) {
+  return fmaf(a, hi, a * lo);
+}
+__device__ __forceinline__ double mulc(double a, float, float, double v) { return a * v; }
+
+// a + i b (inv) or a - i b
+template <typename T2>
+__device__ __forceinline__ T2 pm_i(T2 a, T2 b, bool plus) {
+  return plus ? T2{a.x - b.y, a.y + b.x} : T2{a.x + b.y, a.y - b.x};
+}
+
 template <typename T2, int R, typename T4>
 __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
   if (R == 2) {
@@ -127,9 +140,39 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
     x[6] = csub(e[2], o2);
     x[3] = cadd(e[3], o3);
     x[7] = csub(e[3], o3);
+  } else if (R == 3) {
+    // w = e^(-2 pi i / 3) = -1/2 - i sqrt3/2
+    const T2 t = cadd(x[1], x[2]), d = csub(x[1], x[2]);
+    const T2 a = T2{x[0].x - 0.5f * t.x, x[0].y - 0.5f * t.y};
+    const T2 b = T2{mulc(d.x, 8.660253882e-01f, 1.554362505e-08f, 0.8660254037844386),
+                    mulc(d.y, 8.660253882e-01f, 1.554362505e-08f, 0.8660254037844386)};
+    x[0] = cadd(x[0], t);
+    x[1] = pm_i(a, b, inv);
+    x[2] = pm_i(a, b, !inv);
+  } else if (R == 5) {
+    // w = e^(-2 pi i / 5) = c1 - i s1, w^2 = c2 - i s2
+    const T2 t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
+    const T2 t3 = csub(x[1], x[4]), t4 = csub(x[2], x[3]);
+#define SOG_C1(v) mulc(v, 3.090170026e-01f, -8.207602598e-09f, 0.30901699437494745)
+#define SOG_C2(v) mulc(v, -8.090170026e-01f, 8.207602598e-09f, -0.8090169943749473)
+#define SOG_S1(v) mulc(v, 9.510565400e-01f, -2.371720598e-08f, 0.9510565162951535)
+#define SOG_S2(v) mulc(v, 5.877852440e-01f, 8.304436250e-09f, 0.5877852522924732)
+    const T2 a1 = T2{x[0].x + SOG_C1(t1.x) + SOG_C2(t2.x), x[0].y + SOG_C1(t1.y) + SOG_C2(t2.y)};
+    const T2 a2 = T2{x[0].x + SOG_C2(t1.x) + SOG_C1(t2.x), x[0].y + SOG_C2(t1.y) + SOG_C1(t2.y)};
+    const T2 b1 = T2{SOG_S1(t3.x) + SOG_S2(t4.x), SOG_S1(t3.y) + SOG_S2(t4.y)};
+    const T2 b2 = T2{SOG_S2(t3.x) - SOG_S1(t4.x), SOG_S2(t3.y) - SOG_S1(t4.y)};
+#undef SOG_C1
+#undef SOG_C2
+#undef SOG_S1
+#undef SOG_S2
+    x[0] = cadd(x[0], cadd(t1, t2));
+    x[1] = pm_i(a1, b1, inv);
+    x[4] = pm_i(a1, b1, !inv);
+    x[2] = pm_i(a2, b2, inv);
+    x[3] = pm_i(a2, b2, !inv);
   } else {
-    // odd radix: y_q = sum_p x_p w^(qp), w = exp(-+2 pi i / R) from the
-    // length-n table (entry (qp mod R) n / R)
+    // other odd radix (7): y_q = sum_p x_p w^(qp), w = exp(-+2 pi i / R) from
+    // the length-n table (entry (qp mod R) n / R)
     const int step = n / R;
     T2 y[R];
 #pragma unroll
@@ -158,7 +201,7 @@ __device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T4*
   int wb[KB];
 #pragma unroll
   for (int k = 0; k < KB; ++k) {
-    const int id = threadIdx.x + k * kFftThreads;
+    const int id = threadIdx.x + k * (int)blockDim.x;
     wb[k] = -1;
     if (id < tot) {
       int line, t;
@@ -209,11 +252,11 @@ __device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T4* t
 }
 
 // Largest nl for which nl lines of length n fit the engine.
-static int max_lines(const FftLen& f, int cap) {
+static int max_lines(const FftLen& f, int cap, int nt = kFftThreads) {
   int best = 1 << 30;
   for (int st = 0; st < f.nst; ++st) {
     const int R = f.radix[st];
-    best = std::min(best, kFftThreads * (cap / R) / (f.n / R));
+    best = std::min(best, nt * (cap / R) / (f.n / R));
   }
   return best;
 }
@@ -236,7 +279,7 @@ __device__ __forceinline__ void split_pairs(T2* buf, int Ix, int npairs) {
   int pr[KB], fq[KB];
 #pragma unroll
   for (int k = 0; k < KB; ++k) {
-    const int id = threadIdx.x + k * kFftThreads;
+    const int id = threadIdx.x + k * (int)blockDim.x;
     pr[k] = -1;
     if (id < tot) {
       const int p = fdiv(id, rC), f = id - p * C;
@@ -270,7 +313,7 @@ __device__ __forceinline__ void join_pairs(T2* buf, int Ix, int npairs) {
   int pr[KB], fq[KB];
 #pragma unroll
   for (int k = 0; k < KB; ++k) {
-    const int id = threadIdx.x + k * kFftThreads;
+    const int id = threadIdx.x + k * (int)blockDim.x;
     pr[k] = -1;
     if (id < tot) {
       const int p = fdiv(id, rC), f = id - p * C;
@@ -315,7 +358,7 @@ __global__ void __launch_bounds__(kFftThreads, 1)
   const LineSet ys{Iy, C, 1, C, true};
   if (!inv) {
     const float rI = 1.f / (float)Ix;
-    for (int id = threadIdx.x; id < np * Ix; id += kFftThreads) {
+    for (int id = threadIdx.x; id < np * Ix; id += blockDim.x) {
       const int p = fdiv(id, rI), x = id - p * Ix;
       const T* r0 = pl + (size_t)(2 * p) * pitch + x;
       buf[id] = T2{r0[0], r0[pitch]};
@@ -324,15 +367,15 @@ __global__ void __launch_bounds__(kFftThreads, 1)
     fft_lines<T2, CAP>(buf, xs, fx, twx, false);
     split_pairs<T2, CAP>(buf, Ix, np);
     fft_lines<T2, CAP>(buf, ys, fy, twy, false);
-    for (int id = threadIdx.x; id < Iy * C; id += kFftThreads) plc[id] = buf[id];
+    for (int id = threadIdx.x; id < Iy * C; id += blockDim.x) plc[id] = buf[id];
   } else {
-    for (int id = threadIdx.x; id < Iy * C; id += kFftThreads) buf[id] = plc[id];
+    for (int id = threadIdx.x; id < Iy * C; id += blockDim.x) buf[id] = plc[id];
     __syncthreads();
     fft_lines<T2, CAP>(buf, ys, fy, twy, true);
     join_pairs<T2, CAP>(buf, Ix, np);
     fft_lines<T2, CAP>(buf, xs, fx, twx, true);
     const float rI = 1.f / (float)Ix;
-    for (int id = threadIdx.x; id < np * Ix; id += kFftThreads) {
+    for (int id = threadIdx.x; id < np * Ix; id += blockDim.x) {
       const int p = fdiv(id, rI), x = id - p * Ix;
       T* r0 = pl + (size_t)(2 * p) * pitch + x;
       const T2 z = buf[id];
@@ -361,7 +404,7 @@ __global__ void __launch_bounds__(kFftThreads, 1)
   const LineSet xs{Ix, nl, Ix, 1, false};
   const float rI = 1.f / (float)Ix, rC = 1.f / (float)C;
   if (!inv) {
-    for (int id = threadIdx.x; id < nl * Ix; id += kFftThreads) {
+    for (int id = threadIdx.x; id < nl * Ix; id += blockDim.x) {
       const int p = fdiv(id, rI), x = id - p * Ix;
       const T* r0 = base + (size_t)(2 * p) * pitch + x;
       buf[id] = T2{r0[0], r0[pitch]};
@@ -369,19 +412,19 @@ __global__ void __launch_bounds__(kFftThreads, 1)
     __syncthreads();
     fft_lines<T2, CAP>(buf, xs, fx, twx, false);
     split_pairs<T2, CAP>(buf, Ix, nl);
-    for (int id = threadIdx.x; id < 2 * nl * C; id += kFftThreads) {
+    for (int id = threadIdx.x; id < 2 * nl * C; id += blockDim.x) {
       const int y = fdiv(id, rC), f = id - y * C;
       reinterpret_cast<T2*>(base + (size_t)y * pitch)[f] = buf[id];
     }
   } else {
-    for (int id = threadIdx.x; id < 2 * nl * C; id += kFftThreads) {
+    for (int id = threadIdx.x; id < 2 * nl * C; id += blockDim.x) {
       const int y = fdiv(id, rC), f = id - y * C;
       buf[id] = reinterpret_cast<const T2*>(base + (size_t)y * pitch)[f];
     }
     __syncthreads();
     join_pairs<T2, CAP>(buf, Ix, nl);
     fft_lines<T2, CAP>(buf, xs, fx, twx, true);
-    for (int id = threadIdx.x; id < nl * Ix; id += kFftThreads) {
+    for (int id = threadIdx.x; id < nl * Ix; id += blockDim.x) {
       const int p = fdiv(id, rI), x = id - p * Ix;
       T* r0 = base + (size_t)(2 * p) * pitch + x;
       const T2 z = buf[id];
@@ -413,7 +456,7 @@ __global__ void __launch_bounds__(kFftThreads, 1)
   const int nl = min(B, Cn - c0);
   T2* base = data + (size_t)o * os + c0;
   const float rl = 1.f / (float)nl;
-  for (int id = threadIdx.x; id < nl * n; id += kFftThreads) {
+  for (int id = threadIdx.x; id < nl * n; id += blockDim.x) {
     const int i = fdiv(id, rl), c = id - i * nl;
     buf[id] = base[(size_t)i * es + c];
   }
@@ -421,7 +464,7 @@ __global__ void __launch_bounds__(kFftThreads, 1)
   const LineSet cs{n, nl, 1, nl, true};
   fft_lines<T2, CAP>(buf, cs, f, tw, mult ? false : inv);
   if (mult) {
-    for (int id = threadIdx.x; id < nl * n; id += kFftThreads) {
+    for (int id = threadIdx.x; id < nl * n; id += blockDim.x) {
       const int i = fdiv(id, rl), c = id - i * nl;
       const T sc = mult[((size_t)i * O + o) * Cn + c0 + c];
       const T2 v = buf[id];
@@ -430,21 +473,31 @@ __global__ void __launch_bounds__(kFftThreads, 1)
     __syncthreads();
     fft_lines<T2, CAP>(buf, cs, f, tw, true);
   }
-  for (int id = threadIdx.x; id < nl * n; id += kFftThreads) {
+  for (int id = threadIdx.x; id < nl * n; id += blockDim.x) {
     const int i = fdiv(id, rl), c = id - i * nl;
     base[(size_t)i * es + c] = buf[id];
   }
 }
 
-// True when a whole Ix x Iy plane fits one CTA of k_fft_plane.
+// True when a whole Ix x Iy plane fits one CTA of k_fft_plane with nt
+// threads.
 template <typename T>
-static bool plane_fits(const FftLen& fx, const FftLen& fy) {
+static bool plane_fits(const FftLen& fx, const FftLen& fy, int nt = kFftThreads) {
   constexpr int CAP = FftCap<T>::v;
   const int C = fx.n / 2 + 1;
   const size_t smem = (size_t)(fx.n + fy.n) * sizeof(typename C2<T>::tw) +
                       (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(typename C2<T>::t);
-  return max_lines(fx, CAP) >= fy.n / 2 && max_lines(fy, CAP) >= C &&
-         (fy.n / 2) * C <= kFftThreads * (CAP / 2) && smem <= (size_t)kMaxDynSmem;
+  return max_lines(fx, CAP, nt) >= fy.n / 2 && max_lines(fy, CAP, nt) >= C &&
+         (fy.n / 2) * C <= nt * (CAP / 2) && smem <= (size_t)kMaxDynSmem;
+}
+
+// Fewest threads (a multiple of 128) whose CTA holds the whole plane: small
+// planes (the long range's proxy planes) do not need 1024 threads.
+template <typename T>
+static int plane_threads(const FftLen& fx, const FftLen& fy) {
+  for (int nt = 128; nt < kFftThreads; nt *= 2)
+    if (plane_fits<T>(fx, fy, nt)) return nt;
+  return kFftThreads;
 }
 
 template <typename T>
@@ -455,7 +508,8 @@ static cudaError_t launch_plane(T* data, const FftLen& fx, const FftLen& fy, con
   using T4 = typename C2<T>::tw;
   const size_t sm = (size_t)(fx.n + fy.n) * sizeof(T4) +
                     (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(T2);
-  k_fft_plane<T><<<nplanes, kFftThreads, sm, s>>>(data, fx, fy, reinterpret_cast<const T4*>(tw),
+  k_fft_plane<T><<<nplanes, plane_threads<T>(fx, fy), sm, s>>>(data, fx, fy,
+                                                                reinterpret_cast<const T4*>(tw),
                                                   inv);
   return cudaGetLastError();
 }

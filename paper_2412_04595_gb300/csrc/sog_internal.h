@@ -15,6 +15,22 @@ constexpr int kMaxFftStages = 16;
 constexpr int kMaxCheb = 64;
 constexpr int kMaxWin = 16;
 constexpr int kNearD = 8;  // degree of the near-field table polynomials
+constexpr int kMaxHalfModes = 256;  // long range by direct sums: half-plane modes
+constexpr int kModeBlocks = 152;    // CTAs of its moment sums
+constexpr int kMaxHalfModeCoefs = 8192;  // half-plane modes x P_cheb (on-chip table)
+
+// Half-plane mode idx of the direct long range: n_x = 0 with n_y = 1..Ky,
+// then n_x = 1..Kx with n_y = -Ky..Ky (the other half are the conjugates).
+__host__ __device__ inline void half_mode(int idx, int Ky, int& nx, int& ny) {
+  if (idx < Ky) {
+    nx = 0;
+    ny = idx + 1;
+  } else {
+    const int i = idx - Ky;
+    nx = 1 + i / (2 * Ky + 1);
+    ny = i % (2 * Ky + 1) - Ky;
+  }
+}
 
 // One FFT length: radix sequence of the Stockham stages and the offset of its
 // n roots of unity exp(-2 pi i t / n) in the twiddle table.
@@ -145,6 +161,10 @@ struct sog_plan {
   int long_small;        // long planes small enough for one private copy per CTA
   int long_small_blocks;
   void* d_long_partial;  // per-CTA copies of the long planes (small path)
+  int long_direct;       // long range by direct Fourier sums (Algorithm 3)
+  int n_half;            // its half-plane modes
+  double* d_lmom;        // per-block partial moments [block][mode][n][re, im]
+  void* d_lcoef;         // coefficients [mode][n][re, im] in the element type
   int launch_error;
   cudaStream_t last_stream;
   // stage timers (sog_plan_set_timing) and kernel launch count of the last eval

@@ -1296,6 +1296,243 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
 }
 
 // ---------------------------------------------------------------------------
+// 4b. long range by direct Fourier sums (Algorithm 3, no FFT), in the same
+//     anterpolation reading: moments mu_n(k) = sum_j q_j T_n(x_j) e^{-ik.rho_j}
+//     over the half-plane modes, coefficients c_n(k) = K_k mu(k), and
+//     Phi_i = sum_k Re[e^{ik.rho_i} sum_n c_n(k) T_n(x_i)] (the conjugate
+//     modes are folded into the factor 2 of K_k).
+// ---------------------------------------------------------------------------
+
+constexpr int kModeThreads = 256, kModeBatch = 128;
+
+template <typename T>
+struct Cx {
+  T x, y;
+};
+template <typename T>
+__device__ __forceinline__ Cx<T> cxmul(Cx<T> a, Cx<T> b) {
+  return Cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__device__ __forceinline__ void dsincospi(float a, float* s, float* c) { sincospif(a, s, c); }
+__device__ __forceinline__ void dsincospi(double a, double* s, double* c) { sincospi(a, s, c); }
+
+// e^{sgn i 2 pi n t / L} for n = n0 .. n0 + cnt - 1: the first by sincospi,
+// the rest by products with the step.
+template <typename T>
+__device__ __forceinline__ void cis_run(T t, double L, int n0, int cnt, T sgn, Cx<T>* out,
+                                        int stride) {
+  const T a = (T)(2.0 / L) * t;
+  T s, c;
+  dsincospi(a, &s, &c);
+  const Cx<T> step{c, sgn * s};
+  dsincospi(a * (T)n0, &s, &c);
+  Cx<T> v{c, sgn * s};
+  for (int k = 0; k < cnt; ++k) {
+    out[k * stride] = v;
+    v = cxmul(v, step);
+  }
+}
+
+// Per-block partial moments.  A batch of nbt particles is staged (q T_n,
+// e^{-ik_x x}, e^{-ik_y y}); thread (mode, group) sums the batch's particles
+// j = group (mod groups) for its mode in the element type; at the end the
+// groups are added in a fixed order, kModeRed orders at a time, and written
+// in FP64.
+constexpr int kModeRed = 16;
+
+template <typename T, int PMAX>
+__global__ void __launch_bounds__(kModeThreads) k_lmodes_moments(
+    const T* __restrict__ q, const T* __restrict__ r, int N, int P, int Kx, int Ky, int nhalf,
+    int nbt, double Lx, double Ly, double halfLz, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ny_all = 2 * Ky + 1;
+  T* tq = reinterpret_cast<T*>(smraw);                   // [j][PMAX]
+  Cx<T>* ex = reinterpret_cast<Cx<T>*>(tq + nbt * PMAX);  // [j][Kx + 1]
+  Cx<T>* ey = ex + nbt * (Kx + 1);                        // [j][2 Ky + 1]
+  const int G = kModeThreads / nhalf;
+  const int mode = threadIdx.x % nhalf, grp = threadIdx.x / nhalf;
+  const bool active = grp < G;
+  int nx = 0, ny = 0;
+  half_mode(mode, Ky, nx, ny);
+  T acc[PMAX][2];
+#pragma unroll
+  for (int n = 0; n < PMAX; ++n) acc[n][0] = acc[n][1] = T(0);
+  const int per = (N + gridDim.x - 1) / gridDim.x;
+  const int b = blockIdx.x * per, e = min(N, b + per);
+  const double ih = 1.0 / halfLz;
+  for (int p0 = b; p0 < e; p0 += nbt) {
+    const int nb = min(nbt, e - p0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      const int i = p0 + j;
+      double z = (double)r[3 * i + 2];
+      if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
+      const T x = (T)(z * ih);
+      T qi = q[i];
+      if (!isfinite((double)qi)) qi = T(0);
+      T t0 = T(1), t1 = x;
+#pragma unroll
+      for (int n = 0; n < PMAX; ++n) {
+        tq[j * PMAX + n] = n < P ? qi * t0 : T(0);
+        const T t2 = T(2) * x * t1 - t0;
+        t0 = t1;
+        t1 = t2;
+      }
+      cis_run(r[3 * i], Lx, 0, Kx + 1, T(-1), ex + j * (Kx + 1), 1);
+      cis_run(r[3 * i + 1], Ly, -Ky, ny_all, T(-1), ey + j * ny_all, 1);
+    }
+    __syncthreads();
+    if (active) {
+      for (int j = grp; j < nb; j += G) {
+        const Cx<T> ph = cxmul(ex[j * (Kx + 1) + nx], ey[j * ny_all + ny + Ky]);
+        const T* tj = tq + j * PMAX;
+#pragma unroll
+        for (int n = 0; n < PMAX; ++n) {
+          acc[n][0] += ph.x * tj[n];
+          acc[n][1] += ph.y * tj[n];
+        }
+      }
+    }
+  }
+  // groups -> fixed-order sum, kModeRed orders at a time (reuses the staging)
+  T* red = reinterpret_cast<T*>(smraw);  // [thread][kModeRed][2]
+#pragma unroll
+  for (int c0 = 0; c0 < PMAX; c0 += kModeRed) {
+    if (c0 < P) {
+      __syncthreads();
+      if (active) {
+#pragma unroll
+        for (int k = 0; k < kModeRed; ++k) {
+          red[(threadIdx.x * kModeRed + k) * 2] = acc[c0 + k][0];
+          red[(threadIdx.x * kModeRed + k) * 2 + 1] = acc[c0 + k][1];
+        }
+      }
+      __syncthreads();
+      const int pc = min(kModeRed, P - c0);
+      for (int idx = threadIdx.x; idx < nhalf * pc; idx += blockDim.x) {
+        const int md = idx / pc, k = idx - md * pc;
+        double sr = 0.0, si = 0.0;
+        for (int g = 0; g < G; ++g) {
+          sr += (double)red[((g * nhalf + md) * kModeRed + k) * 2];
+          si += (double)red[((g * nhalf + md) * kModeRed + k) * 2 + 1];
+        }
+        double* o = part + (((size_t)blockIdx.x * nhalf + md) * P + c0 + k) * 2;
+        o[0] = sr;
+        o[1] = si;
+      }
+    }
+  }
+}
+
+// Coefficients: one block per half-plane mode.  Thread t takes the value
+// t mod 2P (order n, real or imaginary part) of the blocks b = t / 2P (mod
+// groups) in a fixed order, the groups are added in a fixed order in FP64,
+// and the mode's P x P kernel is applied.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lmodes_coeffs(const double* __restrict__ part, int nblk,
+                                                       int nhalf, int P, const T* __restrict__ K,
+                                                       T* __restrict__ coef) {
+  __shared__ double gs[256];
+  __shared__ double mu[kMaxCheb * 2];
+  const int mode = blockIdx.x;
+  const int w = 2 * P, G = blockDim.x / w;
+  const int v = threadIdx.x % w, g = threadIdx.x / w;
+  double s = 0.0;
+  if (g < G)
+    for (int b = g; b < nblk; b += G) s += part[((size_t)b * nhalf + mode) * w + v];
+  gs[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < w) {
+    double t = 0.0;
+    for (int k = 0; k < G; ++k) t += gs[k * w + threadIdx.x];
+    mu[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < w) {
+    const int n = threadIdx.x >> 1, c = threadIdx.x & 1;
+    const T* Km = K + ((size_t)mode * P + n) * P;
+    double acc = 0.0;
+    for (int n2 = 0; n2 < P; ++n2) acc += (double)Km[n2] * mu[2 * n2 + c];
+    coef[(size_t)mode * w + threadIdx.x] = (T)acc;
+  }
+}
+
+// Potential and gradient of the long range at every particle (input order).
+template <typename T, int PMAX>
+__global__ void __launch_bounds__(kModeThreads) k_lmodes_eval(
+    const T* __restrict__ r, int N, int P, int Kx, int Ky, int nhalf, double Lx, double Ly,
+    double halfLz, const T* __restrict__ coef, double* __restrict__ phi_out,
+    double* __restrict__ grad_out) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Cx<T>* c = reinterpret_cast<Cx<T>*>(smraw);  // [mode][P]
+  for (int i = threadIdx.x; i < nhalf * P; i += blockDim.x)
+    c[i] = Cx<T>{coef[2 * i], coef[2 * i + 1]};
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double z = (double)r[3 * i + 2];
+  if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
+  const T x = (T)(z / halfLz);
+  T tn[PMAX], dn[PMAX];
+  {
+    T t0 = T(1), t1 = x, d0 = T(0), d1 = T(1);
+#pragma unroll
+    for (int n = 0; n < PMAX; ++n) {
+      tn[n] = t0;
+      dn[n] = d0;
+      const T t2 = T(2) * x * t1 - t0;
+      const T d2 = T(2) * t1 + T(2) * x * d1 - d0;
+      t0 = t1;
+      t1 = t2;
+      d0 = d1;
+      d1 = d2;
+    }
+  }
+  const T kx1 = (T)(2.0 * 3.14159265358979323846 / Lx), ky1 = (T)(2.0 * 3.14159265358979323846 / Ly);
+  const T xv = r[3 * i], yv = r[3 * i + 1];
+  T sa, ca, sb, cb;
+  dsincospi((T)(2.0 / Lx) * xv, &sa, &ca);
+  dsincospi((T)(2.0 / Ly) * yv, &sb, &cb);
+  const Cx<T> stepx{ca, sa}, stepy{cb, sb};
+  T f = 0, gx = 0, gy = 0, gz = 0;
+  Cx<T> exv{T(1), T(0)};
+  int md = 0;
+  for (int mx = 0; mx <= Kx; ++mx) {
+    // e^{i ky y} from n_y = 1 (mx = 0) or -Ky (mx > 0)
+    const int ny0 = mx == 0 ? 1 : -Ky;
+    T s0, c0;
+    dsincospi((T)(2.0 / Ly) * yv * (T)ny0, &s0, &c0);
+    Cx<T> eyv{c0, s0};
+    for (int my = ny0; my <= Ky; ++my, ++md) {
+      const Cx<T> ph = cxmul(exv, eyv);
+      const Cx<T>* cm = c + md * P;
+      T Sr = 0, Si = 0, Zr = 0, Zi = 0;
+#pragma unroll
+      for (int n = 0; n < PMAX; ++n) {
+        if (n < P) {
+          const Cx<T> cn = cm[n];
+          Sr += cn.x * tn[n];
+          Si += cn.y * tn[n];
+          Zr += cn.x * dn[n];
+          Zi += cn.y * dn[n];
+        }
+      }
+      const T re = ph.x * Sr - ph.y * Si, im = ph.x * Si + ph.y * Sr;
+      f += re;
+      gx -= (T)mx * kx1 * im;
+      gy -= (T)my * ky1 * im;
+      gz += ph.x * Zr - ph.y * Zi;
+      eyv = cxmul(eyv, stepy);
+    }
+    exv = cxmul(exv, stepx);
+  }
+  phi_out[i] = (double)f;
+  grad_out[3 * i] = (double)gx;
+  grad_out[3 * i + 1] = (double)gy;
+  grad_out[3 * i + 2] = (double)gz / halfLz;
+}
+
+// ---------------------------------------------------------------------------
 // 5. k = 0 mode of the long range, FP64
 // ---------------------------------------------------------------------------
 
@@ -1547,8 +1784,9 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     g.ntm[d] = p->gm.nt[d];
     g.iTm[d] = p->has_mid ? 1.0 / p->gm.T[d] : 0.0;
   }
+  const int long_bins = p->has_long && !p->long_direct;  // direct sums need no tiles
   g.has_mid = p->has_mid;
-  g.has_long = p->has_long;
+  g.has_long = long_bins;
   g.Lzs_half = 0.5 * p->Lzs;
   for (int d = 0; d < 2; ++d) {
     g.ihl[d] = p->has_long ? 1.0 / p->hl[d] : 0.0;
@@ -1559,7 +1797,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   g.ihalfLz = 2.0 / m.L[2];
   const int3 off = make_int3(p->cnt_off[0], p->cnt_off[1], p->cnt_off[2]);
   const int3 nb = make_int3(p->n_cells, p->has_mid ? p->n_tiles_mid : 0,
-                            p->has_long ? p->n_tiles_long : 0);
+                            long_bins ? p->n_tiles_long : 0);
   P4<T>* rn = reinterpret_cast<P4<T>*>(p->d_rec_near);
   P4<T>* rm = reinterpret_cast<P4<T>*>(p->d_rec_mid);
   P4<T>* rl = reinterpret_cast<P4<T>*>(p->d_rec_long);
@@ -1573,7 +1811,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   LAUNCH_CHECK();
   k_scan3<<<3, 1024, 0, s>>>(p->d_cnt, off, nb);
   LAUNCH_CHECK();
-  k_bin_scatter<T><<<(N + 255) / 256, 256, 0, s>>>(N, p->has_mid, p->has_long, p->d_key,
+  k_bin_scatter<T><<<(N + 255) / 256, 256, 0, s>>>(N, p->has_mid, long_bins, p->d_key,
                                                    p->d_rank, p->d_cnt, off, tmp, rn, rm, rl,
                                                    p->d_perm);
   LAUNCH_CHECK();
@@ -1634,9 +1872,48 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   // 4-5. long range and its k = 0 mode, on long_stream
   const cudaStream_t sl = p->long_stream;
   SOG_CK(cudaStreamWaitEvent(sl, p->ev_fork, 0));
-  if (p->has_long) {
+  if (p->has_long && p->long_direct) {
+    const int P = m.P_cheb, Kx = (m.I_long[0] - 1) / 2, Ky = (m.I_long[1] - 1) / 2;
+    const int nh = p->n_half;
+    const int pmax = P <= 16 ? 16 : (P <= 32 ? 32 : 64);
+    // staging batch: kModeBatch particles, fewer if their tables would not fit
+    const size_t per_part = (size_t)(pmax + 2 * (Kx + 1) + 2 * (2 * Ky + 1)) * sizeof(T);
+    int nbt = kModeBatch;
+    while (nbt > 8 && (size_t)nbt * per_part > (size_t)kMaxDynSmem) nbt /= 2;
+    const size_t sm1 = std::max((size_t)nbt * per_part,
+                                (size_t)kModeThreads * kModeRed * 2 * sizeof(T));
+    const size_t sm3 = (size_t)nh * P * 2 * sizeof(T);
+    const double hz = 0.5 * m.L[2];
     mark_begin(p, 5, sl);
+    if (pmax == 16)
+      k_lmodes_moments<T, 16><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, m.L[0], m.L[1], hz, p->d_lmom);
+    else if (pmax == 32)
+      k_lmodes_moments<T, 32><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, m.L[0], m.L[1], hz, p->d_lmom);
+    else
+      k_lmodes_moments<T, 64><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, m.L[0], m.L[1], hz, p->d_lmom);
+    LAUNCH_CHECK();
+    mark_end(p, 5, sl);
+    mark_begin(p, 6, sl);
+    k_lmodes_coeffs<T><<<nh, 256, 0, sl>>>(p->d_lmom, kModeBlocks, nh, P,
+                                                     reinterpret_cast<const T*>(p->d_kmat),
+                                                     reinterpret_cast<T*>(p->d_lcoef));
+    LAUNCH_CHECK();
+    mark_end(p, 6, sl);
+    mark_begin(p, 7, sl);
+    const T* cf = reinterpret_cast<const T*>(p->d_lcoef);
+    if (pmax == 16)
+      k_lmodes_eval<T, 16><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, m.L[0], m.L[1], hz, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
+    else if (pmax == 32)
+      k_lmodes_eval<T, 32><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, m.L[0], m.L[1], hz, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
+    else
+      k_lmodes_eval<T, 64><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, m.L[0], m.L[1], hz, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
+    LAUNCH_CHECK();
+    mark_end(p, 7, sl);
+  }
+  if (p->has_long) {
     const int P = m.P_cheb;
+    if (!p->long_direct) {
+    mark_begin(p, 5, sl);
     T* A = reinterpret_cast<T*>(p->d_lA);
     T* B = reinterpret_cast<T*>(p->d_lB);
     const WinT<T> w = wint<T>(p->wl);
@@ -1683,6 +1960,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
                     p->d_perm + 2 * (size_t)N, B, sc, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     LAUNCH_CHECK();
     mark_end(p, 7, sl);
+    }
     mark_begin(p, 8, sl);
     double* mpart = p->d_red + 2 * kRedBlocks;
     if (P <= 16)
@@ -1728,6 +2006,15 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
 
 template <typename T>
 static cudaError_t prepare_t() {
+  {
+    cudaError_t e0 = allow_smem(k_lmodes_moments<T, 16>);
+    if (e0 == cudaSuccess) e0 = allow_smem(k_lmodes_moments<T, 32>);
+    if (e0 == cudaSuccess) e0 = allow_smem(k_lmodes_moments<T, 64>);
+    if (e0 == cudaSuccess) e0 = allow_smem(k_lmodes_eval<T, 16>);
+    if (e0 == cudaSuccess) e0 = allow_smem(k_lmodes_eval<T, 32>);
+    if (e0 == cudaSuccess) e0 = allow_smem(k_lmodes_eval<T, 64>);
+    if (e0 != cudaSuccess) return e0;
+  }
   cudaError_t e = allow_pw<T, 0>();
   if (e == cudaSuccess) e = allow_pw<T, 6>();
   if (e == cudaSuccess) e = allow_pw<T, 8>();

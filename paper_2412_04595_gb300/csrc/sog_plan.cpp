@@ -118,7 +118,7 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
 
   bool have = false;
   long best_cost = 0;
-  int bm = 0, bI[3] = {0, 0, 0}, bPw = 0, bIl[2] = {0, 0}, bPl = 0, bPc = 0;
+  int bm = 0, bI[3] = {0, 0, 0}, bPw = 0, bIl[2] = {0, 0}, bPl = 0, bPc = 0, bdirect = 0;
   double bhz = 0.0;
   for (int m = -1; m <= M; ++m) {
     long cost = 0;
@@ -141,7 +141,7 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
       const long G = (long)Ix * Iy * Izs;
       cost += 4 * N * (long)Pw * Pw * Pw + 10 * G * clog2(G);
     }
-    int Ilx = 0, Ily = 0, Pl = 0, Pc = 0;
+    int Ilx = 0, Ily = 0, Pl = 0, Pc = 0, direct = 0;
     if (m < M) {
       const double s1 = s[m + 1];
       const double Kl = 2.0 * sqrt(lne) / s1;
@@ -166,8 +166,21 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
       }
       if (Pc == 0) continue;
       const long Gl = (long)Ilx * Ily;
-      cost += 4 * N * (long)Pl * Pl * Pc + 10 * Gl * Pc * clog2(Gl) + 2 * Gl * (long)Pc * Pc +
-              N * (long)Pc;
+      const long cost_grid = 4 * N * (long)Pl * Pl * Pc + 10 * Gl * Pc * clog2(Gl) +
+                             2 * Gl * (long)Pc * Pc + N * (long)Pc;
+      // Algorithm 3: direct sums over the modes |k| <= Kl (no window, no FFT)
+      const long Kdx = (long)ceil(Kl * Lx / (2.0 * kPi)), Kdy = (long)ceil(Kl * Ly / (2.0 * kPi));
+      const long nhalf = Kdy + Kdx * (2 * Kdy + 1);
+      const long cost_direct = 4 * N * nhalf * (long)Pc;
+      if (nhalf >= 1 && nhalf <= sogk::kMaxHalfModes &&
+          nhalf * Pc <= sogk::kMaxHalfModeCoefs && cost_direct < cost_grid) {
+        direct = 1;
+        Ilx = (int)(2 * Kdx + 1);
+        Ily = (int)(2 * Kdy + 1);
+        cost += cost_direct;
+      } else {
+        cost += cost_grid;
+      }
     }
     if (!have || cost < best_cost) {
       have = true;
@@ -182,6 +195,7 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
       bIl[1] = Ily;
       bPl = Pl;
       bPc = Pc;
+      bdirect = direct;
     }
   }
   if (!have) return SOG_ERR_PARAMS;
@@ -206,6 +220,7 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
   out->shape_long = shape_default(window, out->P_long);
   out->P_cheb = bPc;
   out->window = window;
+  out->long_direct = bdirect;
   return SOG_OK;
 }
 
@@ -232,12 +247,23 @@ sog_status check_params(const sog_params& p) {
       return SOG_ERR_PARAMS;
     if (!(p.shape > 0.0)) return SOG_ERR_PARAMS;
   }
+  if (p.long_direct != 0 && p.long_direct != 1) return SOG_ERR_PARAMS;
   if (p.m < p.M) {
+    if (p.P_cheb < 2 || p.P_cheb > sogk::kMaxCheb) return SOG_ERR_PARAMS;
+    if (p.long_direct) {
+      for (int d = 0; d < 2; ++d)
+        if (p.I_long[d] < 1 || p.I_long[d] % 2 != 1) return SOG_ERR_PARAMS;
+      const int Kx = (p.I_long[0] - 1) / 2, Ky = (p.I_long[1] - 1) / 2;
+      const int nhalf = Ky + Kx * (2 * Ky + 1);
+      if (nhalf < 1 || nhalf > sogk::kMaxHalfModes ||
+          nhalf * p.P_cheb > sogk::kMaxHalfModeCoefs)
+        return SOG_ERR_PARAMS;
+      return SOG_OK;
+    }
     for (int d = 0; d < 2; ++d)
       if (!smooth_even(p.I_long[d])) return SOG_ERR_PARAMS;
     if (p.P_long < 2 || p.P_long > sogk::kMaxWin || p.P_long > std::min(p.I_long[0], p.I_long[1]))
       return SOG_ERR_PARAMS;
-    if (p.P_cheb < 2 || p.P_cheb > sogk::kMaxCheb) return SOG_ERR_PARAMS;
     if (!(p.shape_long > 0.0)) return SOG_ERR_PARAMS;
   }
   return SOG_OK;
@@ -518,7 +544,12 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     ch = std::max(1, std::min(ch, (int)(per_tile / 32.0)));
     g.chunks = std::max(1, ch);
   }
-  if (p->has_long) {
+  p->long_direct = p->has_long && prm.long_direct;
+  if (p->long_direct) {
+    p->n_half = (Ily - 1) / 2 + (Ilx - 1) / 2 * Ily;  // Ky + Kx (2 Ky + 1)
+    p->long_small = 0;
+  }
+  if (p->has_long && !p->long_direct) {
     p->hl[0] = L[0] / Ilx;
     p->hl[1] = L[1] / Ily;
     p->wl = sogk::WinPar{prm.P_long, prm.window, 0.5 * (prm.P_long - 1), prm.shape_long};
@@ -572,14 +603,15 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     add_len(Iy, p->fy);
     add_len(Iz, p->fz);
   }
-  if (p->has_long) {
+  if (p->has_long && !p->long_direct) {
     add_len(Ilx, p->flx);
     add_len(Ily, p->fly);
   }
   if (tw.empty()) tw.assign(4, 0.0);
   if ((p->has_mid && !(sogk::fft_len_ok(prec, p->fx) && sogk::fft_len_ok(prec, p->fy) &&
                        sogk::fft_len_ok(prec, p->fz))) ||
-      (p->has_long && !(sogk::fft_len_ok(prec, p->flx) && sogk::fft_len_ok(prec, p->fly)))) {
+      (p->has_long && !p->long_direct &&
+       !(sogk::fft_len_ok(prec, p->flx) && sogk::fft_len_ok(prec, p->fly)))) {
     delete p;
     return SOG_ERR_PARAMS;  // a grid dimension too long for the shared-memory FFT
   }
@@ -661,14 +693,36 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
           Bl[((size_t)li * P + n) * P + n2] = a;
         }
     }
+    if (p->long_direct) {
+      // Algorithm 3: per half-plane mode (pi/A) sum_l w_l s_l^2 e^{-s_l^2 k^2/4} B_l,
+      // doubled for the conjugate mode (the potential is the real part)
+      const int Ky = (Ily - 1) / 2;
+      kmat.assign((size_t)p->n_half * P * P, 0.0);
+      for (int h = 0; h < p->n_half; ++h) {
+        int nx, ny;
+        sogk::half_mode(h, Ky, nx, ny);
+        const double kxv = 2.0 * kPi * nx / L[0], kyv = 2.0 * kPi * ny / L[1];
+        const double k2 = kxv * kxv + kyv * kyv;
+        double* K = &kmat[(size_t)h * P * P];
+        for (int li = 0; li < nl; ++li) {
+          const int l = prm.m + 1 + li;
+          const double ex = s[l] * s[l] * k2 / 4.0;
+          if (ex > 80.0) break;
+          const double al = 2.0 * kPi / A * w[l] * s[l] * s[l] * exp(-ex);
+          const double* B = &Bl[(size_t)li * P * P];
+          for (int i = 0; i < P * P; ++i) K[i] += al * B[i];
+        }
+      }
+    }
     const int C = Ilx / 2 + 1;
-    const size_t kbytes = (size_t)Ily * C * P * P * es;
+    const size_t kbytes = p->long_direct ? 0 : (size_t)Ily * C * P * P * es;
     // per-mode P x P kernels: up to 32 GB (a 1176^2 long grid with P = 24,
     // the 1000 x 1000 x 10 slab at 1e6 particles, needs 1.6 GB in FP32)
     if (kbytes > ((size_t)32 << 30)) {
       delete p;
       return SOG_ERR_PARAMS;
     }
+    if (!p->long_direct) {
     const double shp = eff_shape(prm.shape_long, prec), hw = eff_half(p->wl.half, prec);
     WinFT fx(prm.window, shp, hw * p->hl[0]);
     WinFT fy(prm.window, shp, hw * p->hl[1]);
@@ -701,6 +755,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     for (int t = 1; t < nthr; ++t) pool.emplace_back(rows, t, nthr);
     rows(0, nthr);
     for (auto& th : pool) th.join();
+    }
     // k = 0: (pi/A) C^T K0 C, K0(d) = -sum_{l>m} w_l d^2 phi1(d^2/s_l^2)
     std::vector<double> K0((size_t)P * P, 0.0);
     for (int c = 0; c < P; ++c)
@@ -760,6 +815,11 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   const size_t o_host = ar.take((size_t)N * 8 * es + sizeof(double));
   const size_t o_lpart = ar.take(p->has_long && p->long_small
                                      ? (size_t)p->long_small_blocks * P * Ilx * Ily * es : 0);
+  // direct long range: per-block partial moments (FP64) and the coefficients
+  const size_t o_lmom = ar.take(p->long_direct
+                                    ? (size_t)sogk::kModeBlocks * p->n_half * P * 2 * sizeof(double)
+                                    : 0);
+  const size_t o_lcoef = ar.take(p->long_direct ? (size_t)p->n_half * P * 2 * es : 0);
   void* base = nullptr;
   if (cudaMalloc(&base, ar.size) != cudaSuccess) {
     cudaGetLastError();
@@ -792,6 +852,8 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   p->d_status = reinterpret_cast<int*>(b + o_st);
   p->d_host_stage = b + o_host;
   p->d_long_partial = b + o_lpart;
+  p->d_lmom = reinterpret_cast<double*>(b + o_lmom);
+  p->d_lcoef = b + o_lcoef;
 
   // upload tables (one host staging buffer)
   std::vector<unsigned char> host(tables_end, 0);

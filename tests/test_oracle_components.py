@@ -64,6 +64,21 @@ def test_long_range_vs_closed_form(oracle_mod, sysA):
     assert np.max(np.abs(gl - gc)) < 1e-6 * scale
 
 
+def test_long_range_direct_vs_closed_form(oracle_mod, sysA):
+    """Algorithm 3 (direct Fourier sums, no window): with enough modes and
+    Chebyshev points it reproduces Eq. 4.40 summed directly; with a cut at
+    the selection's K_max it stays within the tolerance."""
+    q, r, L, prm = sysA
+    pc, gc = oracle_mod.long_closed_form(prm, q, r, with_k0=False)
+    scale = np.max(np.abs(pc))
+    pd, gd = oracle_mod.long_range_direct(dict(prm, P_cheb=24, I_long=(41, 41)), q, r)
+    assert np.max(np.abs(pd - pc)) < 1e-10 * scale
+    assert np.max(np.abs(gd - gc)) < 1e-9 * scale
+    pg, gg = oracle_mod.long_range(dict(prm, P_cheb=24, P_long=12, shape_long=1.9 * 12,
+                                        I_long=(24, 24)), q, r)
+    assert np.max(np.abs(pd - pg)) < 1e-7 * scale
+
+
 def test_long_k0_vs_closed_form(oracle_mod, sysA):
     q, r, L, prm = sysA
     pc, gc = oracle_mod.long_closed_form(prm, q, r, with_k0=True)

@@ -43,6 +43,18 @@ def test_selection_meets_its_constraints(oracle_mod, N, L, tol):
         assert pad >= s[m] * math.sqrt(math.log(1 / eps)) - 1e-9
         assert pad >= (prm["P_win"] - 1) * prm["hz"] - 1e-9
     if m < prm["M"]:
-        assert all(smooth8(n) for n in prm["I_long"])
-        assert min(prm["I_long"]) >= prm["P_long"] + 4
         assert prm["P_cheb"] >= 2
+        if prm["long_direct"]:
+            # Algorithm 3: odd mode counts 2K+1 whose modes cover |k| <= K_long
+            # in each direction, at most 256 half-plane modes
+            Kl = 2 * math.sqrt(math.log(1 / (0.3 * tol))) / s[m + 1]
+            Ix, Iy = prm["I_long"]
+            assert Ix % 2 == 1 and Iy % 2 == 1
+            Kx, Ky = (Ix - 1) // 2, (Iy - 1) // 2
+            assert 2 * math.pi * Kx / Lx >= Kl * (1 - 1e-12)
+            assert 2 * math.pi * Ky / Ly >= Kl * (1 - 1e-12)
+            assert Ky + Kx * (2 * Ky + 1) <= 256
+            assert (Ky + Kx * (2 * Ky + 1)) * prm["P_cheb"] <= 8192
+        else:
+            assert all(smooth8(n) for n in prm["I_long"])
+            assert min(prm["I_long"]) >= prm["P_long"] + 4
