@@ -133,6 +133,13 @@ def stage_units(prm, N, stage):
         Pc = prm["P_cheb"]
         Ilx, Ily = prm["I_long"]
         return "alu", N * Pc * Ilx * Ily * 2.0, "FP32 flop: N x P_cheb x I_long^2 x 2 (dense planes)"
+    if stage in ("long_moments", "long_eval"):
+        Pc = prm["P_cheb"]
+        Kx, Ky = (prm["I_long"][0] - 1) // 2, (prm["I_long"][1] - 1) // 2
+        nh = Ky + Kx * (2 * Ky + 1)
+        k = 4.0 if stage == "long_moments" else 8.0
+        return ("alu", N * nh * Pc * k,
+                "FP32 flop: N x half-plane modes x P_cheb x %d" % k)
     return None, None, None
 
 

@@ -192,6 +192,8 @@ sog_status sog_plan_check(sog_plan* plan);
  *   4 mid gathering (Eq. 3.10) 5 long gridding onto proxy planes
  *   6 long 2D FFTs and z-contraction (Eq. 3.17)
  *   7 long gathering (Eq. 3.19) 8 k = 0 mode       9 assembly and energy
+ * With long_direct (Algorithm 3) stages 5-7 are the mode moments, the mode
+ * coefficients and the evaluation at the particles.
  */
 #define SOG_NSTAGES 10
 sog_status sog_plan_set_timing(sog_plan* plan, int32_t enable);

@@ -260,6 +260,8 @@ class Plan:
 
     STAGES = ("binning", "near", "mid_spread", "mid_fft", "mid_gather", "long_spread",
               "long_fft", "long_gather", "k0", "assemble")
+    # long range by direct sums (Algorithm 3): moments, coefficients, evaluation
+    STAGES_DIRECT = STAGES[:5] + ("long_moments", "long_coeffs", "long_eval") + STAGES[8:]
 
     def set_timing(self, enable: bool):
         _check(self._lib.sog_plan_set_timing(self._h, int(bool(enable))), "sog_plan_set_timing")
@@ -268,7 +270,8 @@ class Plan:
         """Device milliseconds of each stage of the last evaluation."""
         buf = (ctypes.c_float * len(self.STAGES))()
         _check(self._lib.sog_plan_get_timing(self._h, buf), "sog_plan_get_timing")
-        return dict(zip(self.STAGES, [float(x) for x in buf]))
+        names = self.STAGES_DIRECT if self.params.get("long_direct") else self.STAGES
+        return dict(zip(names, [float(x) for x in buf]))
 
     def launches(self) -> int:
         return int(self._lib.sog_plan_launches(self._h))
