@@ -90,6 +90,28 @@ __device__ __forceinline__ void win_eval(const WinT<T>& w, T v, T& val, T& dval)
   }
 }
 
+// A complex number (or a pair of values) in the element type.
+template <typename T>
+struct alignas(2 * sizeof(T)) Cx {
+  T x, y;
+};
+template <typename T>
+__device__ __forceinline__ Cx<T> cxmul(Cx<T> a, Cx<T> b) {
+  return Cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// Window value only (same arithmetic as win_eval's value).
+template <typename T>
+__device__ __forceinline__ T win_val(const WinT<T>& w, T v) {
+  const T one = T(1);
+  if (!(v >= -one && v <= one)) return T(0);
+  if (w.kind == SOG_WIN_ES) {
+    const T a2 = (one - v) * (one + v);
+    return dexp(-w.shape * (v * v / (one + dsqrt(a2))));
+  }
+  return dexp(-w.shape * v * v);
+}
+
 // ---------------------------------------------------------------------------
 // 1. binning
 // ---------------------------------------------------------------------------
@@ -391,20 +413,25 @@ __device__ __forceinline__ void near_pair(T r2, T q, T dx, T dy, T dz, const T* 
   gz += f * dz;
 }
 
-// One warp, one target.  Pass 1 tests the staged sources 32 at a time and
-// keeps one bit per source inside r_c (a ballot per step).  Pass 2 hands the
-// accepted sources to the lanes in order, 32 at a time (prefix counts of the
-// step masks, binary search, k-th set bit), and evaluates them with all
-// lanes busy.  SHIFT: sources carry a periodic shift s
-// (dx = (x_i + s) - (x_j - s), both brackets exact).
+// One warp, one target.  Pass 1 tests the staged sources 32 at a time (one
+// ballot per step) and appends the accepted ones to the warp's list of
+// source indices, in order; pass 2 hands the listed sources to the lanes, 32
+// per round, so that every round but the last has all lanes busy.  The list
+// holds kNearList entries: pass 1 runs in chunks of 8 steps and the list is
+// evaluated and emptied early when another chunk might not fit.  SHIFT:
+// sources carry a periodic shift s (dx = (x_i + s) - (x_j - s), both brackets
+// exact).
+constexpr int kNearList = 512;
+
 template <typename T, bool SHIFT>
 __device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restrict__ src,
                                             const S2<T>* __restrict__ sh, int nsteps, T rc2,
                                             const T* __restrict__ tab, int K, T hK, T ihK,
-                                            unsigned* __restrict__ msk, T& o_phi, T& o_gx, T& o_gy,
-                                            T& o_gz) {
+                                            unsigned short* __restrict__ list, T& o_phi, T& o_gx,
+                                            T& o_gy, T& o_gz) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
   auto diff = [&](int k, T& dx, T& dy, T& dz, T& q) {
     const P4<T> b = src[k];
     if (SHIFT) {
@@ -418,45 +445,39 @@ __device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restr
     dz = a.z - b.z;
     q = b.q;
   };
-  for (int st = 0; st < nsteps; ++st) {
-    T dx, dy, dz, q;
-    diff(st * 32 + lane, dx, dy, dz, q);
-    const T r2 = dx * dx + dy * dy + dz * dz;
-    // r2 == 0 only for the target itself (coincident charges are invalid input)
-    const unsigned m = __ballot_sync(full, r2 < rc2 && r2 > T(0));
-    if (lane == 0) msk[st] = m;
-  }
-  __syncwarp();
   Acc<T> phi{0, 0};
   T gx = 0, gy = 0, gz = 0;
-  for (int c0 = 0; c0 < nsteps; c0 += 32) {
-    const unsigned ms = c0 + lane < nsteps ? msk[c0 + lane] : 0u;
-    const int cnt = __popc(ms);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(full, incl, o);
-      if (lane >= o) incl += v;
-    }
-    const int total = __shfl_sync(full, incl, 31);
-    for (int h0 = 0; h0 < total; h0 += 32) {
-      const int h = min(h0 + lane, total - 1);
-      int sidx = 0;  // number of steps whose inclusive count is <= h
-#pragma unroll
-      for (int stp = 16; stp >= 1; stp >>= 1) {
-        const int v = __shfl_sync(full, incl, sidx + stp - 1);
-        if (v <= h) sidx += stp;
-      }
-      const int ex = __shfl_sync(full, incl, sidx) - __shfl_sync(full, cnt, sidx);
-      const unsigned mk = __shfl_sync(full, ms, sidx);
-      if (h0 + lane < total) {
-        const int k = (c0 + sidx) * 32 + nth_bit(mk, h - ex);
+  auto evaluate = [&](int cnt) {
+    __syncwarp();
+    for (int h0 = 0; h0 < cnt; h0 += 32) {
+      if (h0 + lane < cnt) {
         T dx, dy, dz, q;
-        diff(k, dx, dy, dz, q);
+        diff(list[h0 + lane], dx, dy, dz, q);
         near_pair(dx * dx + dy * dy + dz * dz, q, dx, dy, dz, tab, K, hK, ihK, phi, gx, gy, gz);
       }
     }
+    __syncwarp();
+  };
+  int cnt = 0;  // warp-uniform
+  for (int s0 = 0; s0 < nsteps; s0 += 8) {
+    const int s1 = min(nsteps, s0 + 8);
+    for (int st = s0; st < s1; ++st) {
+      T dx, dy, dz, q;
+      const int k = st * 32 + lane;
+      diff(k, dx, dy, dz, q);
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      // r2 == 0 only for the target itself (coincident charges are invalid input)
+      const bool in = r2 < rc2 && r2 > T(0);
+      const unsigned m = __ballot_sync(full, in);
+      if (in) list[cnt + __popc(m & below)] = (unsigned short)k;
+      cnt += __popc(m);
+    }
+    if (cnt > kNearList - 8 * 32) {
+      evaluate(cnt);
+      cnt = 0;
+    }
   }
+  evaluate(cnt);
   o_phi = phi.get();
   o_gx = gx;
   o_gy = gy;
@@ -479,7 +500,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
   constexpr int kNearSrc = NearCfg<T>::src, kNearTab = NearCfg<T>::tab;
   __shared__ P4<T> src[kNearSrc];                  // x - s, y - s, z, q
   __shared__ S2<T> shs[kNearSrc];                  // s (periodic shift) per source
-  __shared__ unsigned msk[kNearThreads / 32][kNearSrc / 32];  // accepted sources per step
+  __shared__ unsigned short list[kNearThreads / 32][kNearList];  // accepted sources per warp
   __shared__ T stab[kNearTab];
   __shared__ int cb[27], coff[28];
   __shared__ T csx[27], csy[27];
@@ -544,7 +565,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
   const T rc = (T)g.rc, rc2 = rc * rc;
   const T hK = rc / (T)g.K, ihK = (T)g.K / rc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNearThreads / 32;
-  unsigned* mymsk = msk[warp];
+  unsigned short* mylist = list[warp];
   const int ntg = te - tb;
   const int nsrc = coff[ncell];
   const bool shifted = any_shift != 0;
@@ -597,9 +618,9 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
         v2 = gy;
         v3 = gz;
       } else if (shifted) {
-        near_target<T, true>(a, src, shs, nsteps, rc2, tb_, g.K, hK, ihK, mymsk, v0, v1, v2, v3);
+        near_target<T, true>(a, src, shs, nsteps, rc2, tb_, g.K, hK, ihK, mylist, v0, v1, v2, v3);
       } else {
-        near_target<T, false>(a, src, shs, nsteps, rc2, tb_, g.K, hK, ihK, mymsk, v0, v1, v2, v3);
+        near_target<T, false>(a, src, shs, nsteps, rc2, tb_, g.K, hK, ihK, mylist, v0, v1, v2, v3);
       }
       v0 = warp_sum(v0);
       v1 = warp_sum(v1);
@@ -742,7 +763,14 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
   const int ty = (tile / g.nt[0]) % g.nt[1];
   const int tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo, oz = tz * g.T[2] - g.pad_lo;
-  for (int i = threadIdx.x; i < W2 * PS; i += blockDim.x) st[i] = A(0);
+  {
+    // the tile starts 16-byte aligned: zero it in 16-byte stores
+    constexpr int V = 16 / sizeof(A);
+    const int nv = W2 * PS / V;
+    int4* st4 = reinterpret_cast<int4*>(st);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) st4[i] = make_int4(0, 0, 0, 0);
+    for (int i = nv * V + threadIdx.x; i < W2 * PS; i += blockDim.x) st[i] = A(0);
+  }
   tile_tables(g, oy, oz, W2, false, yoff, zoff);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // scale of the fixed-point tile
@@ -755,7 +783,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
   for (int k = 0; k < nw; ++k) qsum += red[k];
   int ex = 0;
   frexp(qsum > T(0) ? qsum : T(1), &ex);  // qsum < 2^ex
-  const T S = (T)ldexp(1.0, FixAcc<T>::bits - ex), iS = (T)ldexp(1.0, ex - FixAcc<T>::bits);
+  const T S = ldexp(T(1), FixAcc<T>::bits - ex), iS = ldexp(T(1), ex - FixAcc<T>::bits);
   constexpr int NIT = PW > 0 ? (PW * PW + 31) / 32 : (kMaxWin * kMaxWin) / 32;
   constexpr int PR = PW > 0 ? PW : kMaxWin;
   int roff[NIT], rdy[NIT], rdz[NIT];  // this lane's (dz, dy) rows, roff -1: none
@@ -771,21 +799,18 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
   for (int p0 = b; p0 < e; p0 += kTileBatch) {
     const int nb = min(kTileBatch, e - p0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * 3 * kMaxWin; idx += blockDim.x) {
-      const int j = idx / (3 * kMaxWin);
-      const int r = idx - j * 3 * kMaxWin;
-      const int ax = r / kMaxWin, k = r - ax * kMaxWin;
-      if (k < P) {
-        const P4<T> a = rec[p0 + j];
-        const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
-        const int g0 = (int)dceil(c - w.half);
-        T v, dv;
-        win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
-        wgt[idx] = ax == 0 ? v * a.q : v;
-        if (r == 0) {
-          const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
-          bofs[j] = (gz0 + g.pad_lo) * PS + (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
-        }
+    for (int idx = threadIdx.x; idx < nb * 3 * P; idx += blockDim.x) {
+      const int j = idx / (3 * P);
+      const int r = idx - j * 3 * P;
+      const int ax = r / P, k = r - ax * P;
+      const P4<T> a = rec[p0 + j];
+      const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
+      const int g0 = (int)dceil(c - w.half);
+      const T v = win_val(w, ((T)(g0 + k) - c) * w.inv_half);
+      wgt[(j * 3 + ax) * kMaxWin + k] = ax == 0 ? v * a.q : v;
+      if (r == 0) {
+        const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
+        bofs[j] = (gz0 + g.pad_lo) * PS + (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
       }
     }
     __syncthreads();
@@ -808,6 +833,30 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
     }
   }
   __syncthreads();
+  if (sizeof(T) == 4 && ((ox | g.I[0] | g.pitch) & 1) == 0) {
+    // FP32: pairs of columns (x even, x + 1) with one 8-byte atomic; an even
+    // tile origin and even grid width keep a pair inside one row (for odd W0
+    // the last pair adds zero to the column after the tile)
+    const int W0h = (W0 + 1) >> 1, tot = W0h * W1 * W2;
+    const int nt = blockDim.x;
+    int lx = threadIdx.x % W0h, rr = threadIdx.x / W0h;
+    int ly = rr % W1, lz = rr / W1;
+    const int sx = nt % W0h, sr = nt / W0h, sy = sr % W1, sz = sr / W1;
+    for (int i = threadIdx.x; i < tot; i += nt) {
+      const A* sp = st + lz * PS + ly * RP + 2 * lx;
+      const A v0 = sp[0], v1 = 2 * lx + 1 < W0 ? sp[1] : A(0);
+      if ((v0 | v1) != 0) {
+        float* gp = reinterpret_cast<float*>(grid) + zoff[lz] + yoff[ly] + pmod(ox + 2 * lx, g.I[0]);
+        atomicAdd(reinterpret_cast<float2*>(gp), make_float2((float)v0 * (float)iS, (float)v1 * (float)iS));
+      }
+      lx += sx;
+      ly += sy;
+      lz += sz;
+      if (lx >= W0h) { lx -= W0h; ++ly; }
+      if (ly >= W1) { ly -= W1; ++lz; }
+    }
+    return;
+  }
   const int xw = lane < W0 ? pmod(ox + lane, g.I[0]) : 0;
   int ly = warp, lz = 0;
   while (ly >= W1) { ly -= W1; ++lz; }
@@ -846,11 +895,31 @@ __device__ __forceinline__ void tile_load(const T* __restrict__ grid, T* __restr
   cp_async_wait_all();
 }
 
+// Sum of four values over the warp by halving exchanges (6 shuffles instead
+// of 20): on return lanes 0-7 hold the sum of a, 8-15 of b, 16-23 of c,
+// 24-31 of d.
+template <typename T>
+__device__ __forceinline__ T warp_sum4(T a, T b, T c, T d) {
+  const int lane = threadIdx.x & 31;
+  const bool hi16 = lane & 16, hi8 = lane & 8;
+  T k0 = hi16 ? c : a, k1 = hi16 ? d : b;
+  k0 += __shfl_xor_sync(0xffffffffu, hi16 ? a : c, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, hi16 ? b : d, 16);
+  T k = hi8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
 // Gathering, Eq. (3.10): Phi^mid_i = sum_g u[g] W(r_i - r_g) and its gradient.
-// The padded tile is loaded into shared memory once.  Window values and
-// derivatives are staged per batch of kGatherBatch particles; then two
-// threads per particle each sum half of the window's z-planes (x, then y,
-// then z contractions in registers) and combine with one shuffle.
+// The padded tile is loaded into shared memory once (odd row pitch, plane
+// stride = P x pitch mod 32).  A warp per particle: its lanes first evaluate
+// the 3P window values and derivatives, then each lane sums whole x rows
+// (dz, dy) of the window; lane e reads word e x pitch + dx (mod 32), so the
+// 32 rows of a step fall in 32 different banks.  The four sums are combined
+// over the warp at the end.
 template <typename T, int PW>
 __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T> w,
                                                              const P4<T>* __restrict__ rec,
@@ -865,14 +934,18 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
   if (!chunk_range(b, e, g.chunks)) return;
   const int W0 = g.W[0], W1 = g.W[1], W2 = g.W[2];
   const int P = PW > 0 ? PW : w.P;
-  const int PS = W0 * W1;
+  const int PP = P * P;
+  const int RP = gather_row_pitch(W0);
+  const int PS = gather_plane_stride(RP, W1, P);
   constexpr int PR = PW > 0 ? PW : kMaxWin;
+  constexpr int NIT = PW > 0 ? (PW * PW + 31) / 32 : (kMaxWin * kMaxWin) / 32;
   long long* zoff = reinterpret_cast<long long*>(smraw);
   int* yoff = reinterpret_cast<int*>(zoff + 64);
   int* xoff = yoff + 32;
-  int* bofs = xoff + 32;
-  T* wgt = reinterpret_cast<T*>(smraw + kGatherHeader);  // [j][6][P]: w, w' for x, y, z
-  T* st = wgt + kGatherBatch * 6 * P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // per warp: (w, w') of the 3 axes, [axis][k]
+  Cx<T>* wsm = reinterpret_cast<Cx<T>*>(smraw + kGatherHeader) + warp * 3 * kMaxWin;
+  T* st = reinterpret_cast<T*>(smraw + kGatherHeader + (size_t)kTileThreads / 32 * 3 * kMaxWin * sizeof(Cx<T>));
   const int tz = tile / (g.nt[0] * g.nt[1]);
   const int ty = (tile / g.nt[0]) % g.nt[1];
   const int tx = tile % g.nt[0];
@@ -880,81 +953,80 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
   tile_tables(g, oy, oz, W2, false, yoff, zoff);
   for (int i = threadIdx.x; i < W0; i += blockDim.x) xoff[i] = pmod(ox + i, g.I[0]);
   __syncthreads();
-  tile_load(grid, st, W0, W1, W2, W0, PS, xoff, yoff, zoff);
-  const int j = threadIdx.x >> 1, sl = threadIdx.x & 1;
-  const int z0 = sl ? (P + 1) / 2 : 0, z1 = sl ? P : (P + 1) / 2;
-  for (int p0 = b; p0 < e; p0 += kGatherBatch) {
-    const int nb = min(kGatherBatch, e - p0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * 3 * P; idx += blockDim.x) {
-      const int jj = idx / (3 * P);
-      const int r = idx - jj * 3 * P;
-      const int ax = r / P, k = r - ax * P;
-      const P4<T> a = rec[p0 + jj];
-      const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
-      const int g0 = (int)dceil(c - w.half);
-      T v, dv;
+  tile_load(grid, st, W0, W1, W2, RP, PS, xoff, yoff, zoff);
+  __syncthreads();
+  // this lane's rows (dz, dy) of the window; roff -1: none
+  int roff[NIT], rdy[NIT], rdz[NIT];
+#pragma unroll
+  for (int it = 0; it < NIT; ++it) {
+    const int s2 = lane + 32 * it;
+    const int dz = s2 / P, dy = s2 - dz * P;
+    const bool ok = s2 < PP;
+    roff[it] = ok ? dz * PS + dy * RP : -1;
+    rdy[it] = ok ? dy : 0;
+    rdz[it] = ok ? dz : 0;
+  }
+  // this lane's window values: index l = lane (and lane + 32) of [axis][k]
+  const int ax0 = lane / P, k0 = lane - ax0 * P;
+  const int l1 = lane + 32, ax1 = l1 / P, k1 = l1 - ax1 * P;
+  for (int j = b + warp; j < e; j += nw) {
+    const P4<T> a = rec[j];
+    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half),
+              gz0 = (int)dceil(a.z - w.half);
+    {
       // d/dt of phi((g - t)/half) = -phi'/half
-      win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
-      T* wj = wgt + jj * 6 * P + 2 * ax * P;
-      wj[k] = v;
-      wj[P + k] = -dv * w.inv_half;
-      if (r == 0) {
-        const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
-        bofs[jj] = (gz0 + g.pad_lo) * PS + (gy0 + g.pad_lo) * W0 + g0 + g.pad_lo;
+      T v, dv;
+      if (ax0 < 3) {
+        const T c = ax0 == 0 ? a.x : (ax0 == 1 ? a.y : a.z);
+        const int g0 = ax0 == 0 ? gx0 : (ax0 == 1 ? gy0 : gz0);
+        win_eval(w, ((T)(g0 + k0) - c) * w.inv_half, v, dv);
+        wsm[ax0 * kMaxWin + k0] = Cx<T>{v, -dv * w.inv_half};
+      }
+      if (3 * P > 32 && ax1 < 3) {
+        const T c = ax1 == 0 ? a.x : (ax1 == 1 ? a.y : a.z);
+        const int g0 = ax1 == 0 ? gx0 : (ax1 == 1 ? gy0 : gz0);
+        win_eval(w, ((T)(g0 + k1) - c) * w.inv_half, v, dv);
+        wsm[ax1 * kMaxWin + k1] = Cx<T>{v, -dv * w.inv_half};
       }
     }
-    __syncthreads();
+    __syncwarp();
+    T wx[PR], dwx[PR];
+#pragma unroll
+    for (int k = 0; k < PR; ++k) {
+      const Cx<T> t = k < P ? wsm[k] : Cx<T>{T(0), T(0)};
+      wx[k] = t.x;
+      dwx[k] = t.y;
+    }
+    const T* bj = st + (gz0 + g.pad_lo) * PS + (gy0 + g.pad_lo) * RP + gx0 + g.pad_lo;
     T f = 0, fx = 0, fy = 0, fz = 0;
-    if (j < nb) {
-      const T* wj = wgt + j * 6 * P;
-      T wx[PR], dwx[PR], wy[PR], dwy[PR];
 #pragma unroll
-      for (int k = 0; k < PR; ++k) {
-        wx[k] = k < P ? wj[k] : T(0);
-        dwx[k] = k < P ? wj[P + k] : T(0);
-        wy[k] = k < P ? wj[2 * P + k] : T(0);
-        dwy[k] = k < P ? wj[3 * P + k] : T(0);
-      }
-      const T* bj = st + bofs[j];
-      for (int dz = z0; dz < z1; ++dz) {
-        const T* pl = bj + dz * PS;
-        T Sx = 0, Sd = 0, Sy = 0;
+    for (int it = 0; it < NIT; ++it) {
+      if (roff[it] >= 0) {
+        const T* rp = bj + roff[it];
+        T sx = 0, sd = 0;
 #pragma unroll
-        for (int dy = 0; dy < PR; ++dy) {
-          if (dy < P) {
-            const T* rp = pl + dy * W0;
-            T sx = 0, sd = 0;
-#pragma unroll
-            for (int dx = 0; dx < PR; ++dx) {
-              if (dx < P) {
-                const T u = rp[dx];
-                sx += u * wx[dx];
-                sd += u * dwx[dx];
-              }
-            }
-            Sx += wy[dy] * sx;
-            Sd += wy[dy] * sd;
-            Sy += dwy[dy] * sx;
+        for (int dx = 0; dx < PR; ++dx) {
+          if (dx < P) {
+            const T u = rp[dx];
+            sx += u * wx[dx];
+            sd += u * dwx[dx];
           }
         }
-        const T wzv = wj[4 * P + dz], dwzv = wj[5 * P + dz];
-        f += wzv * Sx;
-        fx += wzv * Sd;
-        fy += wzv * Sy;
-        fz += dwzv * Sx;
+        const Cx<T> wy = wsm[kMaxWin + rdy[it]], wz = wsm[2 * kMaxWin + rdz[it]];
+        const T wyz = wy.x * wz.x;
+        f += wyz * sx;
+        fx += wyz * sd;
+        fy += wy.y * wz.x * sx;
+        fz += wy.x * wz.y * sx;
       }
     }
-    f += __shfl_xor_sync(0xffffffffu, f, 1);
-    fx += __shfl_xor_sync(0xffffffffu, fx, 1);
-    fy += __shfl_xor_sync(0xffffffffu, fy, 1);
-    fz += __shfl_xor_sync(0xffffffffu, fz, 1);
-    if (j < nb && sl == 0) {
-      const int o = perm[p0 + j];
-      phi_out[o] = (double)f;
-      grad_out[3 * o] = (double)fx * invh.x;
-      grad_out[3 * o + 1] = (double)fy * invh.y;
-      grad_out[3 * o + 2] = (double)fz * invh.z;
+    __syncwarp();
+    const T tot = warp_sum4(f, fx, fy, fz);
+    if ((lane & 7) == 0) {
+      const int o = perm[j];
+      const int which = lane >> 3;
+      if (which == 0) phi_out[o] = (double)tot;
+      else grad_out[3 * o + which - 1] = (double)tot * (which == 1 ? invh.x : (which == 2 ? invh.y : invh.z));
     }
   }
 }
@@ -1305,14 +1377,6 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
 
 constexpr int kModeThreads = 256, kModeBatch = 128;
 
-template <typename T>
-struct Cx {
-  T x, y;
-};
-template <typename T>
-__device__ __forceinline__ Cx<T> cxmul(Cx<T> a, Cx<T> b) {
-  return Cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
-}
 __device__ __forceinline__ void dsincospi(float a, float* s, float* c) { sincospif(a, s, c); }
 __device__ __forceinline__ void dsincospi(double a, double* s, double* c) { sincospi(a, s, c); }
 
@@ -1723,11 +1787,11 @@ static cudaError_t allow_pw() {
 static size_t mid_smem(const sog_plan* p, size_t es, bool gather) {
   const TileGeom& g = p->gm;
   const int P = p->wm.P;
-  if (gather)
-    return kGatherHeader + ((size_t)kGatherBatch * 6 * P + (size_t)g.W[0] * g.W[1] * g.W[2]) * es;
-  // fixed-point tile: int32 for FP32, int64 for FP64 (same size as T)
   const int rp = gather_row_pitch(g.W[0]);
   const size_t tile = (size_t)g.W[2] * gather_plane_stride(rp, g.W[1], P);
+  if (gather)  // per-warp window values (w, w') and the tile
+    return kGatherHeader + ((size_t)kTileThreads / 32 * 3 * kMaxWin * 2 + tile) * es;
+  // fixed-point tile: int32 for FP32, int64 for FP64 (same size as T)
   return kTileHeader + ((size_t)kTileBatch * 3 * kMaxWin + tile) * es;
 }
 static size_t long_smem(const sog_plan* p, size_t es, bool gather) {
