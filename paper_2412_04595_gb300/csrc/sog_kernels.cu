@@ -40,7 +40,47 @@ struct PrepGeom {
   int Tl[2], ntl[2];
   double iTl[2];
   double ihalfLz;
+  // FP32 plans: the same quantities for arithmetic in float pairs (value
+  // rounded to float, plus the rounding error), and float thresholds that
+  // decide the comparisons with the FP64 half box lengths exactly
+  float wrap_hi[2], wrap_lo[2];  // c >= L/2  <=>  c >= wrap_hi;  c < -L/2  <=>  c < wrap_lo
+  float z_lo, z_hi;              // -Lz/2 <= z <= Lz/2  <=>  z_lo <= z <= z_hi
+  float halfLf[3];               // L/2 rounded (clamp values)
+  float2 halfLp[3], icellp[3], ihp[3], Lzs_halfp, iTmp[3], ihlp[2], iTlp[2], ihalfLzp;
 };
+
+// Float pairs: value h plus error l (|l| <= ulp(h) / 2).
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF ff_fast2(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return FF{s, b - (s - a)};
+}
+// c + H exactly up to the rounding of H's pair
+__device__ __forceinline__ FF ff_add(float c, float2 H) {
+  const float s = c + H.x;
+  const float bb = s - c;
+  const float e = (c - (s - bb)) + (H.x - bb);
+  return ff_fast2(s, e + H.y);
+}
+__device__ __forceinline__ FF ff_mul(FF a, float2 b) {
+  const float p = a.h * b.x;
+  float e = fmaf(a.h, b.x, -p);
+  e = fmaf(a.h, b.y, e);
+  e = fmaf(a.l, b.x, e);
+  return ff_fast2(p, e);
+}
+// floor(a.h + a.l) clamped to [0, n - 1] (0 for NaN)
+__device__ __forceinline__ int ff_floor_clamp(FF a, int n) {
+  if (!(a.h >= 0.0f)) return 0;
+  float k = floorf(a.h);
+  if (k == a.h && a.l < 0.0f) k -= 1.0f;
+  if (k >= (float)n) return n - 1;
+  return k < 0.0f ? 0 : (int)k;
+}
+// (a.h + a.l) - k m rounded once (k m exact: both small integers)
+__device__ __forceinline__ float ff_sub_int(FF a, int k, int m) { return (a.h - (float)(k * m)) + a.l; }
 
 template <typename T>
 struct WinT {
@@ -124,11 +164,80 @@ __device__ __forceinline__ int floor_clamp(double t, int n) {
   return (int)t;
 }
 
+// FP32 plans: prep_particle in float and float-pair arithmetic (the FP64
+// pipe of this GPU is slow): the wrap and range decisions are exact, bins
+// follow the rounded pair sums, and the tile-local coordinates carry one
+// rounding, as when they are computed in FP64 and rounded.
+__device__ void prep_particle_f(const PrepGeom& g, const float* __restrict__ q,
+                                const float* __restrict__ r, int i, int& bits, P4<float>& rn,
+                                int& kn, int& km, P4<float>& rm, int& kl, P4<float>& rl) {
+  float c[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
+  float qi = q[i];
+  for (int d = 0; d < 2; ++d) {
+    const float Ld = (float)g.L[d];
+    if (c[d] >= g.wrap_hi[d]) c[d] = c[d] - Ld;
+    else if (c[d] < g.wrap_lo[d]) c[d] = c[d] + Ld;
+    if (!(c[d] >= g.wrap_lo[d] && c[d] < g.wrap_hi[d])) {
+      bits |= 2;
+      c[d] = isfinite(c[d]) ? (c[d] < 0.0f ? -g.halfLf[d] : 0.0f) : 0.0f;
+    }
+  }
+  if (!(c[2] >= g.z_lo && c[2] <= g.z_hi)) {
+    bits |= 2;
+    c[2] = isfinite(c[2]) ? (c[2] < 0.0f ? -g.halfLf[2] : g.halfLf[2]) : 0.0f;
+  }
+  if (!isfinite(qi)) {
+    bits |= 2;
+    qi = 0.0f;
+  }
+  rn = P4<float>{c[0], c[1], c[2], qi};
+  FF s[3];
+  int cc[3];
+  for (int d = 0; d < 3; ++d) {
+    s[d] = ff_add(c[d], g.halfLp[d]);
+    cc[d] = ff_floor_clamp(ff_mul(s[d], g.icellp[d]), g.nc[d]);
+  }
+  kn = (cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
+  km = 0;
+  kl = 0;
+  if (g.has_mid) {
+    FF t[3];
+    t[0] = ff_mul(s[0], g.ihp[0]);
+    t[1] = ff_mul(s[1], g.ihp[1]);
+    t[2] = ff_mul(ff_add(c[2], g.Lzs_halfp), g.ihp[2]);
+    int tt[3];
+    float loc[3];
+    for (int d = 0; d < 3; ++d) {
+      tt[d] = ff_floor_clamp(ff_mul(t[d], g.iTmp[d]), g.ntm[d]);
+      loc[d] = ff_sub_int(t[d], tt[d], g.Tm[d]);
+    }
+    km = (tt[2] * g.ntm[1] + tt[1]) * g.ntm[0] + tt[0];
+    rm = P4<float>{loc[0], loc[1], loc[2], qi};
+  }
+  if (g.has_long) {
+    FF t[2];
+    int tt[2];
+    float loc[2];
+    for (int d = 0; d < 2; ++d) {
+      t[d] = ff_mul(s[d], g.ihlp[d]);
+      tt[d] = ff_floor_clamp(ff_mul(t[d], g.iTlp[d]), g.ntl[d]);
+      loc[d] = ff_sub_int(t[d], tt[d], g.Tl[d]);
+    }
+    kl = tt[1] * g.ntl[0] + tt[0];
+    const FF zz = ff_mul(FF{c[2], 0.0f}, g.ihalfLzp);
+    rl = P4<float>{loc[0], loc[1], zz.h + zz.l, qi};
+  }
+}
+
 // Wrap / clamp one particle and compute its bins and tile-local records.
 template <typename T>
 __device__ void prep_particle(const PrepGeom& g, const T* __restrict__ q, const T* __restrict__ r,
                               int i, int& bits, P4<T>& rn, int& kn, int& km, P4<T>& rm, int& kl,
                               P4<T>& rl) {
+  if constexpr (sizeof(T) == 4) {
+    prep_particle_f(g, q, r, i, bits, rn, kn, km, rm, kl, rl);
+    return;
+  }
   T x = r[3 * i], y = r[3 * i + 1], z = r[3 * i + 2], qi = q[i];
   T c[3] = {x, y, z};
   for (int d = 0; d < 2; ++d) {
@@ -191,6 +300,54 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Sum of four values over the warp by halving exchanges (6 shuffles instead
+// of 20): on return lanes 0-7 hold the sum of a, 8-15 of b, 16-23 of c,
+// 24-31 of d.
+template <typename T>
+__device__ __forceinline__ T warp_sum4(T a, T b, T c, T d) {
+  const int lane = threadIdx.x & 31;
+  const bool hi16 = lane & 16, hi8 = lane & 8;
+  T k0 = hi16 ? c : a, k1 = hi16 ? d : b;
+  k0 += __shfl_xor_sync(0xffffffffu, hi16 ? a : c, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, hi16 ? b : d, 16);
+  T k = hi8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
+// Per-particle results (potential and three gradient components) of up to
+// 8 particles of a warp, held one per lane: lane 8 v + s keeps value v of
+// the particle in slot s.  Writing them out in FP64 then costs one
+// conversion for 8 particles (a warp-wide FP64 instruction occupies the FP64
+// pipe for many cycles however few lanes are active).
+template <typename T>
+struct OutSlots {
+  T val;
+  int o, n;
+  // tot: value (lane >> 3) of the current particle, as left by warp_sum4
+  __device__ __forceinline__ void put(T tot, int out_index) {
+    if (((threadIdx.x & 31) & 7) == n) {
+      val = tot;
+      o = out_index;
+    }
+    ++n;
+  }
+  // add: accumulate into the outputs instead of overwriting them
+  __device__ __forceinline__ void flush(double* __restrict__ phi, double* __restrict__ grad,
+                                        bool add) {
+    const int lane = threadIdx.x & 31, which = lane >> 3;
+    if ((lane & 7) < n) {
+      double* dst = which == 0 ? phi + o : grad + 3 * (size_t)o + which - 1;
+      if (add) *dst += (double)val;
+      else *dst = (double)val;
+    }
+    n = 0;
+  }
+};
+
 // Block-wide sum of a double; result valid in thread 0.
 __device__ double block_sum(double v, double* sh) {
   v = warp_sum(v);
@@ -222,7 +379,7 @@ __global__ void k_bin_count(PrepGeom g, const T* __restrict__ q, const T* __rest
                             int* __restrict__ key, int* __restrict__ rank, int* __restrict__ cnt,
                             int3 off, P4<T>* __restrict__ tmp, double* __restrict__ red,
                             int* __restrict__ status) {
-  __shared__ double sh[32];
+  __shared__ double2 sh2[256];
   double sq = 0.0, sa = 0.0;
   int bits = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -246,11 +403,22 @@ __global__ void k_bin_count(PrepGeom g, const T* __restrict__ q, const T* __rest
     sa += fabs((double)rn.q);
   }
   if (bits) atomicOr(status, bits);
-  const double tq = block_sum(sq, sh);
-  const double ta = block_sum(sa, sh);
-  if (threadIdx.x == 0) {
-    red[2 * blockIdx.x] = tq;
-    red[2 * blockIdx.x + 1] = ta;
+  // block sums of q and |q| in a fixed order: warp 0 adds the threads'
+  // values from shared memory (few warp-wide FP64 instructions)
+  sh2[threadIdx.x] = make_double2(sq, sa);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double tq = 0.0, ta = 0.0;
+    for (int k = threadIdx.x; k < (int)blockDim.x; k += 32) {
+      tq += sh2[k].x;
+      ta += sh2[k].y;
+    }
+    tq = warp_sum(tq);
+    ta = warp_sum(ta);
+    if (threadIdx.x == 0) {
+      red[2 * blockIdx.x] = tq;
+      red[2 * blockIdx.x + 1] = ta;
+    }
   }
 }
 
@@ -594,6 +762,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
       shs[k] = S2<T>{T(0), T(0)};
     }
     __syncthreads();
+    OutSlots<T> out{T(0), 0, 0};
     for (int t0 = 0; t0 < ntg; t0 += nw) {
       const int tt = t0 + warp;
       if (tt >= ntg) break;
@@ -622,25 +791,10 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
       } else {
         near_target<T, false>(a, src, shs, nsteps, rc2, tb_, g.K, hK, ihK, mylist, v0, v1, v2, v3);
       }
-      v0 = warp_sum(v0);
-      v1 = warp_sum(v1);
-      v2 = warp_sum(v2);
-      v3 = warp_sum(v3);
-      if (lane == 0) {
-        const int o = perm[ti];
-        if (s0 == 0) {
-          phi_out[o] = (double)v0;
-          grad_out[3 * o] = (double)v1;
-          grad_out[3 * o + 1] = (double)v2;
-          grad_out[3 * o + 2] = (double)v3;
-        } else {
-          phi_out[o] += (double)v0;
-          grad_out[3 * o] += (double)v1;
-          grad_out[3 * o + 1] += (double)v2;
-          grad_out[3 * o + 2] += (double)v3;
-        }
-      }
+      out.put(warp_sum4(v0, v1, v2, v3), perm[ti]);
+      if (out.n == 8) out.flush(phi_out, grad_out, s0 > 0);
     }
+    out.flush(phi_out, grad_out, s0 > 0);
   }
 }
 
@@ -895,24 +1049,6 @@ __device__ __forceinline__ void tile_load(const T* __restrict__ grid, T* __restr
   cp_async_wait_all();
 }
 
-// Sum of four values over the warp by halving exchanges (6 shuffles instead
-// of 20): on return lanes 0-7 hold the sum of a, 8-15 of b, 16-23 of c,
-// 24-31 of d.
-template <typename T>
-__device__ __forceinline__ T warp_sum4(T a, T b, T c, T d) {
-  const int lane = threadIdx.x & 31;
-  const bool hi16 = lane & 16, hi8 = lane & 8;
-  T k0 = hi16 ? c : a, k1 = hi16 ? d : b;
-  k0 += __shfl_xor_sync(0xffffffffu, hi16 ? a : c, 16);
-  k1 += __shfl_xor_sync(0xffffffffu, hi16 ? b : d, 16);
-  T k = hi8 ? k1 : k0;
-  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
-  k += __shfl_xor_sync(0xffffffffu, k, 4);
-  k += __shfl_xor_sync(0xffffffffu, k, 2);
-  k += __shfl_xor_sync(0xffffffffu, k, 1);
-  return k;
-}
-
 // Gathering, Eq. (3.10): Phi^mid_i = sum_g u[g] W(r_i - r_g) and its gradient.
 // The padded tile is loaded into shared memory once (odd row pitch, plane
 // stride = P x pitch mod 32).  A warp per particle: its lanes first evaluate
@@ -969,6 +1105,8 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
   // this lane's window values: index l = lane (and lane + 32) of [axis][k]
   const int ax0 = lane / P, k0 = lane - ax0 * P;
   const int l1 = lane + 32, ax1 = l1 / P, k1 = l1 - ax1 * P;
+  const T ih_lane = (T)((lane >> 3) == 1 ? invh.x : ((lane >> 3) == 2 ? invh.y : invh.z));
+  OutSlots<T> out{T(0), 0, 0};
   for (int j = b + warp; j < e; j += nw) {
     const P4<T> a = rec[j];
     const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half),
@@ -1022,13 +1160,10 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
     }
     __syncwarp();
     const T tot = warp_sum4(f, fx, fy, fz);
-    if ((lane & 7) == 0) {
-      const int o = perm[j];
-      const int which = lane >> 3;
-      if (which == 0) phi_out[o] = (double)tot;
-      else grad_out[3 * o + which - 1] = (double)tot * (which == 1 ? invh.x : (which == 2 ? invh.y : invh.z));
-    }
+    out.put(lane < 8 ? tot : tot * ih_lane, perm[j]);
+    if (out.n == 8) out.flush(phi_out, grad_out, false);
   }
+  out.flush(phi_out, grad_out, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -1380,12 +1515,32 @@ constexpr int kModeThreads = 256, kModeBatch = 128;
 __device__ __forceinline__ void dsincospi(float a, float* s, float* c) { sincospif(a, s, c); }
 __device__ __forceinline__ void dsincospi(double a, double* s, double* c) { sincospi(a, s, c); }
 
-// e^{sgn i 2 pi n t / L} for n = n0 .. n0 + cnt - 1: the first by sincospi,
-// the rest by products with the step.
+// Geometry of the direct long range in the element type (no FP64 in the
+// per-particle work): 2/Lx, 2/Ly, Lz/2, 2/Lz, 2 pi/Lx, 2 pi/Ly.
 template <typename T>
-__device__ __forceinline__ void cis_run(T t, double L, int n0, int cnt, T sgn, Cx<T>* out,
+struct ModeGeom {
+  T tx, ty, hz, ihz, kx1, ky1;
+};
+template <typename T>
+__host__ ModeGeom<T> mode_geom(double Lx, double Ly, double Lz) {
+  const double pi = 3.14159265358979323846;
+  return ModeGeom<T>{(T)(2.0 / Lx), (T)(2.0 / Ly), (T)(0.5 * Lz), (T)(2.0 / Lz), (T)(2.0 * pi / Lx),
+                     (T)(2.0 * pi / Ly)};
+}
+// z / (Lz/2), clamped to [-1, 1] (0 for non-finite z)
+template <typename T>
+__device__ __forceinline__ T cheb_x(T z, const ModeGeom<T>& mg) {
+  T x = z * mg.ihz;
+  if (!(x >= T(-1) && x <= T(1))) x = isfinite(z) ? (x < T(0) ? T(-1) : T(1)) : T(0);
+  return x;
+}
+
+// e^{sgn i 2 pi n t / L} for n = n0 .. n0 + cnt - 1 (tl = 2/L): the first by
+// sincospi, the rest by products with the step.
+template <typename T>
+__device__ __forceinline__ void cis_run(T t, T tl, int n0, int cnt, T sgn, Cx<T>* out,
                                         int stride) {
-  const T a = (T)(2.0 / L) * t;
+  const T a = tl * t;
   T s, c;
   dsincospi(a, &s, &c);
   const Cx<T> step{c, sgn * s};
@@ -1407,7 +1562,7 @@ constexpr int kModeRed = 16;
 template <typename T, int PMAX>
 __global__ void __launch_bounds__(kModeThreads) k_lmodes_moments(
     const T* __restrict__ q, const T* __restrict__ r, int N, int P, int Kx, int Ky, int nhalf,
-    int nbt, double Lx, double Ly, double halfLz, double* __restrict__ part) {
+    int nbt, ModeGeom<T> mg, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ny_all = 2 * Ky + 1;
   T* tq = reinterpret_cast<T*>(smraw);                   // [j][PMAX]
@@ -1423,17 +1578,14 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_moments(
   for (int n = 0; n < PMAX; ++n) acc[n][0] = acc[n][1] = T(0);
   const int per = (N + gridDim.x - 1) / gridDim.x;
   const int b = blockIdx.x * per, e = min(N, b + per);
-  const double ih = 1.0 / halfLz;
   for (int p0 = b; p0 < e; p0 += nbt) {
     const int nb = min(nbt, e - p0);
     __syncthreads();
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
       const int i = p0 + j;
-      double z = (double)r[3 * i + 2];
-      if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
-      const T x = (T)(z * ih);
+      const T x = cheb_x(r[3 * i + 2], mg);
       T qi = q[i];
-      if (!isfinite((double)qi)) qi = T(0);
+      if (!isfinite(qi)) qi = T(0);
       T t0 = T(1), t1 = x;
 #pragma unroll
       for (int n = 0; n < PMAX; ++n) {
@@ -1442,8 +1594,8 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_moments(
         t0 = t1;
         t1 = t2;
       }
-      cis_run(r[3 * i], Lx, 0, Kx + 1, T(-1), ex + j * (Kx + 1), 1);
-      cis_run(r[3 * i + 1], Ly, -Ky, ny_all, T(-1), ey + j * ny_all, 1);
+      cis_run(r[3 * i], mg.tx, 0, Kx + 1, T(-1), ex + j * (Kx + 1), 1);
+      cis_run(r[3 * i + 1], mg.ty, -Ky, ny_all, T(-1), ey + j * ny_all, 1);
     }
     __syncthreads();
     if (active) {
@@ -1524,9 +1676,8 @@ __global__ void __launch_bounds__(256) k_lmodes_coeffs(const double* __restrict_
 // Potential and gradient of the long range at every particle (input order).
 template <typename T, int PMAX>
 __global__ void __launch_bounds__(kModeThreads) k_lmodes_eval(
-    const T* __restrict__ r, int N, int P, int Kx, int Ky, int nhalf, double Lx, double Ly,
-    double halfLz, const T* __restrict__ coef, double* __restrict__ phi_out,
-    double* __restrict__ grad_out) {
+    const T* __restrict__ r, int N, int P, int Kx, int Ky, int nhalf, ModeGeom<T> mg,
+    const T* __restrict__ coef, double* __restrict__ phi_out, double* __restrict__ grad_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Cx<T>* c = reinterpret_cast<Cx<T>*>(smraw);  // [mode][P]
   for (int i = threadIdx.x; i < nhalf * P; i += blockDim.x)
@@ -1534,9 +1685,7 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_eval(
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double z = (double)r[3 * i + 2];
-  if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
-  const T x = (T)(z / halfLz);
+  const T x = cheb_x(r[3 * i + 2], mg);
   T tn[PMAX], dn[PMAX];
   {
     T t0 = T(1), t1 = x, d0 = T(0), d1 = T(1);
@@ -1552,11 +1701,11 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_eval(
       d1 = d2;
     }
   }
-  const T kx1 = (T)(2.0 * 3.14159265358979323846 / Lx), ky1 = (T)(2.0 * 3.14159265358979323846 / Ly);
+  const T kx1 = mg.kx1, ky1 = mg.ky1;
   const T xv = r[3 * i], yv = r[3 * i + 1];
   T sa, ca, sb, cb;
-  dsincospi((T)(2.0 / Lx) * xv, &sa, &ca);
-  dsincospi((T)(2.0 / Ly) * yv, &sb, &cb);
+  dsincospi(mg.tx * xv, &sa, &ca);
+  dsincospi(mg.ty * yv, &sb, &cb);
   const Cx<T> stepx{ca, sa}, stepy{cb, sb};
   T f = 0, gx = 0, gy = 0, gz = 0;
   Cx<T> exv{T(1), T(0)};
@@ -1565,7 +1714,7 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_eval(
     // e^{i ky y} from n_y = 1 (mx = 0) or -Ky (mx > 0)
     const int ny0 = mx == 0 ? 1 : -Ky;
     T s0, c0;
-    dsincospi((T)(2.0 / Ly) * yv * (T)ny0, &s0, &c0);
+    dsincospi(mg.ty * yv * (T)ny0, &s0, &c0);
     Cx<T> eyv{c0, s0};
     for (int my = ny0; my <= Ky; ++my, ++md) {
       const Cx<T> ph = cxmul(exv, eyv);
@@ -1593,7 +1742,7 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_eval(
   phi_out[i] = (double)f;
   grad_out[3 * i] = (double)gx;
   grad_out[3 * i + 1] = (double)gy;
-  grad_out[3 * i + 2] = (double)gz / halfLz;
+  grad_out[3 * i + 2] = (double)(gz * mg.ihz);
 }
 
 // ---------------------------------------------------------------------------
@@ -1623,7 +1772,7 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_moments(const T* __restrict__
     if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
     const T x = (T)(z * ih);
     T qi = q[i];
-    if (!isfinite((double)qi)) qi = T(0);
+    if (!isfinite(qi)) qi = T(0);
     T t0 = T(1), t1 = x;
 #pragma unroll
     for (int n = 0; n < PMAX; ++n) {
@@ -1830,6 +1979,22 @@ static void mark_end(sog_plan* p, int stage, cudaStream_t s) { mark_ev(p, 2 * st
     SOG_CK(cudaGetLastError());        \
   } while (0)
 
+// Smallest float >= v, largest float <= v, and v as float plus remainder.
+static float float_ceil(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+static float float_floor(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+static float2 float_pair(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 template <typename T>
 static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E, T* F,
                          double* pp, double* pg, cudaStream_t s) {
@@ -1859,6 +2024,26 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     g.iTl[d] = p->has_long ? 1.0 / p->gl.T[d] : 0.0;
   }
   g.ihalfLz = 2.0 / m.L[2];
+  // float forms for FP32 plans
+  for (int d = 0; d < 2; ++d) {
+    g.wrap_hi[d] = float_ceil(g.halfL[d]);
+    g.wrap_lo[d] = float_ceil(-g.halfL[d]);
+  }
+  g.z_lo = float_ceil(-g.halfL[2]);
+  g.z_hi = float_floor(g.halfL[2]);
+  for (int d = 0; d < 3; ++d) {
+    g.halfLf[d] = (float)g.halfL[d];
+    g.halfLp[d] = float_pair(g.halfL[d]);
+    g.icellp[d] = float_pair(g.icell[d]);
+    g.ihp[d] = float_pair(g.ih[d]);
+    g.iTmp[d] = float_pair(g.iTm[d]);
+  }
+  g.Lzs_halfp = float_pair(g.Lzs_half);
+  for (int d = 0; d < 2; ++d) {
+    g.ihlp[d] = float_pair(g.ihl[d]);
+    g.iTlp[d] = float_pair(g.iTl[d]);
+  }
+  g.ihalfLzp = float_pair(g.ihalfLz);
   const int3 off = make_int3(p->cnt_off[0], p->cnt_off[1], p->cnt_off[2]);
   const int3 nb = make_int3(p->n_cells, p->has_mid ? p->n_tiles_mid : 0,
                             long_bins ? p->n_tiles_long : 0);
@@ -1947,14 +2132,14 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     const size_t sm1 = std::max((size_t)nbt * per_part,
                                 (size_t)kModeThreads * kModeRed * 2 * sizeof(T));
     const size_t sm3 = (size_t)nh * P * 2 * sizeof(T);
-    const double hz = 0.5 * m.L[2];
+    const ModeGeom<T> mg = mode_geom<T>(m.L[0], m.L[1], m.L[2]);
     mark_begin(p, 5, sl);
     if (pmax == 16)
-      k_lmodes_moments<T, 16><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, m.L[0], m.L[1], hz, p->d_lmom);
+      k_lmodes_moments<T, 16><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, p->d_lmom);
     else if (pmax == 32)
-      k_lmodes_moments<T, 32><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, m.L[0], m.L[1], hz, p->d_lmom);
+      k_lmodes_moments<T, 32><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, p->d_lmom);
     else
-      k_lmodes_moments<T, 64><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, m.L[0], m.L[1], hz, p->d_lmom);
+      k_lmodes_moments<T, 64><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, p->d_lmom);
     LAUNCH_CHECK();
     mark_end(p, 5, sl);
     mark_begin(p, 6, sl);
@@ -1966,11 +2151,11 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     mark_begin(p, 7, sl);
     const T* cf = reinterpret_cast<const T*>(p->d_lcoef);
     if (pmax == 16)
-      k_lmodes_eval<T, 16><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, m.L[0], m.L[1], hz, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
+      k_lmodes_eval<T, 16><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, mg, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     else if (pmax == 32)
-      k_lmodes_eval<T, 32><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, m.L[0], m.L[1], hz, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
+      k_lmodes_eval<T, 32><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, mg, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     else
-      k_lmodes_eval<T, 64><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, m.L[0], m.L[1], hz, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
+      k_lmodes_eval<T, 64><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, mg, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     LAUNCH_CHECK();
     mark_end(p, 7, sl);
   }
