@@ -38,10 +38,12 @@ template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; using tw = TwF; };
 template <> struct C2<double> { using t = double2; using tw = TwD; };
 
-constexpr int kFftThreads = 1024;
-template <typename T> struct FftCap;
-template <> struct FftCap<float> { static constexpr int v = 10; };
-template <> struct FftCap<double> { static constexpr int v = 8; };
+// Threads per CTA, complex values a thread holds in a stage, and CTAs per
+// SM the register budget is sized for: FP32 runs two CTAs of 512 threads per
+// SM (one CTA's barriers overlap the other's work), FP64 one of 1024.
+template <typename T> struct FftCfg;
+template <> struct FftCfg<float> { static constexpr int threads = 512, cap = 16, minb = 2; };
+template <> struct FftCfg<double> { static constexpr int threads = 1024, cap = 8, minb = 1; };
 
 template <typename T2>
 __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return T2{a.x + b.x, a.y + b.y}; }
@@ -252,7 +254,7 @@ __device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T4* t
 }
 
 // Largest nl for which nl lines of length n fit the engine.
-static int max_lines(const FftLen& f, int cap, int nt = kFftThreads) {
+static int max_lines(const FftLen& f, int cap, int nt) {
   int best = 1 << 30;
   for (int st = 0; st < f.nst; ++st) {
     const int R = f.radix[st];
@@ -338,12 +340,12 @@ __device__ __forceinline__ void join_pairs(T2* buf, int Ix, int npairs) {
 // Ix + 2 at data + z * Iy * (Ix + 2); the half spectrum [ky][kx] (C complex
 // per row) is stored over the same memory.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 1)
+__global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
     k_fft_plane(T* __restrict__ data, FftLen fx, FftLen fy, const typename C2<T>::tw* __restrict__ twg,
                 bool inv) {
   using T2 = typename C2<T>::t;
   using T4 = typename C2<T>::tw;
-  constexpr int CAP = FftCap<T>::v;
+  constexpr int CAP = FftCfg<T>::cap;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Ix = fx.n, Iy = fy.n, C = Ix / 2 + 1, pitch = Ix + 2;
   const int np = Iy / 2;
@@ -387,11 +389,11 @@ __global__ void __launch_bounds__(kFftThreads, 1)
 
 // x pass alone: rows 2p, 2p+1 (pitch Ix + 2) of pairs p0 .. p0 + B - 1.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 1)
+__global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
     k_fft_rows(T* __restrict__ data, FftLen fx, const typename C2<T>::tw* __restrict__ twg,
                int npairs, int B, bool inv) {
   using T2 = typename C2<T>::t;
-  constexpr int CAP = FftCap<T>::v;
+  constexpr int CAP = FftCfg<T>::cap;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int Ix = fx.n, C = Ix / 2 + 1, pitch = Ix + 2;
   using T4 = typename C2<T>::tw;
@@ -439,11 +441,11 @@ __global__ void __launch_bounds__(kFftThreads, 1)
 // (z pass of Algorithm 1): forward FFT, multiply element (o, c, i) by
 // mult[(i*O + o)*Cn + c], backward FFT.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads, 1)
+__global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
     k_fft_cols(typename C2<T>::t* __restrict__ data, FftLen f, const typename C2<T>::tw* __restrict__ twg,
                int Cn, int O, long os, long es, int B, bool inv, const T* __restrict__ mult) {
   using T2 = typename C2<T>::t;
-  constexpr int CAP = FftCap<T>::v;
+  constexpr int CAP = FftCfg<T>::cap;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int n = f.n;
   using T4 = typename C2<T>::tw;
@@ -482,8 +484,8 @@ __global__ void __launch_bounds__(kFftThreads, 1)
 // True when a whole Ix x Iy plane fits one CTA of k_fft_plane with nt
 // threads.
 template <typename T>
-static bool plane_fits(const FftLen& fx, const FftLen& fy, int nt = kFftThreads) {
-  constexpr int CAP = FftCap<T>::v;
+static bool plane_fits(const FftLen& fx, const FftLen& fy, int nt = FftCfg<T>::threads) {
+  constexpr int CAP = FftCfg<T>::cap;
   const int C = fx.n / 2 + 1;
   const size_t smem = (size_t)(fx.n + fy.n) * sizeof(typename C2<T>::tw) +
                       (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(typename C2<T>::t);
@@ -495,9 +497,9 @@ static bool plane_fits(const FftLen& fx, const FftLen& fy, int nt = kFftThreads)
 // planes (the long range's proxy planes) do not need 1024 threads.
 template <typename T>
 static int plane_threads(const FftLen& fx, const FftLen& fy) {
-  for (int nt = 128; nt < kFftThreads; nt *= 2)
+  for (int nt = 128; nt < FftCfg<T>::threads; nt *= 2)
     if (plane_fits<T>(fx, fy, nt)) return nt;
-  return kFftThreads;
+  return FftCfg<T>::threads;
 }
 
 template <typename T>
@@ -518,15 +520,16 @@ template <typename T>
 static cudaError_t launch_rows(T* data, const FftLen& fx, const void* tw, int nrows, bool inv,
                                cudaStream_t s) {
   using T2 = typename C2<T>::t;
-  constexpr int CAP = FftCap<T>::v;
+  constexpr int CAP = FftCfg<T>::cap;
   const int npairs = nrows / 2;
   const int C = fx.n / 2 + 1;
-  int B = std::min(max_lines(fx, CAP), kFftThreads * (CAP / 2) / C);
+  constexpr int NT = FftCfg<T>::threads;
+  int B = std::min(max_lines(fx, CAP, NT), NT * (CAP / 2) / C);
   B = std::max(1, std::min(B, npairs));
   using T4 = typename C2<T>::tw;
   const size_t sm = (size_t)fx.n * sizeof(T4) + (size_t)B * std::max(fx.n, 2 * C) * sizeof(T2);
   const int grid = (npairs + B - 1) / B;
-  k_fft_rows<T><<<grid, kFftThreads, sm, s>>>(data, fx, reinterpret_cast<const T4*>(tw), npairs,
+  k_fft_rows<T><<<grid, NT, sm, s>>>(data, fx, reinterpret_cast<const T4*>(tw), npairs,
                                               B, inv);
   return cudaGetLastError();
 }
@@ -535,15 +538,16 @@ template <typename T>
 static cudaError_t launch_cols(T* data, const FftLen& f, const void* tw, int Cn, int O, long os,
                                long es, bool inv, const T* mult, cudaStream_t s) {
   using T2 = typename C2<T>::t;
-  constexpr int CAP = FftCap<T>::v;
-  int B = std::max(1, std::min(max_lines(f, CAP), Cn));
+  constexpr int CAP = FftCfg<T>::cap;
+  constexpr int NT = FftCfg<T>::threads;
+  int B = std::max(1, std::min(max_lines(f, CAP, NT), Cn));
   // balance the groups of one o
   const int groups = (Cn + B - 1) / B;
   B = (Cn + groups - 1) / groups;
   using T4 = typename C2<T>::tw;
   const size_t sm = (size_t)f.n * sizeof(T4) + (size_t)B * f.n * sizeof(T2);
   const int grid = O * groups;
-  k_fft_cols<T><<<grid, kFftThreads, sm, s>>>(reinterpret_cast<T2*>(data), f,
+  k_fft_cols<T><<<grid, NT, sm, s>>>(reinterpret_cast<T2*>(data), f,
                                               reinterpret_cast<const T4*>(tw), Cn, O, os, es, B,
                                               inv, mult);
   return cudaGetLastError();
@@ -599,10 +603,11 @@ template cudaError_t fft_long_pass<double>(const sog_plan*, bool, cudaStream_t, 
 // True when transforms of this length fit the engine (at least one line per
 // CTA; the x pass also needs its half spectrum to fit one CTA).
 bool fft_len_ok(int prec, const FftLen& f) {
-  const int cap = prec == SOG_PREC_FP64 ? FftCap<double>::v : FftCap<float>::v;
+  const int cap = prec == SOG_PREC_FP64 ? FftCfg<double>::cap : FftCfg<float>::cap;
+  const int nt = prec == SOG_PREC_FP64 ? FftCfg<double>::threads : FftCfg<float>::threads;
   const size_t elem = prec == SOG_PREC_FP64 ? sizeof(double2) : sizeof(float2);
   const size_t twe = prec == SOG_PREC_FP64 ? sizeof(TwD) : sizeof(TwF);
-  return f.n >= 2 && max_lines(f, cap) >= 1 && (f.n / 2 + 1) <= kFftThreads * (cap / 2) &&
+  return f.n >= 2 && max_lines(f, cap, nt) >= 1 && (f.n / 2 + 1) <= nt * (cap / 2) &&
          (size_t)f.n * twe + (size_t)(f.n + 2) * elem <= (size_t)kMaxDynSmem;
 }
 
