@@ -498,17 +498,43 @@ struct NearGeom {
   double L[2];
   double rc;
   int K, D;
+  // per-launch constants in both element types (no FP64 work per thread):
+  // r_c^2, table interval h_K and 1/h_K, Lx, Ly, 1/Lx, 1/Ly, Lx/2, Ly/2
+  float cf[9];
+  double cd[9];
 };
+enum { kNcRc2, kNcHK, kNcIhK, kNcLx, kNcLy, kNcILx, kNcILy, kNcHLx, kNcHLy };
+template <typename T>
+__device__ __forceinline__ T near_const(const NearGeom& g, int i) {
+  if constexpr (sizeof(T) == 4) return g.cf[i];
+  else return g.cd[i];
+}
+// The same constants computed as the kernels would in the element type.
+template <typename T>
+__host__ void near_consts(NearGeom& g, T* out) {
+  const T rc = (T)g.rc;
+  out[kNcRc2] = rc * rc;
+  out[kNcHK] = rc / (T)g.K;
+  out[kNcIhK] = (T)g.K / rc;
+  out[kNcLx] = (T)g.L[0];
+  out[kNcLy] = (T)g.L[1];
+  out[kNcILx] = (T)(1.0 / g.L[0]);
+  out[kNcILy] = (T)(1.0 / g.L[1]);
+  out[kNcHLx] = (T)g.halfL[0];
+  out[kNcHLy] = (T)g.halfL[1];
+}
 
-// Compensated (Neumaier) accumulation for the FP32 path: the near-field sum
+// Compensated accumulation for the FP32 path: the near-field sum
 // adds ~100 terms whose largest (1/r of a close pair) sets the rounding of
 // every later addition; the compensation keeps the sum at one rounding.
 template <typename T>
 struct Acc {
   T s, c;
   __device__ __forceinline__ void add(T v) {
+    // error of s + v by the branch-free two-sum (adds only)
     const T t = s + v;
-    c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+    const T bv = t - s;
+    c += (s - (t - bv)) + (v - bv);
     s = t;
   }
   __device__ __forceinline__ T get() const { return s + c; }
@@ -621,7 +647,9 @@ __device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restr
       if (h0 + lane < cnt) {
         T dx, dy, dz, q;
         diff(list[h0 + lane], dx, dy, dz, q);
-        near_pair(dx * dx + dy * dy + dz * dz, q, dx, dy, dz, tab, K, hK, ihK, phi, gx, gy, gz);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        // r2 == 0 only for the target itself (coincident charges are invalid input)
+        if (r2 > T(0)) near_pair(r2, q, dx, dy, dz, tab, K, hK, ihK, phi, gx, gy, gz);
       }
     }
     __syncwarp();
@@ -634,8 +662,7 @@ __device__ __forceinline__ void near_target(const P4<T>& a, const P4<T>* __restr
       const int k = st * 32 + lane;
       diff(k, dx, dy, dz, q);
       const T r2 = dx * dx + dy * dy + dz * dz;
-      // r2 == 0 only for the target itself (coincident charges are invalid input)
-      const bool in = r2 < rc2 && r2 > T(0);
+      const bool in = r2 < rc2;  // the target itself is listed and skipped when evaluated
       const unsigned m = __ballot_sync(full, in);
       if (in) list[cnt + __popc(m & below)] = (unsigned short)k;
       cnt += __popc(m);
@@ -705,8 +732,9 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
       cnt = cstart[k + 1] - st;
       // source beyond the -L/2 edge sits near +L/2: s = +L/2, and vice versa
       if (periodic_cells) {
-        sx = x0 < 0 ? (T)g.halfL[0] : (x0 >= g.nc[0] ? (T)(-g.halfL[0]) : T(0));
-        sy = y0 < 0 ? (T)g.halfL[1] : (y0 >= g.nc[1] ? (T)(-g.halfL[1]) : T(0));
+        const T hx = near_const<T>(g, kNcHLx), hy = near_const<T>(g, kNcHLy);
+        sx = x0 < 0 ? hx : (x0 >= g.nc[0] ? -hx : T(0));
+        sy = y0 < 0 ? hy : (y0 >= g.nc[1] ? -hy : T(0));
       }
     }
     int incl = cnt;
@@ -730,15 +758,15 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
   }
   __syncthreads();
   const T* tb_ = tab_sm ? stab : tab;
-  const T rc = (T)g.rc, rc2 = rc * rc;
-  const T hK = rc / (T)g.K, ihK = (T)g.K / rc;
+  const T rc2 = near_const<T>(g, kNcRc2);
+  const T hK = near_const<T>(g, kNcHK), ihK = near_const<T>(g, kNcIhK);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kNearThreads / 32;
   unsigned short* mylist = list[warp];
   const int ntg = te - tb;
   const int nsrc = coff[ncell];
   const bool shifted = any_shift != 0;
-  const T Lx = (T)g.L[0], Ly = (T)g.L[1];
-  const T iLx = (T)(1.0 / g.L[0]), iLy = (T)(1.0 / g.L[1]);
+  const T Lx = near_const<T>(g, kNcLx), Ly = near_const<T>(g, kNcLy);
+  const T iLx = near_const<T>(g, kNcILx), iLy = near_const<T>(g, kNcILy);
   // sources in passes of at most kNearSrc (one pass in the usual case)
   for (int s0 = 0; s0 < nsrc; s0 += kNearSrc) {
     const int ns = min(kNearSrc, nsrc - s0);
@@ -2078,6 +2106,8 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   ng.rc = m.rc;
   ng.K = p->near_K;
   ng.D = p->near_D;
+  near_consts<float>(ng, ng.cf);
+  near_consts<double>(ng, ng.cd);
   // the near field depends only on the binning: fork it onto the side stream
   const cudaStream_t sn = p->side_stream;
   SOG_CK(cudaEventRecord(p->ev_fork, s));

@@ -532,7 +532,9 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     g.I[1] = Iy;
     g.I[2] = Iz;
     for (int d = 0; d < 3; ++d) {
-      g.T[d] = std::min(T, g.I[d]);
+      // as many tiles as edge T needs, their edge evened out (120 = 8 x 15)
+      const int nt = (g.I[d] + T - 1) / T;
+      g.T[d] = (g.I[d] + nt - 1) / nt;
       g.nt[d] = (g.I[d] + g.T[d] - 1) / g.T[d];
       g.W[d] = g.T[d] + prm.P_win;
     }
