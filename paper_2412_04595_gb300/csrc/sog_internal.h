@@ -16,7 +16,7 @@ constexpr int kMaxCheb = 64;
 constexpr int kMaxWin = 16;
 constexpr int kNearD = 8;  // degree of the near-field table polynomials
 constexpr int kMaxHalfModes = 256;  // long range by direct sums: half-plane modes
-constexpr int kModeBlocks = 152;    // CTAs of its moment sums
+constexpr int kModeBlocks = 608;    // CTAs of its moment sums (4 per SM)
 constexpr int kMaxHalfModeCoefs = 8192;  // half-plane modes x P_cheb (on-chip table)
 
 // Half-plane mode idx of the direct long range: n_x = 0 with n_y = 1..Ky,

@@ -1015,20 +1015,22 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
     }
   }
   __syncthreads();
-  if (sizeof(T) == 4 && ((ox | g.I[0] | g.pitch) & 1) == 0) {
-    // FP32: pairs of columns (x even, x + 1) with one 8-byte atomic; an even
-    // tile origin and even grid width keep a pair inside one row (for odd W0
-    // the last pair adds zero to the column after the tile)
-    const int W0h = (W0 + 1) >> 1, tot = W0h * W1 * W2;
+  if (sizeof(T) == 4 && ((g.I[0] | g.pitch) & 1) == 0) {
+    // FP32: pairs of columns (x even, x + 1) with one 8-byte atomic; the
+    // even grid width keeps a pair inside one row.  Pairs start at the even
+    // column ox0 <= ox; columns outside the tile add zero.
+    const int ox0 = ox & ~1;
+    const int W0h = (ox + W0 - ox0 + 1) >> 1, tot = W0h * W1 * W2;
     const int nt = blockDim.x;
     int lx = threadIdx.x % W0h, rr = threadIdx.x / W0h;
     int ly = rr % W1, lz = rr / W1;
     const int sx = nt % W0h, sr = nt / W0h, sy = sr % W1, sz = sr / W1;
     for (int i = threadIdx.x; i < tot; i += nt) {
-      const A* sp = st + lz * PS + ly * RP + 2 * lx;
-      const A v0 = sp[0], v1 = 2 * lx + 1 < W0 ? sp[1] : A(0);
+      const int c0 = ox0 + 2 * lx - ox;  // tile column of the pair's first element
+      const A* sp = st + lz * PS + ly * RP;
+      const A v0 = c0 >= 0 ? sp[c0] : A(0), v1 = c0 + 1 < W0 ? sp[c0 + 1] : A(0);
       if ((v0 | v1) != 0) {
-        float* gp = reinterpret_cast<float*>(grid) + zoff[lz] + yoff[ly] + pmod(ox + 2 * lx, g.I[0]);
+        float* gp = reinterpret_cast<float*>(grid) + zoff[lz] + yoff[ly] + pmod(ox0 + 2 * lx, g.I[0]);
         atomicAdd(reinterpret_cast<float2*>(gp), make_float2((float)v0 * (float)iS, (float)v1 * (float)iS));
       }
       lx += sx;
@@ -1583,14 +1585,14 @@ __device__ __forceinline__ void cis_run(T t, T tl, int n0, int cnt, T sgn, Cx<T>
 // Per-block partial moments.  A batch of nbt particles is staged (q T_n,
 // e^{-ik_x x}, e^{-ik_y y}); thread (mode, group) sums the batch's particles
 // j = group (mod groups) for its mode in the element type; at the end the
-// groups are added in a fixed order, kModeRed orders at a time, and written
-// in FP64.
+// groups are added in a fixed order in the element type, kModeRed orders at
+// a time, and written per block.
 constexpr int kModeRed = 16;
 
 template <typename T, int PMAX>
 __global__ void __launch_bounds__(kModeThreads) k_lmodes_moments(
     const T* __restrict__ q, const T* __restrict__ r, int N, int P, int Kx, int Ky, int nhalf,
-    int nbt, ModeGeom<T> mg, double* __restrict__ part) {
+    int nbt, ModeGeom<T> mg, T* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ny_all = 2 * Ky + 1;
   T* tq = reinterpret_cast<T*>(smraw);                   // [j][PMAX]
@@ -1655,12 +1657,12 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_moments(
       const int pc = min(kModeRed, P - c0);
       for (int idx = threadIdx.x; idx < nhalf * pc; idx += blockDim.x) {
         const int md = idx / pc, k = idx - md * pc;
-        double sr = 0.0, si = 0.0;
+        T sr = T(0), si = T(0);
         for (int g = 0; g < G; ++g) {
-          sr += (double)red[((g * nhalf + md) * kModeRed + k) * 2];
-          si += (double)red[((g * nhalf + md) * kModeRed + k) * 2 + 1];
+          sr += red[((g * nhalf + md) * kModeRed + k) * 2];
+          si += red[((g * nhalf + md) * kModeRed + k) * 2 + 1];
         }
-        double* o = part + (((size_t)blockIdx.x * nhalf + md) * P + c0 + k) * 2;
+        T* o = part + (((size_t)blockIdx.x * nhalf + md) * P + c0 + k) * 2;
         o[0] = sr;
         o[1] = si;
       }
@@ -1670,21 +1672,35 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_moments(
 
 // Coefficients: one block per half-plane mode.  Thread t takes the value
 // t mod 2P (order n, real or imaginary part) of the blocks b = t / 2P (mod
-// groups) in a fixed order, the groups are added in a fixed order in FP64,
-// and the mode's P x P kernel is applied.
+// groups) in a fixed order (FP32 plans: compensated float sums, as precise
+// as FP64 here and without the slow FP64 pipe), the groups are added in a
+// fixed order in FP64, and the mode's P x P kernel is applied.
+constexpr int kCoefThreads = 1024;
 template <typename T>
-__global__ void __launch_bounds__(256) k_lmodes_coeffs(const double* __restrict__ part, int nblk,
-                                                       int nhalf, int P, const T* __restrict__ K,
-                                                       T* __restrict__ coef) {
-  __shared__ double gs[256];
+__global__ void __launch_bounds__(kCoefThreads) k_lmodes_coeffs(const T* __restrict__ part,
+                                                                int nblk, int nhalf, int P,
+                                                                const T* __restrict__ K,
+                                                                T* __restrict__ coef) {
+  __shared__ double gs[kCoefThreads];
   __shared__ double mu[kMaxCheb * 2];
   const int mode = blockIdx.x;
   const int w = 2 * P, G = blockDim.x / w;
   const int v = threadIdx.x % w, g = threadIdx.x / w;
-  double s = 0.0;
-  if (g < G)
-    for (int b = g; b < nblk; b += G) s += part[((size_t)b * nhalf + mode) * w + v];
-  gs[threadIdx.x] = s;
+  T s = T(0), c = T(0);
+  if (g < G) {
+#pragma unroll 4
+    for (int b = g; b < nblk; b += G) {
+      const T x = part[((size_t)b * nhalf + mode) * w + v];
+      if constexpr (sizeof(T) == 4) {
+        const T t = s + x, bx = t - s;
+        c += (s - (t - bx)) + (x - bx);
+        s = t;
+      } else {
+        s += x;
+      }
+    }
+  }
+  gs[threadIdx.x] = (double)s + (double)c;
   __syncthreads();
   if (threadIdx.x < w) {
     double t = 0.0;
@@ -2163,17 +2179,18 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
                                 (size_t)kModeThreads * kModeRed * 2 * sizeof(T));
     const size_t sm3 = (size_t)nh * P * 2 * sizeof(T);
     const ModeGeom<T> mg = mode_geom<T>(m.L[0], m.L[1], m.L[2]);
+    T* lmom = reinterpret_cast<T*>(p->d_lmom);  // per-block moments in the element type
     mark_begin(p, 5, sl);
     if (pmax == 16)
-      k_lmodes_moments<T, 16><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, p->d_lmom);
+      k_lmodes_moments<T, 16><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
     else if (pmax == 32)
-      k_lmodes_moments<T, 32><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, p->d_lmom);
+      k_lmodes_moments<T, 32><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
     else
-      k_lmodes_moments<T, 64><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, p->d_lmom);
+      k_lmodes_moments<T, 64><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
     LAUNCH_CHECK();
     mark_end(p, 5, sl);
     mark_begin(p, 6, sl);
-    k_lmodes_coeffs<T><<<nh, 256, 0, sl>>>(p->d_lmom, kModeBlocks, nh, P,
+    k_lmodes_coeffs<T><<<nh, kCoefThreads, 0, sl>>>(lmom, kModeBlocks, nh, P,
                                                      reinterpret_cast<const T*>(p->d_kmat),
                                                      reinterpret_cast<T*>(p->d_lcoef));
     LAUNCH_CHECK();
