@@ -1803,18 +1803,15 @@ constexpr int kK0Blocks = 152, kK0Threads = 128;
 template <typename T, int PMAX>
 __global__ void __launch_bounds__(kK0Threads) k_k0_moments(const T* __restrict__ q,
                                                            const T* __restrict__ r, int N, int P,
-                                                           double halfLz, double* __restrict__ part) {
+                                                           ModeGeom<T> mg, double* __restrict__ part) {
   __shared__ double wsum[kK0Threads / 32][PMAX];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // a thread sums its few particles in T, the block sums in double
   T mom[PMAX];
 #pragma unroll
   for (int n = 0; n < PMAX; ++n) mom[n] = T(0);
-  const double ih = 1.0 / halfLz;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    double z = (double)r[3 * i + 2];
-    if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
-    const T x = (T)(z * ih);
+    const T x = cheb_x(r[3 * i + 2], mg);
     T qi = q[i];
     if (!isfinite(qi)) qi = T(0);
     T t0 = T(1), t1 = x;
@@ -1829,7 +1826,23 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_moments(const T* __restrict__
 #pragma unroll
   for (int n = 0; n < PMAX; ++n) {
     if (n < P) {
-      const double v = warp_sum((double)mom[n]);
+      double v;
+      if constexpr (sizeof(T) == 4) {
+        // warp sum as a float pair (two-sum at every level): FP64 precision
+        // without warp-wide FP64 instructions
+        float hi = mom[n], lo = 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+          const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+          const float sm = hi + h2, bv = sm - hi;
+          lo += l2 + ((hi - (sm - bv)) + (h2 - bv));
+          hi = sm;
+        }
+        v = (double)hi + (double)lo;
+      } else {
+        v = warp_sum((double)mom[n]);
+      }
       if (lane == 0) wsum[warp][n] = v;
     }
   }
@@ -2164,7 +2177,9 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     SOG_CK(cudaMemsetAsync(pg + 3 * (size_t)N, 0, sizeof(double) * 3 * N, s));
   }
 
-  // 4-5. long range and its k = 0 mode, on long_stream
+  // 4-5. long range and its k = 0 mode, on long_stream (started after the
+  // binning: starting the direct sums and the k = 0 moments with the
+  // evaluation only delays the binning that every other part waits for)
   const cudaStream_t sl = p->long_stream;
   SOG_CK(cudaStreamWaitEvent(sl, p->ev_fork, 0));
   if (p->has_long && p->long_direct) {
@@ -2205,6 +2220,19 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
       k_lmodes_eval<T, 64><<<(N + kModeThreads - 1) / kModeThreads, kModeThreads, sm3, sl>>>(r, N, P, Kx, Ky, nh, mg, cf, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     LAUNCH_CHECK();
     mark_end(p, 7, sl);
+  }
+  if (p->has_long) {
+    mark_begin(p, 8, sl);
+    const int P = m.P_cheb;
+    double* mpart = p->d_red + 2 * kRedBlocks;
+    const ModeGeom<T> mg0 = mode_geom<T>(m.L[0], m.L[1], m.L[2]);
+    if (P <= 16)
+      k_k0_moments<T, 16><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+    else if (P <= 32)
+      k_k0_moments<T, 32><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+    else
+      k_k0_moments<T, 64><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+    LAUNCH_CHECK();
   }
   if (p->has_long) {
     const int P = m.P_cheb;
@@ -2257,15 +2285,6 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     LAUNCH_CHECK();
     mark_end(p, 7, sl);
     }
-    mark_begin(p, 8, sl);
-    double* mpart = p->d_red + 2 * kRedBlocks;
-    if (P <= 16)
-      k_k0_moments<T, 16><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, 0.5 * m.L[2], mpart);
-    else if (P <= 32)
-      k_k0_moments<T, 32><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, 0.5 * m.L[2], mpart);
-    else
-      k_k0_moments<T, 64><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, 0.5 * m.L[2], mpart);
-    LAUNCH_CHECK();
     k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, P, p->d_k0mat,
                                      p->d_k0nu, p->d_red, kRedBlocks, p->d_status);
     LAUNCH_CHECK();
