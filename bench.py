@@ -489,7 +489,8 @@ def main():
             "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": roof,
             "roofline_stages": [o for o in others if o is not None],
             "stage_ms": {k: round(v, 5) for k, v in res["stage_ms"].items()},
-            "params": {k: prm[k] for k in ("rc", "M", "m", "I", "P_win", "I_long", "P_cheb")}}
+            "params": {k: prm[k] for k in ("rc", "M", "m", "I", "P_win", "I_long", "P_cheb",
+                                           "long_direct")}}
     if not args.no_cpu_baseline:
         from oracle import sog as osog
         oprm = osog.select_params(N, *wl["L"], wl["tol"], n_nb=args.n_nb)

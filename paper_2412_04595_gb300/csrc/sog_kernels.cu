@@ -2177,9 +2177,10 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     SOG_CK(cudaMemsetAsync(pg + 3 * (size_t)N, 0, sizeof(double) * 3 * N, s));
   }
 
-  // 4-5. long range and its k = 0 mode, on long_stream (started after the
-  // binning: starting the direct sums and the k = 0 moments with the
-  // evaluation only delays the binning that every other part waits for)
+  // 4-5. long range and its k = 0 mode, on long_stream, after the binning
+  // (the direct sums and the k = 0 moments could start with the evaluation,
+  // but measured no faster: they compete with the binning that every other
+  // part waits for)
   const cudaStream_t sl = p->long_stream;
   SOG_CK(cudaStreamWaitEvent(sl, p->ev_fork, 0));
   if (p->has_long && p->long_direct) {
