@@ -4,12 +4,13 @@
 // backward 3D FFT on the real grid; Algorithm 2 needs forward and backward 2D
 // FFTs of every Chebyshev proxy plane with a z-contraction in between.
 //
-// Engine: a CTA of kFftThreads threads holds a set of lines in shared memory
-// and transforms them in place with self-sorting (Stockham) stages of radix
-// 2, 3, 4, 5, 7 or 8.  In a stage every thread reads the inputs of its
-// butterflies into registers, applies twiddles and the butterfly, waits at a
-// barrier and writes the outputs, so one buffer suffices; a thread holds at
-// most kFftCap complex values.  Index arithmetic uses exact float
+// Engine: a CTA (FftCfg: threads, values per thread) holds a set of lines in
+// shared memory and transforms them in place with self-sorting (Stockham)
+// stages of radix 2, 3, 4, 5, 7, 8, and for FP32 also 15 (3 x 5) and 16
+// (4 x 4).  In a stage every thread reads the inputs of its butterflies into
+// registers, applies twiddles and the butterfly, waits at a barrier and
+// writes the outputs, so one buffer suffices; a thread holds at most
+// FftCfg::cap complex values.  Index arithmetic uses exact float
 // reciprocals instead of integer division.  Transforms are unnormalised; the
 // 1/n factors live in the scaling tables.
 //
@@ -109,18 +110,18 @@ __device__ __forceinline__ T2 pm_i(T2 a, T2 b, bool plus) {
 
 template <typename T2, int R, typename T4>
 __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
-  if (R == 2) {
+  if constexpr (R == 2) {
     const T2 a = x[0], b = x[1];
     x[0] = cadd(a, b);
     x[1] = csub(a, b);
-  } else if (R == 4) {
+  } else if constexpr (R == 4) {
     const T2 s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
     const T2 s13 = cadd(x[1], x[3]), d13 = rot(csub(x[1], x[3]), inv);
     x[0] = cadd(s02, s13);
     x[2] = csub(s02, s13);
     x[1] = cadd(d02, d13);
     x[3] = csub(d02, d13);
-  } else if (R == 8) {
+  } else if constexpr (R == 8) {
     // two DFT4 on even and odd samples, odd part rotated by w8^k
     T2 e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
     dft<T2, 4>(e, inv, tw, n);
@@ -142,7 +143,7 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
     x[6] = csub(e[2], o2);
     x[3] = cadd(e[3], o3);
     x[7] = csub(e[3], o3);
-  } else if (R == 3) {
+  } else if constexpr (R == 3) {
     // w = e^(-2 pi i / 3) = -1/2 - i sqrt3/2
     const T2 t = cadd(x[1], x[2]), d = csub(x[1], x[2]);
     const T2 a = T2{x[0].x - 0.5f * t.x, x[0].y - 0.5f * t.y};
@@ -151,7 +152,7 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
     x[0] = cadd(x[0], t);
     x[1] = pm_i(a, b, inv);
     x[2] = pm_i(a, b, !inv);
-  } else if (R == 5) {
+  } else if constexpr (R == 5) {
     // w = e^(-2 pi i / 5) = c1 - i s1, w^2 = c2 - i s2
     const T2 t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
     const T2 t3 = csub(x[1], x[4]), t4 = csub(x[2], x[3]);
@@ -172,6 +173,45 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
     x[4] = pm_i(a1, b1, !inv);
     x[2] = pm_i(a2, b2, inv);
     x[3] = pm_i(a2, b2, !inv);
+  } else if constexpr (R == 16) {
+    // 4 x 4: DFT4 over x[j2 + 4 j1] for each j2, twiddles w16^(j2 k1) from
+    // the length-n table (entry j2 k1 n / 16), DFT4 over j2 for each k1;
+    // output k1 + 4 k2
+    T2 a[4][4];
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+      T2 v[4] = {x[j2], x[4 + j2], x[8 + j2], x[12 + j2]};
+      dft<T2, 4>(v, inv, tw, n);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1)
+        a[j2][k1] = (j2 == 0 || k1 == 0) ? v[k1] : cmul_tw(v[k1], tw[j2 * k1 * (n / 16)], inv);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      T2 v[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+      dft<T2, 4>(v, inv, tw, n);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = v[k2];
+    }
+  } else if constexpr (R == 15) {
+    // 3 x 5: DFT3 over x[j2 + 5 j1] for each j2, twiddles w15^(j2 k1) from
+    // the length-n table, DFT5 over j2 for each k1; output k1 + 3 k2
+    T2 a[5][3];
+#pragma unroll
+    for (int j2 = 0; j2 < 5; ++j2) {
+      T2 v[3] = {x[j2], x[5 + j2], x[10 + j2]};
+      dft<T2, 3>(v, inv, tw, n);
+#pragma unroll
+      for (int k1 = 0; k1 < 3; ++k1)
+        a[j2][k1] = (j2 == 0 || k1 == 0) ? v[k1] : cmul_tw(v[k1], tw[j2 * k1 * (n / 15)], inv);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+      T2 v[5] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1], a[4][k1]};
+      dft<T2, 5>(v, inv, tw, n);
+#pragma unroll
+      for (int k2 = 0; k2 < 5; ++k2) x[k1 + 3 * k2] = v[k2];
+    }
   } else {
     // other odd radix (7): y_q = sum_p x_p w^(qp), w = exp(-+2 pi i / R) from
     // the length-n table (entry (qp mod R) n / R)
@@ -238,13 +278,19 @@ __device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T4*
   __syncthreads();
 }
 
-// All stages of one length.  The factorisation orders the radices 8..8, 4,
-// 2, 3..3, 5..5, 7..7; each group is a separate straight-line block so that
-// the registers of one stage are free for the next.
+// All stages of one length.  The factorisation orders the radices 16..16,
+// 15..15 (engines holding at least 16 values per thread), 8..8, 4, 2, 3..3,
+// 5..5, 7..7; each group is a separate straight-line block so that the
+// registers of one stage are free for the next.
 template <typename T2, int CAP, typename T4>
 __device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T4* tw, bool inv) {
-  const int n8 = f.n8, n4 = f.n4, n2 = f.n2, n3 = f.n3, n5 = f.n5, n7 = f.n7;
+  const int n16 = f.n16, n15 = f.n15, n8 = f.n8, n4 = f.n4, n2 = f.n2, n3 = f.n3, n5 = f.n5,
+            n7 = f.n7;
   int L = 1;
+  if constexpr (CAP >= 16) {
+    for (int i = 0; i < n16; ++i, L *= 16) stage<T2, CAP, 16>(buf, s, L, tw, inv);
+    for (int i = 0; i < n15; ++i, L *= 15) stage<T2, CAP, 15>(buf, s, L, tw, inv);
+  }
   for (int i = 0; i < n8; ++i, L *= 8) stage<T2, CAP, 8>(buf, s, L, tw, inv);
   if (n4) { stage<T2, CAP, 4>(buf, s, L, tw, inv); L *= 4; }
   if (n2) { stage<T2, CAP, 2>(buf, s, L, tw, inv); L *= 2; }

@@ -39,7 +39,7 @@ struct FftLen {
   int nst;
   int radix[kMaxFftStages];
   int tw_off;
-  int n8, n4, n2, n3, n5, n7;  // stages of each radix, in this order
+  int n16, n15, n8, n4, n2, n3, n5, n7;  // stages of each radix, in this order
 };
 
 // Particle record (x, y, z, q) or (local grid coordinates, q).

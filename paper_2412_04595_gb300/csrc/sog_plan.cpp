@@ -273,18 +273,25 @@ sog_status check_params(const sog_params& p) {
 // tables
 // ---------------------------------------------------------------------------
 
-void factorize(int n, sogk::FftLen& f) {
+// big: radices 16 and 15 first (engines holding 16 values per thread)
+void factorize(int n, sogk::FftLen& f, bool big) {
   f.n = n;
   f.nst = 0;
   int k = n;
+  if (big) {
+    while (k % 16 == 0) { f.radix[f.nst++] = 16; k /= 16; }
+    while (k % 15 == 0) { f.radix[f.nst++] = 15; k /= 15; }
+  }
   while (k % 8 == 0 && k > 1) { f.radix[f.nst++] = 8; k /= 8; }
   while (k % 4 == 0) { f.radix[f.nst++] = 4; k /= 4; }
   while (k % 2 == 0) { f.radix[f.nst++] = 2; k /= 2; }
   for (int p : {3, 5, 7})
     while (k % p == 0) { f.radix[f.nst++] = p; k /= p; }
-  f.n8 = f.n4 = f.n2 = f.n3 = f.n5 = f.n7 = 0;
+  f.n16 = f.n15 = f.n8 = f.n4 = f.n2 = f.n3 = f.n5 = f.n7 = 0;
   for (int st = 0; st < f.nst; ++st) {
     const int R = f.radix[st];
+    f.n16 += R == 16;
+    f.n15 += R == 15;
     f.n8 += R == 8;
     f.n4 += R == 4;
     f.n2 += R == 2;
@@ -588,7 +595,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   std::vector<double> tw;
   const int tw_vals = prec == SOG_PREC_MIXED ? 4 : 2;
   auto add_len = [&](int n, sogk::FftLen& f) {
-    factorize(n, f);
+    factorize(n, f, prec != SOG_PREC_FP64);
     f.tw_off = (int)(tw.size() / tw_vals);
     for (int t = 0; t < n; ++t) {
       const double c = cos(2.0 * kPi * t / n), sn = -sin(2.0 * kPi * t / n);
