@@ -791,11 +791,22 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
     }
     __syncthreads();
     OutSlots<T> out{T(0), 0, 0};
+    // the next target's record and output index are loaded one target ahead
+    P4<T> a_next{};
+    int o_next = 0;
+    if (warp < ntg) {
+      a_next = rec[tb + warp];
+      o_next = perm[tb + warp];
+    }
     for (int t0 = 0; t0 < ntg; t0 += nw) {
       const int tt = t0 + warp;
       if (tt >= ntg) break;
-      const int ti = tb + tt;
-      const P4<T> a = rec[ti];
+      const P4<T> a = a_next;
+      const int oi = o_next;
+      if (tt + nw < ntg) {
+        a_next = rec[tb + tt + nw];
+        o_next = perm[tb + tt + nw];
+      }
       T v0, v1, v2, v3;
       if (!periodic_cells) {
         // few cells: minimum image per pair (sources unshifted)
@@ -819,7 +830,7 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
       } else {
         near_target<T, false>(a, src, shs, nsteps, rc2, tb_, g.K, hK, ihK, mylist, v0, v1, v2, v3);
       }
-      out.put(warp_sum4(v0, v1, v2, v3), perm[ti]);
+      out.put(warp_sum4(v0, v1, v2, v3), oi);
       if (out.n == 8) out.flush(phi_out, grad_out, s0 > 0);
     }
     out.flush(phi_out, grad_out, s0 > 0);
@@ -1137,8 +1148,21 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
   const int l1 = lane + 32, ax1 = l1 / P, k1 = l1 - ax1 * P;
   const T ih_lane = (T)((lane >> 3) == 1 ? invh.x : ((lane >> 3) == 2 ? invh.y : invh.z));
   OutSlots<T> out{T(0), 0, 0};
+  // the next particle's record and output index are loaded one iteration
+  // ahead, so their latency overlaps the current particle's sums
+  P4<T> a_next{};
+  int o_next = 0;
+  if (b + warp < e) {
+    a_next = rec[b + warp];
+    o_next = perm[b + warp];
+  }
   for (int j = b + warp; j < e; j += nw) {
-    const P4<T> a = rec[j];
+    const P4<T> a = a_next;
+    const int oj = o_next;
+    if (j + nw < e) {
+      a_next = rec[j + nw];
+      o_next = perm[j + nw];
+    }
     const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half),
               gz0 = (int)dceil(a.z - w.half);
     {
@@ -1190,7 +1214,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
     }
     __syncwarp();
     const T tot = warp_sum4(f, fx, fy, fz);
-    out.put(lane < 8 ? tot : tot * ih_lane, perm[j]);
+    out.put(lane < 8 ? tot : tot * ih_lane, oj);
     if (out.n == 8) out.flush(phi_out, grad_out, false);
   }
   out.flush(phi_out, grad_out, false);
