@@ -361,19 +361,6 @@ __device__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// Rank of this thread's particle inside bin `key`: one atomic per group of
-// lanes of the warp that share the key (many particles share a bin).
-__device__ __forceinline__ int agg_rank(int* __restrict__ cnt, int key) {
-  const unsigned act = __activemask();
-  const unsigned peers = __match_any_sync(act, key);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(cnt + key, __popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  return base + __popc(peers & ((1u << lane) - 1u));
-}
-
 template <typename T>
 __global__ void k_bin_count(PrepGeom g, const T* __restrict__ q, const T* __restrict__ r, int N,
                             int* __restrict__ key, int* __restrict__ rank, int* __restrict__ cnt,
@@ -386,18 +373,31 @@ __global__ void k_bin_count(PrepGeom g, const T* __restrict__ q, const T* __rest
     P4<T> rn, rm, rl;
     int kn, km, kl;
     prep_particle<T>(g, q, r, i, bits, rn, kn, km, rm, kl, rl);
+    // ranks in the three binnings: the atomics of all three are issued
+    // before any result is used, so their latencies overlap
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned pn = __match_any_sync(act, kn);
+    const unsigned pm = g.has_mid ? __match_any_sync(act, km) : 0u;
+    const unsigned pl = g.has_long ? __match_any_sync(act, kl) : 0u;
+    const int ln = __ffs(pn) - 1, lm = __ffs(pm) - 1, ll = __ffs(pl) - 1;
+    int bn = 0, bm = 0, bl = 0;
+    if (lane == ln) bn = atomicAdd(cnt + off.x + kn, __popc(pn));
+    if (g.has_mid && lane == lm) bm = atomicAdd(cnt + off.y + km, __popc(pm));
+    if (g.has_long && lane == ll) bl = atomicAdd(cnt + off.z + kl, __popc(pl));
     key[i] = kn;
-    rank[i] = agg_rank(cnt + off.x, kn);
     tmp[i] = rn;
+    rank[i] = __shfl_sync(pn, bn, ln) + __popc(pn & below);
     if (g.has_mid) {
       key[N + i] = km;
-      rank[N + i] = agg_rank(cnt + off.y, km);
       tmp[N + i] = rm;
+      rank[N + i] = __shfl_sync(pm, bm, lm) + __popc(pm & below);
     }
     if (g.has_long) {
       key[2 * N + i] = kl;
-      rank[2 * N + i] = agg_rank(cnt + off.z, kl);
       tmp[2 * N + i] = rl;
+      rank[2 * N + i] = __shfl_sync(pl, bl, ll) + __popc(pl & below);
     }
     sq += (double)rn.q;
     sa += fabs((double)rn.q);
