@@ -240,3 +240,49 @@ def test_small_and_ragged(B, oracle_mod):
         assert out["status"] == 0
         assert rel_max(out["phi"], ref["phi"]) < 1e-10
         assert rel_max(out["F"], ref["F"]) < 1e-9
+
+
+def long_variants(oracle_mod, prm, tol):
+    """The same parameters with the long range by direct sums (Algorithm 3)
+    and by window gridding and FFTs (Algorithm 2), mode counts and grids
+    sized for |k| <= K_long as the selection does."""
+    w, s = oracle_mod.sog_weights(prm["b"], prm["sigma"], prm["omega"], prm["M"])
+    Kl = 2.0 * math.sqrt(math.log(1.0 / (0.3 * tol))) / s[prm["m"] + 1]
+    Lx, Ly, _ = prm["L"]
+    Kx, Ky = math.ceil(Kl * Lx / (2 * math.pi)), math.ceil(Kl * Ly / (2 * math.pi))
+    grid = tuple(oracle_mod._fft_size(max(math.ceil(Kl * Ld / math.pi), prm["P_win"] + 4))
+                 for Ld in (Lx, Ly))
+    common = dict(L=prm["L"], b=prm["b"], r0=prm["r0"], omega=prm["omega"], rc=prm["rc"],
+                  M=prm["M"], m=prm["m"], I=prm["I"], hz=prm["hz"], P_win=prm["P_win"],
+                  P_cheb=prm["P_cheb"], window=prm["window"], shape=prm["shape"])
+    out = {"grid": oracle_mod.make_params(I_long=grid, P_long=prm["P_win"], long_direct=False,
+                                          **common)}
+    if Ky + Kx * (2 * Ky + 1) <= 256 and (Ky + Kx * (2 * Ky + 1)) * prm["P_cheb"] <= 8192:
+        out["direct"] = oracle_mod.make_params(I_long=(2 * Kx + 1, 2 * Ky + 1),
+                                               P_long=prm["P_win"], long_direct=True, **common)
+    return out
+
+
+@pytest.mark.parametrize("name", ["cube10", "box_rect"])
+def test_fp64_long_range_both_algorithms(B, oracle_mod, name):
+    """Algorithms 2 and 3 on the same system: each matches the oracle's own
+    evaluation of that algorithm to rounding, and the two long ranges agree
+    with each other to the tolerance."""
+    N, L, tol, nnb = CASES[name]
+    q, r = uniform_system(N, L, 21)
+    prm = oracle_mod.select_params(N, *L, tol, n_nb=nnb)
+    assert prm["m"] < prm["M"]
+    variants = long_variants(oracle_mod, prm, tol)
+    assert "direct" in variants
+    longs = {}
+    for kind, pv in variants.items():
+        ref = oracle_mod.sog_eval(pv, q, r)
+        out = run_gpu(B, pv, q, r, B.SOG_PREC_FP64, parts=True)
+        assert out["status"] == 0
+        rp, rg = ref["parts"]["long"]
+        assert rel_max(out["pp"][2], rp) < 1e-11, (name, kind, rel_max(out["pp"][2], rp))
+        assert rel_max(out["pg"][2], rg) < 1e-10, (name, kind, rel_max(out["pg"][2], rg))
+        longs[kind] = out["pp"][2]
+    # both approximate the same long-range potential within the tolerance
+    scale = np.max(np.abs(longs["grid"]))
+    assert np.max(np.abs(longs["direct"] - longs["grid"])) < 10 * tol * max(scale, 1.0)
