@@ -54,10 +54,10 @@ typedef enum {
 } sog_status;
 
 enum { SOG_PREC_FP64 = 0, SOG_PREC_MIXED = 1 };
-enum { SOG_WIN_ES = 0, SOG_WIN_GAUSS = 1 };
+enum { SOG_WIN_ES = 0, SOG_WIN_GAUSS = 1, SOG_WIN_KB = 2 };
 
 /*
- * Method parameters (Sec. 4.4 names).  Filled by sog_select_params or by the
+ * Method parameters (Sec. 4.3 names).  Filled by sog_select_params or by the
  * caller (sog_opts.manual).
  *   L        box lengths (Lx, Ly, Lz)
  *   b, r0, omega   SOG row (Table 1): bandwidth ratio, scaled cutoff, w_0 factor
@@ -68,11 +68,12 @@ enum { SOG_WIN_ES = 0, SOG_WIN_GAUSS = 1 };
  *   I        mid grid Ix, Iy, Iz* (Iz* spans the padded box, Eq. 3.20)
  *   hz       mid grid spacing in z; Lz* = Iz* hz
  *   P_win    window support in grid points (Sec. 3.4), 2..16
- *   shape    window shape: ES beta, or Gaussian S (Eq. 4.7)
+ *   shape    window shape: ES or KB beta, or Gaussian S (Eq. 4.7)
  *   I_long   long-range grid Ix_long, Iy_long (Sec. 3.4)
  *   P_long, shape_long   long-range window support and shape
  *   P_cheb   number of Chebyshev proxy points in z (Eq. A.6), 2..64
- *   window   SOG_WIN_ES or SOG_WIN_GAUSS (Remark 3.4)
+ *   window   SOG_WIN_ES, SOG_WIN_GAUSS or SOG_WIN_KB (Kaiser-Bessel,
+ *            I0(beta sqrt(1 - v^2)) / I0(beta); Remark 3.4, Sec. 5.1)
  *   long_direct  0: long range by window gridding and 2D FFTs (Algorithm 2);
  *            1: by direct Fourier sums without FFT (Algorithm 3) over the
  *            modes |n_x| <= (Ix_long-1)/2, |n_y| <= (Iy_long-1)/2 (odd
@@ -112,7 +113,7 @@ typedef struct sog_opts {
 } sog_opts;
 
 /*
- * Analytic parameter selection of Sec. 4.4 (host only, no device work):
+ * Analytic parameter selection of Sec. 4.3 (host only, no device work):
  * Table 1 row, cutoff from the density, M, mid grid from K_max (Theorem 4.2),
  * window support, then the split index m, padding Lz* and Chebyshev order P
  * chosen by minimising an operation count (the role of Eq. 4.49) under the
@@ -235,7 +236,7 @@ void sog_batch_destroy(sog_batch* batch);
 
 /*
  * Learned parameter proposer (the paper selects parameters analytically,
- * Sec. 4.4; that selection remains the fallback).  A multilayer perceptron
+ * Sec. 4.3; that selection remains the fallback).  A multilayer perceptron
  * with two tanh hidden layers of n_hidden units and one output, in FP32 on
  * the device, with its own forward, backward and Adam kernels.  Parameters
  * form one array: W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], w3 [H], b3 [1].

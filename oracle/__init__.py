@@ -7,7 +7,7 @@ never loads them.  Its results are the expected values of every parity test.
 
 Modules:
   sog          the method step by step in numpy (Algorithms 1 and 2), the
-               parameter selection of Sec. 4.4, and wrappers of the C sums.
+               parameter selection of Sec. 4.3, and wrappers of the C sums.
   sog_oracle.c Ewald2D, brute-force image sums, the near-field direct sum and
                real-space Gaussian image sums, in plain C with OpenMP.
 

@@ -22,7 +22,7 @@ The steps follow the paper in its own order and notation:
 * the k = 0 mode of the long range in exact moments (Eq. 4.40 at k = 0 with
   the neutral constant removed, Eq. 2.4).
 * assembly Eq. 3.22 with the self term subtracted (Eq. 2.13, 2.28).
-* parameter selection, Sec. 4.4.
+* parameter selection, Sec. 4.3.
 
 Readings where the paper is silent or inconsistent are marked READING.
 """
@@ -127,7 +127,9 @@ def table1_row_for(tol: float):
 class Window:
     """Window on a support of P grid points, half-width H = (P-1) h / 2
     (Sec. 3.4).  kind 'es': exponential of semicircle exp(beta(sqrt(1-v^2)-1));
-    kind 'gauss': exp(-S v^2) (Eq. 4.7).  v = x / H, zero for |v| > 1."""
+    kind 'gauss': exp(-S v^2) (Eq. 4.7); kind 'kb': Kaiser-Bessel
+    I0(beta sqrt(1-v^2)) / I0(beta) (Remark 3.4, Sec. 5.1).  v = x / H, zero
+    for |v| > 1."""
     kind: str
     P: int
     shape: float
@@ -142,6 +144,10 @@ class Window:
         if self.kind == "es":
             a = np.sqrt(np.clip((1.0 - v) * (1.0 + v), 0.0, None))
             val = np.exp(self.shape * (a - 1.0))
+        elif self.kind == "kb":
+            # I0(b a) / I0(b) through the scaled Bessel function i0e(x) = e^-x I0(x)
+            a = np.sqrt(np.clip((1.0 - v) * (1.0 + v), 0.0, None))
+            val = special.i0e(self.shape * a) / special.i0e(self.shape) * np.exp(self.shape * (a - 1.0))
         else:
             val = np.exp(-self.shape * v * v)
         return np.where(inside, val, 0.0)
@@ -152,17 +158,38 @@ class Window:
         if self.kind == "es":
             a = np.sqrt(np.clip((1.0 - v) * (1.0 + v), 1e-300, None))
             val = np.exp(self.shape * (a - 1.0)) * self.shape * (-v / a)
+        elif self.kind == "kb":
+            # d/dv I0(b a) = I1(b a) b da/dv, da/dv = -v / a
+            a = np.sqrt(np.clip((1.0 - v) * (1.0 + v), 1e-300, None))
+            val = (special.i1e(self.shape * a) / special.i0e(self.shape)
+                   * np.exp(self.shape * (a - 1.0)) * self.shape * (-v / a))
         else:
             val = np.exp(-self.shape * v * v) * (-2.0 * self.shape * v)
         return np.where(inside, val, 0.0)
 
     def ft(self, k, H: float):
         """hat W(k) = int W(x) e^{-ikx} dx for W(x) = phi(x/H).  Gaussian: the
-        closed form of Eq. 4.7.  ES: adaptive quadrature of
+        closed form of Eq. 4.7.  KB: its closed form (sinh of the root).  ES:
+        adaptive quadrature of
         H int_{-pi/2}^{pi/2} exp(beta(cos t - 1)) cos(k H sin t) cos t dt."""
         k = np.atleast_1d(np.asarray(k, dtype=np.float64))
         if self.kind == "gauss":
             return math.sqrt(PI / self.shape) * H * np.exp(-k * k * H * H / (4.0 * self.shape))
+        if self.kind == "kb":
+            # int_{-1}^{1} I0(b sqrt(1-v^2)) cos(w v) dv = 2 sinh(sqrt(b^2 - w^2)) / sqrt(b^2 - w^2)
+            # (2 sin(sqrt(w^2 - b^2)) / sqrt(w^2 - b^2) for w > b), w = k H; over I0(b)
+            b = self.shape
+            w = np.abs(k) * H
+            d = b * b - w * w
+            out = np.empty_like(k)
+            inv = 1.0 / special.i0e(b)          # e^-b / I0(b) = 1 / i0e(b)
+            pos, neg = d > 0.0, d < 0.0
+            x = np.sqrt(d[pos])
+            out[pos] = (np.exp(x - b) - np.exp(-x - b)) / x * inv
+            y = np.sqrt(-d[neg])
+            out[neg] = 2.0 * np.sin(y) / y * math.exp(-b) * inv
+            out[d == 0.0] = 2.0 * math.exp(-b) * inv
+            return H * out
         out = np.empty_like(k)
         cache = {}
         for i, kv in enumerate(k):
@@ -191,12 +218,12 @@ class Window:
 
 def make_window(kind: str, P: int, shape: float | None = None) -> Window:
     """Default shape parameters: S = 0.455 pi P for the Gaussian (Sec. 5.1);
-    beta = 1.9 P for ES.  READING: Sec. 5.1 uses beta = 2.5 P on oversampled
-    grids; on the grids of Sec. 4.4, which are not upsampled, beta = 1.9 P
-    gives a smaller window error for the same P (checked against the direct
-    Fourier sum in the tests)."""
+    beta = 1.9 P for ES and 2.0 P for KB.  READING: Sec. 5.1 uses beta = 2.5 P
+    (ES and KB) on oversampled grids; on the grids of Sec. 4.3, which are not
+    upsampled, beta = 1.9 P (ES) and 2.0 P (KB) give a smaller window error
+    for the same P (checked against the direct Fourier sum in the tests)."""
     if shape is None:
-        shape = 1.9 * P if kind == "es" else 0.455 * PI * P
+        shape = {"es": 1.9 * P, "kb": 2.0 * P}.get(kind, 0.455 * PI * P)
     return Window(kind, int(P), float(shape))
 
 
@@ -294,9 +321,9 @@ def _clog2(n: int) -> int:
 
 def select_params(N: int, Lx: float, Ly: float, Lz: float, tol: float,
                   n_nb: float = 120.0, window: str = "es"):
-    """Parameter selection of Sec. 4.4.
+    """Parameter selection of Sec. 4.3.
 
-    1. r_c from the density, r_c ~ rho^(-1/3) (Sec. 4.4, first step); READING:
+    1. r_c from the density, r_c ~ rho^(-1/3) (Sec. 4.3, first step); READING:
        r_c is set so that (4/3) pi r_c^3 rho = n_nb neighbours, capped at
        min(Lx, Ly)/2 (minimum image, Assumption 2.5).
     2. b, r_0, omega from Table 1 (row of ``table1_row_for``); sigma = r_c/r_0;
@@ -337,7 +364,7 @@ def select_params(N: int, Lx: float, Ly: float, Lz: float, tol: float,
             break
         M += 1
     w, s = sog_weights(b, sigma, omega, M)
-    C = 1.226 if window == "es" else 1.563
+    C = 1.563 if window == "gauss" else 1.226      # ES and KB alike (Sec. 5.1)
     P_win = int(math.ceil((special.erfcinv(eps) / C) ** 2))
     P_win = min(max(P_win, 4), 16)
     lne = math.log(1.0 / eps)
@@ -353,7 +380,8 @@ def select_params(N: int, Lx: float, Ly: float, Lz: float, tol: float,
             hz = Lz / Izb
             Pw = P_win
             Hz = 0.5 * (Pw - 1) * hz
-            pad = max(2.0 * Hz, s[m] * math.sqrt(lne))
+            # KB decays slowly towards its support's edge: 2.6 H_z (Sec. 3.4)
+            pad = max((2.6 if window == "kb" else 2.0) * Hz, s[m] * math.sqrt(lne))
             nz = math.ceil((Lz + pad) / hz)
             if nz > 8192 or nx > 4096 or ny > 4096:
                 continue

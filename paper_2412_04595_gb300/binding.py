@@ -12,7 +12,8 @@ import os
 from . import _build
 
 SOG_PREC_FP64, SOG_PREC_MIXED = 0, 1
-SOG_WIN_ES, SOG_WIN_GAUSS = 0, 1
+SOG_WIN_ES, SOG_WIN_GAUSS, SOG_WIN_KB = 0, 1, 2
+_WIN_NAMES = {SOG_WIN_ES: "es", SOG_WIN_GAUSS: "gauss", SOG_WIN_KB: "kb"}
 
 STATUS = {0: "SOG_OK", 1: "SOG_ERR_ARG", 2: "SOG_ERR_NONNEUTRAL", 3: "SOG_ERR_OUT_OF_BOX",
           4: "SOG_ERR_NOMEM", 5: "SOG_ERR_CUDA", 6: "SOG_ERR_PARAMS"}
@@ -33,7 +34,7 @@ class SogParams(ctypes.Structure):
                     rc=self.rc, M=self.M, m=self.m, I=tuple(self.I), hz=self.hz,
                     P_win=self.P_win, shape=self.shape, I_long=tuple(self.I_long),
                     P_long=self.P_long, shape_long=self.shape_long, P_cheb=self.P_cheb,
-                    window="es" if self.window == SOG_WIN_ES else "gauss",
+                    window=_WIN_NAMES[self.window],
                     long_direct=bool(self.long_direct))
 
     @classmethod
@@ -46,7 +47,7 @@ class SogParams(ctypes.Structure):
             setattr(p, k, int(d[k]))
         p.I[:] = list(d["I"])
         p.I_long[:] = list(d["I_long"])
-        p.window = SOG_WIN_ES if d.get("window", "es") == "es" else SOG_WIN_GAUSS
+        p.window = {v: k for k, v in _WIN_NAMES.items()}[d.get("window", "es")]
         p.long_direct = 1 if d.get("long_direct", False) else 0
         return p
 

@@ -52,7 +52,7 @@ struct alignas(4 * sizeof(T)) P4 {
 // half-width `half` = (P-1)/2 grid units, shape beta (ES) or S (Gaussian).
 struct WinPar {
   int P;
-  int kind;          // SOG_WIN_ES or SOG_WIN_GAUSS
+  int kind;          // SOG_WIN_ES, SOG_WIN_GAUSS or SOG_WIN_KB
   double half;
   double shape;
 };

@@ -20,6 +20,8 @@
 // The element type T is float (mixed precision) or double (FP64).
 #include <math.h>
 
+#include <cmath>
+
 #include "sog_internal.h"
 
 namespace sogk {
@@ -86,6 +88,7 @@ template <typename T>
 struct WinT {
   int P, kind;
   T half, inv_half, shape;
+  T norm;  // KB: 1/I0(shape) of the rounded shape
 };
 
 template <typename T>
@@ -96,9 +99,14 @@ __host__ WinT<T> wint(const WinPar& w) {
   o.half = (T)w.half;
   o.inv_half = (T)(1.0 / w.half);
   o.shape = (T)w.shape;
+  o.norm = w.kind == SOG_WIN_KB ? (T)(1.0 / std::cyl_bessel_i(0.0, (double)o.shape)) : T(0);
   return o;
 }
 
+__device__ __forceinline__ float dbessel_i0(float x) { return cyl_bessel_i0f(x); }
+__device__ __forceinline__ double dbessel_i0(double x) { return cyl_bessel_i0(x); }
+__device__ __forceinline__ float dbessel_i1(float x) { return cyl_bessel_i1f(x); }
+__device__ __forceinline__ double dbessel_i1(double x) { return cyl_bessel_i1(x); }
 __device__ __forceinline__ float dexp(float x) { return expf(x); }
 __device__ __forceinline__ double dexp(double x) { return exp(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
@@ -124,6 +132,12 @@ __device__ __forceinline__ void win_eval(const WinT<T>& w, T v, T& val, T& dval)
     const T a = dsqrt(a2);
     val = dexp(-w.shape * (v * v / (one + a)));
     if (a2 > T(0)) dval = -val * w.shape * v * drsqrt(a2);
+  } else if (w.kind == SOG_WIN_KB) {
+    // I0(beta a) / I0(beta), a = sqrt(1 - v^2); d/dv = I1(beta a) beta (-v / a) / I0(beta)
+    const T a2 = (one - v) * (one + v);
+    const T a = dsqrt(a2);
+    val = dbessel_i0(w.shape * a) * w.norm;
+    if (a2 > T(0)) dval = -dbessel_i1(w.shape * a) * w.norm * w.shape * v / a;
   } else {
     val = dexp(-w.shape * v * v);
     dval = T(-2) * w.shape * v * val;
@@ -149,6 +163,7 @@ __device__ __forceinline__ T win_val(const WinT<T>& w, T v) {
     const T a2 = (one - v) * (one + v);
     return dexp(-w.shape * (v * v / (one + dsqrt(a2))));
   }
+  if (w.kind == SOG_WIN_KB) return dbessel_i0(w.shape * dsqrt((one - v) * (one + v))) * w.norm;
   return dexp(-w.shape * v * v);
 }
 

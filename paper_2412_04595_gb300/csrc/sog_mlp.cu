@@ -1,7 +1,7 @@
 // Small multilayer perceptron that proposes the near-field neighbour count
 // (hence r_c and the rest of the split) from features of a system, with its
 // own forward, backward and Adam kernels (sog_mlp_* and sog_features in
-// sog.h).  The paper selects parameters analytically (Sec. 4.4); that
+// sog.h).  The paper selects parameters analytically (Sec. 4.3); that
 // selection stays the fallback and the judge of feasibility.
 //
 // Network: x (n_in) -> tanh(W1 x + b1) (H) -> tanh(W2 h1 + b2) (H) ->

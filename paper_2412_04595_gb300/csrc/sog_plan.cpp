@@ -1,7 +1,9 @@
-// Host side of the GB300 SOG library: parameter selection (Sec. 4.4), the
+// Host side of the GB300 SOG library: parameter selection (Sec. 4.3), the
 // FP64 tables every evaluation reads, device memory, and the C ABI of sog.h.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdlib.h>
 #include <string.h>
 
@@ -78,7 +80,9 @@ double erfcinv(double y) {
 }
 
 double shape_default(int window, int P) {
-  return window == SOG_WIN_ES ? 1.9 * P : 0.455 * kPi * P;
+  if (window == SOG_WIN_ES) return 1.9 * P;
+  if (window == SOG_WIN_KB) return 2.0 * P;
+  return 0.455 * kPi * P;
 }
 
 sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol, int window,
@@ -111,7 +115,7 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
   }
   std::vector<double> w, s;
   sog_table(b, sigma, omega, M, w, s);
-  const double C = window == SOG_WIN_ES ? 1.226 : 1.563;
+  const double C = window == SOG_WIN_GAUSS ? 1.563 : 1.226;  // ES and KB alike (Sec. 5.1)
   int P_win = (int)ceil(pow(erfcinv(eps) / C, 2));
   P_win = std::min(std::max(P_win, 4), 16);
   const double lne = log(1.0 / eps);
@@ -131,7 +135,8 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
       hz = Lz / Izb;
       Pw = P_win;
       const double Hz = 0.5 * (Pw - 1) * hz;
-      const double pad = std::max(2.0 * Hz, s[m] * sqrt(lne));
+      // KB decays slowly towards its support's edge: 2.6 H_z of padding (Sec. 3.4)
+      const double pad = std::max((window == SOG_WIN_KB ? 2.6 : 2.0) * Hz, s[m] * sqrt(lne));
       const double nz = ceil((Lz + pad) / hz);
       if (nz > 8192 || nx > 4096 || ny > 4096) continue;
       Ix = fft_size((long)nx);
@@ -237,7 +242,8 @@ sog_status check_params(const sog_params& p) {
   if (!(p.b > 1.0) || !(p.sigma > 0.0) || !(p.rc > 0.0) || !(p.omega > 0.0)) return SOG_ERR_PARAMS;
   if (p.rc > 0.5 * std::min(p.L[0], p.L[1]) * (1.0 + 1e-12)) return SOG_ERR_PARAMS;
   if (p.M < 0 || p.M > 4000 || p.m < -1 || p.m > p.M) return SOG_ERR_PARAMS;
-  if (p.window != SOG_WIN_ES && p.window != SOG_WIN_GAUSS) return SOG_ERR_PARAMS;
+  if (p.window != SOG_WIN_ES && p.window != SOG_WIN_GAUSS && p.window != SOG_WIN_KB)
+    return SOG_ERR_PARAMS;
   if (p.m >= 0) {
     for (int d = 0; d < 3; ++d)
       if (!smooth_even(p.I[d])) return SOG_ERR_PARAMS;
@@ -337,13 +343,25 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wt) {
 //   H int_{-pi/2}^{pi/2} exp(beta(cos t - 1)) cos(k H sin t) cos t dt.
 struct WinFT {
   int kind;
-  double shape, H;
+  double shape, H, norm;  // norm: the KB normalisation 1/I0(beta) the kernels apply
   std::vector<double> gx, gw;
-  WinFT(int kind_, double shape_, double H_) : kind(kind_), shape(shape_), H(H_) {
+  WinFT(int kind_, double shape_, double H_, double norm_ = 0.0)
+      : kind(kind_), shape(shape_), H(H_), norm(norm_) {
+    if (kind == SOG_WIN_KB && norm == 0.0) norm = 1.0 / std::cyl_bessel_i(0.0, shape);
     if (kind == SOG_WIN_ES) gauss_legendre(256, gx, gw);
   }
   double operator()(double k) const {
     if (kind == SOG_WIN_GAUSS) return sqrt(kPi / shape) * H * exp(-k * k * H * H / (4.0 * shape));
+    if (kind == SOG_WIN_KB) {
+      // H / I0(b) int_{-1}^{1} I0(b sqrt(1 - v^2)) cos(w v) dv, w = k H:
+      // 2 sinh(sqrt(b^2 - w^2)) / sqrt(b^2 - w^2), or 2 sin(sqrt(w^2 - b^2)) / sqrt(w^2 - b^2)
+      const double b = shape, wv = fabs(k) * H, d = b * b - wv * wv;
+      double f;
+      if (d > 0.0) f = 2.0 * sinh(sqrt(d)) / sqrt(d);
+      else if (d < 0.0) f = 2.0 * sin(sqrt(-d)) / sqrt(-d);
+      else f = 2.0;
+      return H * f * norm;
+    }
     double acc = 0.0;
     for (size_t i = 0; i < gx.size(); ++i) {
       const double t = 0.5 * kPi * gx[i];
@@ -362,6 +380,12 @@ double eff_shape(double shape, int prec) {
 }
 double eff_half(double half, int prec) {
   return prec == SOG_PREC_MIXED ? 1.0 / (double)(float)(1.0 / half) : half;
+}
+// KB normalisation 1/I0(beta) of the (rounded) shape, rounded as the kernels hold it
+double eff_norm(int kind, double shape, int prec) {
+  if (kind != SOG_WIN_KB) return 0.0;
+  const double n = 1.0 / std::cyl_bessel_i(0.0, shape);
+  return prec == SOG_PREC_MIXED ? (double)(float)n : n;
 }
 
 // Near kernel table: g(r) = 1 - r F_M(r) on [0, rc], K intervals, degree D
@@ -473,7 +497,7 @@ sog_status sog_select_params(int64_t N, double Lx, double Ly, double Lz, double 
   sog_status st = check_args(N, Lx, Ly, Lz, tol);
   if (st != SOG_OK) return st;
   const int window = opts ? opts->window : SOG_WIN_ES;
-  if (window != SOG_WIN_ES && window != SOG_WIN_GAUSS) return SOG_ERR_ARG;
+  if (window != SOG_WIN_ES && window != SOG_WIN_GAUSS && window != SOG_WIN_KB) return SOG_ERR_ARG;
   const double nnb = (opts && opts->n_nb > 0.0) ? opts->n_nb : 120.0;
   return select_params(N, Lx, Ly, Lz, tol, window, nnb, out);
 }
@@ -638,9 +662,9 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   if (p->has_mid) {
     const int C = Ix / 2 + 1;
     const double shp = eff_shape(prm.shape, prec), hw = eff_half(p->wm.half, prec);
-    WinFT fx(prm.window, shp, hw * p->h[0]);
-    WinFT fy(prm.window, shp, hw * p->h[1]);
-    WinFT fz(prm.window, shp, hw * p->h[2]);
+    WinFT fx(prm.window, shp, hw * p->h[0], eff_norm(prm.window, shp, prec));
+    WinFT fy(prm.window, shp, hw * p->h[1], eff_norm(prm.window, shp, prec));
+    WinFT fz(prm.window, shp, hw * p->h[2], eff_norm(prm.window, shp, prec));
     std::vector<double> kx(C), ky(Iy), kz(Iz), Wx(C), Wy(Iy), Wz(Iz);
     for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
     for (int f = 0; f < Iy; ++f) { ky[f] = 2.0 * kPi * std::min(f, Iy - f) / L[1]; Wy[f] = fy(ky[f]); }
@@ -733,8 +757,8 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     }
     if (!p->long_direct) {
     const double shp = eff_shape(prm.shape_long, prec), hw = eff_half(p->wl.half, prec);
-    WinFT fx(prm.window, shp, hw * p->hl[0]);
-    WinFT fy(prm.window, shp, hw * p->hl[1]);
+    WinFT fx(prm.window, shp, hw * p->hl[0], eff_norm(prm.window, shp, prec));
+    WinFT fy(prm.window, shp, hw * p->hl[1], eff_norm(prm.window, shp, prec));
     std::vector<double> Wx(C), Wy(Ily), kx(C), ky(Ily);
     for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
     for (int f = 0; f < Ily; ++f) { ky[f] = 2.0 * kPi * std::min(f, Ily - f) / L[1]; Wy[f] = fy(ky[f]); }

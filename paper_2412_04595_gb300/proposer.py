@@ -1,5 +1,5 @@
 """Learned proposal of the near-field neighbour count n_nb, and hence of the
-cutoff r_c and of everything the analytic selection (Sec. 4.4) derives from
+cutoff r_c and of everything the analytic selection (Sec. 4.3) derives from
 it: mid grid, window support, split index m, Chebyshev order.
 
 The analytic selection sizes each part for the tolerance; n_nb only moves

@@ -31,17 +31,21 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
-def test_select_params_through_the_abi_without_gpu(oracle_mod):
+@pytest.mark.parametrize("window", ["es", "kb", "gauss"])
+def test_select_params_through_the_abi_without_gpu(oracle_mod, window):
     """sog_select_params is host-only: callable here and equal to the
-    oracle's own selection (Sec. 4.4) for the benchmark configuration."""
+    oracle's own selection (Sec. 4.3) for the benchmark configuration, for
+    each window."""
     from paper_2412_04595_gb300 import _build, binding
     _build.build()
-    a = binding.sog_select_params(100000, 100.0, 100.0, 100.0, 1e-6, n_nb=120)
-    b = oracle_mod.select_params(100000, 100.0, 100.0, 100.0, 1e-6, n_nb=120)
+    code = {"es": binding.SOG_WIN_ES, "kb": binding.SOG_WIN_KB, "gauss": binding.SOG_WIN_GAUSS}
+    a = binding.sog_select_params(100000, 100.0, 100.0, 100.0, 1e-6, window=code[window], n_nb=120)
+    b = oracle_mod.select_params(100000, 100.0, 100.0, 100.0, 1e-6, n_nb=120, window=window)
+    assert a["window"] == window and a["long_direct"] == b["long_direct"]
     for k in ("M", "m", "I", "P_win", "I_long", "P_cheb"):
         assert tuple(map(int, __import__("numpy").atleast_1d(a[k]))) == \
             tuple(map(int, __import__("numpy").atleast_1d(b[k]))), k
-    for k in ("rc", "sigma", "hz"):
+    for k in ("rc", "sigma", "hz", "shape"):
         assert abs(a[k] - b[k]) <= 1e-13 * abs(b[k])
 
 

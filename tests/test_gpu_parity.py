@@ -286,3 +286,27 @@ def test_fp64_long_range_both_algorithms(B, oracle_mod, name):
     # both approximate the same long-range potential within the tolerance
     scale = np.max(np.abs(longs["grid"]))
     assert np.max(np.abs(longs["direct"] - longs["grid"])) < 10 * tol * max(scale, 1.0)
+
+
+@pytest.mark.parametrize("window", ["kb", "gauss"])
+def test_other_windows_match_oracle(B, oracle_mod, window):
+    """The Kaiser-Bessel and Gaussian windows (Remark 3.4): FP64 parts against
+    the oracle to rounding, mixed precision within the FP32 tolerance."""
+    N, L, tol, nnb = CASES["cube10"]
+    q, r = uniform_system(N, L, 21)
+    prm = oracle_mod.select_params(N, *L, tol, n_nb=nnb, window=window)
+    assert prm["window"] == window and prm["m"] >= 0
+    ref = oracle_mod.sog_eval(prm, q, r)
+    out = run_gpu(B, prm, q, r, B.SOG_PREC_FP64, parts=True)
+    assert out["status"] == 0
+    for k, key in enumerate(("near", "mid", "long", "k0")):
+        rp, rg = ref["parts"][key]
+        if np.max(np.abs(rp)) == 0.0:
+            continue
+        assert rel_max(out["pp"][k], rp) < 1e-11, (window, key, rel_max(out["pp"][k], rp))
+        assert rel_max(out["pg"][k], rg) < 1e-10, (window, key, rel_max(out["pg"][k], rg))
+    q32, r32 = q.astype(np.float32), r.astype(np.float32)
+    outm = run_gpu(B, prm, q32, r32, B.SOG_PREC_MIXED)
+    assert outm["status"] == 0
+    relE, rmsF, linf = compare(outm, ref, q)
+    assert relE < 1e-5 and rmsF < 1e-4 and linf < 1e-4, (window, relE, rmsF, linf)

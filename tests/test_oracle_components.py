@@ -41,6 +41,13 @@ def test_mid_window_vs_direct_fourier(oracle_mod, sysA):
     # Gaussian window (Eq. 4.7, closed-form transform) converges as well
     pg, _ = oracle_mod.mid_range(dict(prm, window="gauss", P_win=16, shape=0.455 * math.pi * 16), q, r)
     assert np.max(np.abs(pg - pa)) < 1e-5 * scale
+    # and the Kaiser-Bessel window (closed-form transform), like ES for the same P
+    errs = []
+    for P in (6, 9, 12, 14):
+        pk, gk = oracle_mod.mid_range(dict(prm, window="kb", P_win=P, shape=2.0 * P), q, r)
+        errs.append(np.max(np.abs(pk - pa)))
+    assert errs[0] > errs[1] > errs[2] and errs[3] < 3e-7 * scale
+    assert np.max(np.abs(gk - ga)) < 3e-6 * scale
 
 
 def test_mid_direct_fourier_vs_real_space(oracle_mod, sysA):
@@ -122,7 +129,7 @@ def test_lagrange_basis_properties(oracle_mod):
     assert np.allclose(dLt @ poly(zc), dpoly(z), atol=1e-10)
 
 
-@pytest.mark.parametrize("kind,P", [("es", 10), ("es", 7), ("gauss", 12)])
+@pytest.mark.parametrize("kind,P", [("es", 10), ("es", 7), ("gauss", 12), ("kb", 10), ("kb", 7)])
 def test_window_transform_vs_riemann_sum(oracle_mod, kind, P):
     """Poisson summation: h sum_g W(g h) e^{-i k g h} = sum_n hatW(k + 2 pi n/h);
     with h = H/4000 the aliases are negligible, so the sum is hatW(k)."""

@@ -1,4 +1,4 @@
-"""Pins of the parameter selection (Sec. 4.4) in the oracle."""
+"""Pins of the parameter selection (Sec. 4.3) in the oracle."""
 import math
 
 import pytest
