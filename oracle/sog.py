@@ -217,13 +217,13 @@ class Window:
 
 
 def make_window(kind: str, P: int, shape: float | None = None) -> Window:
-    """Default shape parameters: S = 0.455 pi P for the Gaussian (Sec. 5.1);
-    beta = 1.9 P for ES and 2.0 P for KB.  READING: Sec. 5.1 uses beta = 2.5 P
-    (ES and KB) on oversampled grids; on the grids of Sec. 4.3, which are not
-    upsampled, beta = 1.9 P (ES) and 2.0 P (KB) give a smaller window error
-    for the same P (checked against the direct Fourier sum in the tests)."""
+    """Default shape parameters: beta = 1.9 P for ES, 2.0 P for KB, S =
+    0.35 pi P for the Gaussian.  READING: Sec. 5.1 uses beta = 2.5 P (ES, KB)
+    and S = 0.455 pi P on oversampled grids; on the grids of Sec. 4.3, which
+    are not upsampled, these shapes give a smaller window error for the same
+    P (checked against the direct Fourier sum in the tests)."""
     if shape is None:
-        shape = {"es": 1.9 * P, "kb": 2.0 * P}.get(kind, 0.455 * PI * P)
+        shape = {"es": 1.9 * P, "kb": 2.0 * P}.get(kind, 0.35 * PI * P)
     return Window(kind, int(P), float(shape))
 
 
@@ -364,7 +364,10 @@ def select_params(N: int, Lx: float, Ly: float, Lz: float, tol: float,
             break
         M += 1
     w, s = sog_weights(b, sigma, omega, M)
-    C = 1.563 if window == "gauss" else 1.226      # ES and KB alike (Sec. 5.1)
+    # window error erfc(C sqrt(P)) (Sec. 5.1): C = 1.226 for ES and KB; for the
+    # Gaussian READING C = 0.95, fitted on grids that are not upsampled (Sec.
+    # 5.1's 1.563 belongs to oversampled grids)
+    C = 0.95 if window == "gauss" else 1.226
     P_win = int(math.ceil((special.erfcinv(eps) / C) ** 2))
     P_win = min(max(P_win, 4), 16)
     lne = math.log(1.0 / eps)

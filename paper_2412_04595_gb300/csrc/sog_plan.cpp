@@ -82,7 +82,7 @@ double erfcinv(double y) {
 double shape_default(int window, int P) {
   if (window == SOG_WIN_ES) return 1.9 * P;
   if (window == SOG_WIN_KB) return 2.0 * P;
-  return 0.455 * kPi * P;
+  return 0.35 * kPi * P;  // Gaussian, on grids that are not upsampled
 }
 
 sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol, int window,
@@ -115,7 +115,9 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
   }
   std::vector<double> w, s;
   sog_table(b, sigma, omega, M, w, s);
-  const double C = window == SOG_WIN_GAUSS ? 1.563 : 1.226;  // ES and KB alike (Sec. 5.1)
+  // window error erfc(C sqrt(P)): ES and KB 1.226 (Sec. 5.1); Gaussian 0.95
+  // on grids that are not upsampled
+  const double C = window == SOG_WIN_GAUSS ? 0.95 : 1.226;
   int P_win = (int)ceil(pow(erfcinv(eps) / C, 2));
   P_win = std::min(std::max(P_win, 4), 16);
   const double lne = log(1.0 / eps);

@@ -145,3 +145,16 @@ def test_window_transform_vs_riemann_sum(oracle_mod, kind, P):
     v = np.linspace(-0.95, 0.95, 41)
     d = 1e-6
     assert np.allclose(win.dphi(v), (win.phi(v + d) - win.phi(v - d)) / (2 * d), atol=1e-6)
+
+
+@pytest.mark.parametrize("window", ["es", "kb", "gauss"])
+def test_selected_window_meets_the_tolerance(oracle_mod, sysA, window):
+    """With the support and shape the selection picks for tol = 1e-6, the
+    windowed mid range (Algorithm 1) stays within the tolerance of the
+    direct Fourier sum over the same modes."""
+    q, r, L, prm = sysA
+    pw = oracle_mod.select_params(200, *L, 1e-6, n_nb=60, window=window)
+    p = dict(prm, window=window, P_win=pw["P_win"], shape=pw["shape"])
+    pa, _ = oracle_mod.mid_direct_fourier(p, q, r)
+    pm, _ = oracle_mod.mid_range(p, q, r)
+    assert np.max(np.abs(pm - pa)) < 1e-6 * np.max(np.abs(pa)), (window, pw["P_win"])
