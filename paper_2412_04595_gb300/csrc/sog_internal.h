@@ -7,6 +7,8 @@
 
 #include <vector>
 
+#include <cmath>
+
 #include "../../include/sog.h"
 
 namespace sogk {
@@ -50,6 +52,25 @@ struct alignas(4 * sizeof(T)) P4 {
 
 // Window of Sec. 3.4 / Remark 3.4 on a support of P grid points,
 // half-width `half` = (P-1)/2 grid units, shape beta (ES) or S (Gaussian).
+// Kaiser-Bessel window I0(beta sqrt(1 - v^2)) / I0(beta) as a power series
+// in u = 1 - v^2 (the series of I0): c[k] = (beta^2/4)^k / (k!)^2 / I0(beta),
+// rounded to T, up to cap terms; returns the number of terms.  The kernels
+// evaluate this series and the plan transforms this same series, so that a
+// plan deconvolves exactly the window it applies (coefficients included).
+template <typename T>
+inline int kb_series(double beta, T* c, int cap) {
+  const double x = 0.25 * beta * beta, norm = 1.0 / std::cyl_bessel_i(0.0, beta);
+  double t = norm;
+  int n = 0;
+  for (int k = 0; k < cap; ++k) {
+    c[k] = (T)t;
+    n = k + 1;
+    if (k * k > x && t < 1e-20) break;  // past the peak term (k^2 ~ x) and negligible
+    t *= x / ((k + 1.0) * (k + 1.0));
+  }
+  return n;
+}
+
 struct WinPar {
   int P;
   int kind;          // SOG_WIN_ES, SOG_WIN_GAUSS or SOG_WIN_KB

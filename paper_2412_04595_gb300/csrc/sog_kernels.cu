@@ -84,11 +84,16 @@ __device__ __forceinline__ int ff_floor_clamp(FF a, int n) {
 // (a.h + a.l) - k m rounded once (k m exact: both small integers)
 __device__ __forceinline__ float ff_sub_int(FF a, int k, int m) { return (a.h - (float)(k * m)) + a.l; }
 
+// KB: I0(beta sqrt(1 - v^2)) / I0(beta) = sum_k kbc[k] u^k, u = 1 - v^2, from
+// the power series of I0 (kbc[k] = (beta^2/4)^k / (k!)^2 / I0(beta); all
+// terms positive, so Horner in u in [0, 1] is accurate in FP32 too).
+constexpr int kKbTerms = 64;
 template <typename T>
 struct WinT {
   int P, kind;
   T half, inv_half, shape;
-  T norm;  // KB: 1/I0(shape) of the rounded shape
+  int kbn;           // KB: number of series terms
+  T kbc[kKbTerms];   // KB: series coefficients for the rounded shape
 };
 
 template <typename T>
@@ -99,14 +104,12 @@ __host__ WinT<T> wint(const WinPar& w) {
   o.half = (T)w.half;
   o.inv_half = (T)(1.0 / w.half);
   o.shape = (T)w.shape;
-  o.norm = w.kind == SOG_WIN_KB ? (T)(1.0 / std::cyl_bessel_i(0.0, (double)o.shape)) : T(0);
+  o.kbn = 0;
+  for (int k = 0; k < kKbTerms; ++k) o.kbc[k] = T(0);
+  if (w.kind == SOG_WIN_KB) o.kbn = kb_series<T>((double)o.shape, o.kbc, kKbTerms);
   return o;
 }
 
-__device__ __forceinline__ float dbessel_i0(float x) { return cyl_bessel_i0f(x); }
-__device__ __forceinline__ double dbessel_i0(double x) { return cyl_bessel_i0(x); }
-__device__ __forceinline__ float dbessel_i1(float x) { return cyl_bessel_i1f(x); }
-__device__ __forceinline__ double dbessel_i1(double x) { return cyl_bessel_i1(x); }
 __device__ __forceinline__ float dexp(float x) { return expf(x); }
 __device__ __forceinline__ double dexp(double x) { return exp(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
@@ -133,11 +136,15 @@ __device__ __forceinline__ void win_eval(const WinT<T>& w, T v, T& val, T& dval)
     val = dexp(-w.shape * (v * v / (one + a)));
     if (a2 > T(0)) dval = -val * w.shape * v * drsqrt(a2);
   } else if (w.kind == SOG_WIN_KB) {
-    // I0(beta a) / I0(beta), a = sqrt(1 - v^2); d/dv = I1(beta a) beta (-v / a) / I0(beta)
-    const T a2 = (one - v) * (one + v);
-    const T a = dsqrt(a2);
-    val = dbessel_i0(w.shape * a) * w.norm;
-    if (a2 > T(0)) dval = -dbessel_i1(w.shape * a) * w.norm * w.shape * v / a;
+    // series in u = 1 - v^2 and its u-derivative by Horner; d/dv = -2 v d/du
+    const T u = (one - v) * (one + v);
+    T p = w.kbc[w.kbn - 1], dp = T(0);
+    for (int k = w.kbn - 2; k >= 0; --k) {
+      dp = dp * u + p;
+      p = p * u + w.kbc[k];
+    }
+    val = p;
+    dval = T(-2) * v * dp;
   } else {
     val = dexp(-w.shape * v * v);
     dval = T(-2) * w.shape * v * val;
@@ -163,7 +170,12 @@ __device__ __forceinline__ T win_val(const WinT<T>& w, T v) {
     const T a2 = (one - v) * (one + v);
     return dexp(-w.shape * (v * v / (one + dsqrt(a2))));
   }
-  if (w.kind == SOG_WIN_KB) return dbessel_i0(w.shape * dsqrt((one - v) * (one + v))) * w.norm;
+  if (w.kind == SOG_WIN_KB) {
+    const T u = (one - v) * (one + v);
+    T p = w.kbc[w.kbn - 1];
+    for (int k = w.kbn - 2; k >= 0; --k) p = p * u + w.kbc[k];
+    return p;
+  }
   return dexp(-w.shape * v * v);
 }
 

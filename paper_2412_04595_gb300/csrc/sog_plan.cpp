@@ -342,27 +342,42 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wt) {
 
 // hat W(k) of the window W(x) = phi(x/H): Gaussian closed form (Eq. 4.7);
 // ES by Gauss-Legendre quadrature of
-//   H int_{-pi/2}^{pi/2} exp(beta(cos t - 1)) cos(k H sin t) cos t dt.
+//   H int_{-pi/2}^{pi/2} exp(beta(cos t - 1)) cos(k H sin t) cos t dt;
+// KB by Gauss-Legendre quadrature of the series the kernels evaluate.
 struct WinFT {
   int kind;
-  double shape, H, norm;  // norm: the KB normalisation 1/I0(beta) the kernels apply
-  std::vector<double> gx, gw;
-  WinFT(int kind_, double shape_, double H_, double norm_ = 0.0)
-      : kind(kind_), shape(shape_), H(H_), norm(norm_) {
-    if (kind == SOG_WIN_KB && norm == 0.0) norm = 1.0 / std::cyl_bessel_i(0.0, shape);
+  double shape, H;
+  std::vector<double> gx, gw, kbw;  // KB: node weight x the series the kernels evaluate
+  WinFT(int kind_, double shape_, double H_, int prec) : kind(kind_), shape(shape_), H(H_) {
+    if (kind == SOG_WIN_KB) {
+      gauss_legendre(256, gx, gw);
+      std::vector<double> kbc;
+      if (prec == SOG_PREC_MIXED) {
+        float c[64];
+        kbc.assign(c, c + sogk::kb_series<float>(shape, c, 64));
+      } else {
+        double c[64];
+        kbc.assign(c, c + sogk::kb_series<double>(shape, c, 64));
+      }
+      kbw.resize(gx.size());
+      for (size_t i = 0; i < gx.size(); ++i) {
+        const double u = (1.0 - gx[i]) * (1.0 + gx[i]);
+        double p = 0.0;
+        for (size_t j = kbc.size(); j-- > 0;) p = p * u + kbc[j];
+        kbw[i] = gw[i] * p;
+      }
+    }
     if (kind == SOG_WIN_ES) gauss_legendre(256, gx, gw);
   }
   double operator()(double k) const {
     if (kind == SOG_WIN_GAUSS) return sqrt(kPi / shape) * H * exp(-k * k * H * H / (4.0 * shape));
     if (kind == SOG_WIN_KB) {
-      // H / I0(b) int_{-1}^{1} I0(b sqrt(1 - v^2)) cos(w v) dv, w = k H:
-      // 2 sinh(sqrt(b^2 - w^2)) / sqrt(b^2 - w^2), or 2 sin(sqrt(w^2 - b^2)) / sqrt(w^2 - b^2)
-      const double b = shape, wv = fabs(k) * H, d = b * b - wv * wv;
-      double f;
-      if (d > 0.0) f = 2.0 * sinh(sqrt(d)) / sqrt(d);
-      else if (d < 0.0) f = 2.0 * sin(sqrt(-d)) / sqrt(-d);
-      else f = 2.0;
-      return H * f * norm;
+      // H int_{-1}^{1} sum_j kbc[j] (1 - v^2)^j cos(k H v) dv by Gauss-Legendre
+      // (the series with the kernels' rounded coefficients; the closed form
+      // 2 sinh(sqrt(b^2 - w^2)) / sqrt(b^2 - w^2) / I0(b) holds for exact ones)
+      double acc = 0.0;
+      for (size_t i = 0; i < gx.size(); ++i) acc += kbw[i] * cos(k * H * gx[i]);
+      return H * acc;
     }
     double acc = 0.0;
     for (size_t i = 0; i < gx.size(); ++i) {
@@ -383,12 +398,7 @@ double eff_shape(double shape, int prec) {
 double eff_half(double half, int prec) {
   return prec == SOG_PREC_MIXED ? 1.0 / (double)(float)(1.0 / half) : half;
 }
-// KB normalisation 1/I0(beta) of the (rounded) shape, rounded as the kernels hold it
-double eff_norm(int kind, double shape, int prec) {
-  if (kind != SOG_WIN_KB) return 0.0;
-  const double n = 1.0 / std::cyl_bessel_i(0.0, shape);
-  return prec == SOG_PREC_MIXED ? (double)(float)n : n;
-}
+
 
 // Near kernel table: g(r) = 1 - r F_M(r) on [0, rc], K intervals, degree D
 // monomials in u = 2 (r - r_k)/(rc/K) - 1 (fitted at Chebyshev points).
@@ -664,9 +674,9 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   if (p->has_mid) {
     const int C = Ix / 2 + 1;
     const double shp = eff_shape(prm.shape, prec), hw = eff_half(p->wm.half, prec);
-    WinFT fx(prm.window, shp, hw * p->h[0], eff_norm(prm.window, shp, prec));
-    WinFT fy(prm.window, shp, hw * p->h[1], eff_norm(prm.window, shp, prec));
-    WinFT fz(prm.window, shp, hw * p->h[2], eff_norm(prm.window, shp, prec));
+    WinFT fx(prm.window, shp, hw * p->h[0], prec);
+    WinFT fy(prm.window, shp, hw * p->h[1], prec);
+    WinFT fz(prm.window, shp, hw * p->h[2], prec);
     std::vector<double> kx(C), ky(Iy), kz(Iz), Wx(C), Wy(Iy), Wz(Iz);
     for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
     for (int f = 0; f < Iy; ++f) { ky[f] = 2.0 * kPi * std::min(f, Iy - f) / L[1]; Wy[f] = fy(ky[f]); }
@@ -759,8 +769,8 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     }
     if (!p->long_direct) {
     const double shp = eff_shape(prm.shape_long, prec), hw = eff_half(p->wl.half, prec);
-    WinFT fx(prm.window, shp, hw * p->hl[0], eff_norm(prm.window, shp, prec));
-    WinFT fy(prm.window, shp, hw * p->hl[1], eff_norm(prm.window, shp, prec));
+    WinFT fx(prm.window, shp, hw * p->hl[0], prec);
+    WinFT fy(prm.window, shp, hw * p->hl[1], prec);
     std::vector<double> Wx(C), Wy(Ily), kx(C), ky(Ily);
     for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
     for (int f = 0; f < Ily; ++f) { ky[f] = 2.0 * kPi * std::min(f, Ily - f) / L[1]; Wy[f] = fy(ky[f]); }
