@@ -310,3 +310,26 @@ def test_other_windows_match_oracle(B, oracle_mod, window):
     assert outm["status"] == 0
     relE, rmsF, linf = compare(outm, ref, q)
     assert relE < 1e-5 and rmsF < 1e-4 and linf < 1e-4, (window, relE, rmsF, linf)
+
+
+def test_forces_are_the_gradient_of_the_energy(B, oracle_mod):
+    """The forces are the exact gradient of the energy the plan computes
+    (spread and gather share the window, the near table is C1 at r_c): central
+    differences of the FP64 energy in a few coordinates match -F."""
+    N, L, tol, nnb = CASES["cube10"]
+    q, r = uniform_system(N, L, 21)
+    prm = oracle_mod.select_params(N, *L, tol, n_nb=nnb)
+    base = run_gpu(B, prm, q, r, B.SOG_PREC_FP64)
+    assert base["status"] == 0
+    Fmax = np.max(np.abs(base["F"]))
+    h = 1e-5
+    rng = np.random.default_rng(3)
+    for i in rng.choice(N, 4, replace=False):
+        for d in range(3):
+            rp, rm = r.copy(), r.copy()
+            rp[i, d] += h
+            rm[i, d] -= h
+            Ep = run_gpu(B, prm, q, rp, B.SOG_PREC_FP64)["E"]
+            Em = run_gpu(B, prm, q, rm, B.SOG_PREC_FP64)["E"]
+            fd = -(Ep - Em) / (2 * h)
+            assert abs(fd - base["F"][i, d]) < 1e-6 * Fmax, (i, d, fd, base["F"][i, d])
