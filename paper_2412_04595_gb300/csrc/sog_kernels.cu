@@ -122,7 +122,10 @@ __device__ __forceinline__ float drsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double drsqrt(double x) { return rsqrt(x); }
 
 // Window phi(v) (v = offset / half-width) and d phi / dv; zero outside |v| <= 1.
-template <typename T>
+// KB: whether the Kaiser-Bessel branch is compiled in (only the kernels for a
+// run-time support take it, so that the fixed-support kernels of the ES and
+// Gaussian windows keep their code).
+template <typename T, bool KB>
 __device__ __forceinline__ void win_eval(const WinT<T>& w, T v, T& val, T& dval) {
   const T one = T(1);
   val = T(0);
@@ -135,7 +138,7 @@ __device__ __forceinline__ void win_eval(const WinT<T>& w, T v, T& val, T& dval)
     const T a = dsqrt(a2);
     val = dexp(-w.shape * (v * v / (one + a)));
     if (a2 > T(0)) dval = -val * w.shape * v * drsqrt(a2);
-  } else if (w.kind == SOG_WIN_KB) {
+  } else if (KB && w.kind == SOG_WIN_KB) {
     // series in u = 1 - v^2 and its u-derivative by Horner; d/dv = -2 v d/du
     const T u = (one - v) * (one + v);
     T p = w.kbc[w.kbn - 1], dp = T(0);
@@ -162,7 +165,7 @@ __device__ __forceinline__ Cx<T> cxmul(Cx<T> a, Cx<T> b) {
 }
 
 // Window value only (same arithmetic as win_eval's value).
-template <typename T>
+template <typename T, bool KB>
 __device__ __forceinline__ T win_val(const WinT<T>& w, T v) {
   const T one = T(1);
   if (!(v >= -one && v <= one)) return T(0);
@@ -170,7 +173,7 @@ __device__ __forceinline__ T win_val(const WinT<T>& w, T v) {
     const T a2 = (one - v) * (one + v);
     return dexp(-w.shape * (v * v / (one + dsqrt(a2))));
   }
-  if (w.kind == SOG_WIN_KB) {
+  if (KB && w.kind == SOG_WIN_KB) {
     const T u = (one - v) * (one + v);
     T p = w.kbc[w.kbn - 1];
     for (int k = w.kbn - 2; k >= 0; --k) p = p * u + w.kbc[k];
@@ -1026,7 +1029,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
       const P4<T> a = rec[p0 + j];
       const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
       const int g0 = (int)dceil(c - w.half);
-      const T v = win_val(w, ((T)(g0 + k) - c) * w.inv_half);
+      const T v = win_val<T, PW == 0>(w, ((T)(g0 + k) - c) * w.inv_half);
       wgt[(j * 3 + ax) * kMaxWin + k] = ax == 0 ? v * a.q : v;
       if (r == 0) {
         const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
@@ -1198,13 +1201,13 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
       if (ax0 < 3) {
         const T c = ax0 == 0 ? a.x : (ax0 == 1 ? a.y : a.z);
         const int g0 = ax0 == 0 ? gx0 : (ax0 == 1 ? gy0 : gz0);
-        win_eval(w, ((T)(g0 + k0) - c) * w.inv_half, v, dv);
+        win_eval<T, PW == 0>(w, ((T)(g0 + k0) - c) * w.inv_half, v, dv);
         wsm[ax0 * kMaxWin + k0] = Cx<T>{v, -dv * w.inv_half};
       }
       if (3 * P > 32 && ax1 < 3) {
         const T c = ax1 == 0 ? a.x : (ax1 == 1 ? a.y : a.z);
         const int g0 = ax1 == 0 ? gx0 : (ax1 == 1 ? gy0 : gz0);
-        win_eval(w, ((T)(g0 + k1) - c) * w.inv_half, v, dv);
+        win_eval<T, PW == 0>(w, ((T)(g0 + k1) - c) * w.inv_half, v, dv);
         wsm[ax1 * kMaxWin + k1] = Cx<T>{v, -dv * w.inv_half};
       }
     }
@@ -1304,9 +1307,9 @@ __global__ void __launch_bounds__(256) k_long_spread(TileGeom g, WinT<T> w, int 
     const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half);
     if (lane < Pw) {
       T v, dv;
-      win_eval(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
+      win_eval<T, PW == 0>(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
       wsx[lane] = v;
-      win_eval(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
+      win_eval<T, PW == 0>(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
       wsy[lane] = v * a.q;
     }
     if (lane == 0) cheb_all(a.z, P, tn);
@@ -1375,7 +1378,7 @@ __global__ void __launch_bounds__(256) k_long_spread_small(int I0, int I1, WinT<
           T d = (T)k - (ax ? a.y : a.x);
           d -= (T)Id * drint(d * (ax ? iI1 : iI0));
           T v, dv;
-          win_eval(w, d * w.inv_half, v, dv);
+          win_eval<T, true>(w, d * w.inv_half, v, dv);
           if (ax) wy[j][k] = v;
           else wx[j][k] = v * a.q;
         }
@@ -1509,7 +1512,7 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
       const T c = ax == 0 ? a.x : a.y;
       const int g0 = (int)dceil(c - w.half);
       T v, dv;
-      win_eval(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
+      win_eval<T, PW == 0>(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
       T* wj = wgt + jj * 4 * Pw + 2 * ax * Pw;
       wj[k] = v;
       wj[Pw + k] = -dv * w.inv_half;
@@ -2010,6 +2013,10 @@ __global__ void k_energy(const double* __restrict__ part, int nblk, double* __re
 
 // Window supports with dedicated (unrolled) kernels; others use the generic
 // instantiation (PW = 0).
+// Support of the kernel instantiation a window runs on: the KB window runs on
+// the run-time-support kernels (0), the others on their fixed support.
+static int pw_dispatch(const WinPar& w) { return w.kind == SOG_WIN_KB ? 0 : w.P; }
+
 #define SOG_DISPATCH_PW(P_, KER, GRID, SMEM, STREAM, ...)                 \
   do {                                                                     \
     switch (P_) {                                                          \
@@ -2208,7 +2215,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     const WinT<T> w = wint<T>(p->wm);
     const size_t sm = mid_smem(p, sizeof(T), false);
     const dim3 mgrid(p->n_tiles_mid, p->gm.chunks);
-    SOG_DISPATCH_PW(p->wm.P, k_mid_spread, mgrid, sm, s, p->gm, w, rm, p->d_cnt + off.y, grid);
+    SOG_DISPATCH_PW(pw_dispatch(p->wm), k_mid_spread, mgrid, sm, s, p->gm, w, rm, p->d_cnt + off.y, grid);
     LAUNCH_CHECK();
     mark_end(p, 2, s);
     mark_begin(p, 3, s);
@@ -2219,7 +2226,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     mark_begin(p, 4, s);
     const size_t sm2 = mid_smem(p, sizeof(T), true);
     const double3 invh = make_double3(1.0 / p->h[0], 1.0 / p->h[1], 1.0 / p->h[2]);
-    SOG_DISPATCH_PW(p->wm.P, k_mid_gather, mgrid, sm2, s, p->gm, w, rm, p->d_cnt + off.y,
+    SOG_DISPATCH_PW(pw_dispatch(p->wm), k_mid_gather, mgrid, sm2, s, p->gm, w, rm, p->d_cnt + off.y,
                     p->d_perm + N, grid, invh, pp + N, pg + 3 * (size_t)N);
     LAUNCH_CHECK();
     mark_end(p, 4, s);
@@ -2312,7 +2319,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
       SOG_CK(cudaMemsetAsync(A, 0, pbytes, sl));
       const size_t sm = long_smem(p, sizeof(T), false);
       const dim3 lgrid(p->n_tiles_long, p->gl.chunks);
-      SOG_DISPATCH_PW(p->wl.P, k_long_spread, lgrid, sm, sl, p->gl, w, P, rl, p->d_cnt + off.z, A);
+      SOG_DISPATCH_PW(pw_dispatch(p->wl), k_long_spread, lgrid, sm, sl, p->gl, w, P, rl, p->d_cnt + off.z, A);
       LAUNCH_CHECK();
     }
     mark_end(p, 5, sl);
@@ -2332,7 +2339,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     const size_t sm2 = long_smem(p, sizeof(T), true);
     const double3 sc = make_double3(1.0 / p->hl[0], 1.0 / p->hl[1], 2.0 / m.L[2]);
     const dim3 lgrid2(p->n_tiles_long, p->gl.chunks);
-    SOG_DISPATCH_PW(p->wl.P, k_long_gather, lgrid2, sm2, sl, p->gl, w, P, rl, p->d_cnt + off.z,
+    SOG_DISPATCH_PW(pw_dispatch(p->wl), k_long_gather, lgrid2, sm2, sl, p->gl, w, P, rl, p->d_cnt + off.z,
                     p->d_perm + 2 * (size_t)N, B, sc, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     LAUNCH_CHECK();
     mark_end(p, 7, sl);
