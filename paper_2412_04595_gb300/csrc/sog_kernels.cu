@@ -186,7 +186,6 @@ __device__ __forceinline__ T win_val(const WinT<T>& w, T v) {
 // 1. binning
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 __device__ __forceinline__ int floor_clamp(double t, int n) {
   if (!(t >= 0.0)) return 0;  // also NaN
@@ -594,21 +593,6 @@ template <typename T>
 struct alignas(2 * sizeof(T)) S2 {
   T x, y;
 };
-
-// Position of the k-th (from 0) set bit of m; k < popc(m).
-__device__ __forceinline__ int nth_bit(unsigned m, int k) {
-  int pos = 0;
-#pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
-    const int c = __popc(m & ((1u << w) - 1u));
-    if (k >= c) {
-      k -= c;
-      m >>= w;
-      pos += w;
-    }
-  }
-  return pos;
-}
 
 // Near kernel g(r)/r and its radial derivative from the piecewise
 // polynomial table (degree kNearD in u on each of the K intervals).
@@ -1260,21 +1244,6 @@ __device__ __forceinline__ void cheb_all(T x, int P, T* t) {
   t[0] = T(1);
   if (P > 1) t[1] = x;
   for (int n = 2; n < P; ++n) t[n] = T(2) * x * t[n - 1] - t[n - 2];
-}
-
-// T_n(x) and T_n'(x), n < P.
-template <typename T>
-__device__ __forceinline__ void cheb_all_d(T x, int P, T* t, T* dt) {
-  t[0] = T(1);
-  dt[0] = T(0);
-  if (P > 1) {
-    t[1] = x;
-    dt[1] = T(1);
-  }
-  for (int n = 2; n < P; ++n) {
-    t[n] = T(2) * x * t[n - 1] - t[n - 2];
-    dt[n] = T(2) * t[n - 1] + T(2) * x * dt[n - 1] - dt[n - 2];
-  }
 }
 
 // Spread q_j T_n(x_j) W2(rho_g - rho_j) onto the P proxy planes (layout
