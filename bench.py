@@ -226,13 +226,10 @@ def run_ours(args, wl, rank, world):
     torch.cuda.synchronize()
     launches = plan.launches() * args.steps
     clk = clocks.stop()
-    total_ms = sum(times)
+    total_ms = max_over_ranks(sum(times), dev)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        total_ms = float(t.item())
     torch.cuda.synchronize()
     value = world * N * args.steps / (total_ms * 1e-3)
     stage_ms = {k: sum(v) / len(v) for k, v in stages.items()}
@@ -274,13 +271,28 @@ def oracle_run(prm, q, r):
     return ref, time.perf_counter() - t0, oracle.num_threads()
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Largest value of x over the ranks of the current process group (x
+    itself without one); device: where the reduction tensor lives (CUDA for
+    NCCL, CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def emit(d):
     print(json.dumps(d), flush=True)
 
 
 def run_batched(args, wl, config, rank, world):
-    """Batched workload: all systems in one sog_batch_eval (mixed precision),
-    compared with a loop of per-system FP64 evaluations on the same GPU."""
+    """Batched workload: the systems in one sog_batch_eval per GPU (mixed
+    precision), compared with a loop of per-system FP64 evaluations on the
+    same GPU.  With several ranks the fixed set of systems is split between
+    them (balanced shares, no exchange): strong scaling."""
     import numpy as np
     import torch
     import __graft_entry__ as g
@@ -292,7 +304,10 @@ def run_batched(args, wl, config, rank, world):
     # positions rounded to FP32 once, so that both arms see the same inputs
     systems = [(qq, rr.astype(np.float32).astype(np.float64), LL)
                for qq, rr, LL in workloads.batched_slabs(wl["batch"], seed=wl["seed"])]
-    Ntot = sum(s[0].size for s in systems)
+    Ntot = sum(s[0].size for s in systems)          # the whole job, all ranks
+    from paper_2412_04595_gb300.sharding import shard_systems
+    mine = shard_systems([s[0].size for s in systems], world)[rank]
+    systems = [systems[i] for i in mine]
     prec = B.SOG_PREC_FP64 if args.precision == "fp64" else B.SOG_PREC_MIXED
     batch = B.Batch([(s[0].size, s[2]) for s in systems], wl["tol"], precision=prec)
     dt = batch.dtype
@@ -328,13 +343,11 @@ def run_batched(args, wl, config, rank, world):
         e1.synchronize()
         t += e0.elapsed_time(e1)
     clk = clocks.stop()
+    t = max_over_ranks(t, dev)
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
         dist.barrier()
-    value = world * Ntot * steps / (t * 1e-3)
+    value = Ntot * steps / (t * 1e-3)
     launches = batch.launches() * steps
     # the plain form: one FP64 plan per system, evaluated one after another
     plans = [B.Plan(s[0].size, s[2], wl["tol"], precision=B.SOG_PREC_FP64) for s in systems]
@@ -363,6 +376,7 @@ def run_batched(args, wl, config, rank, world):
         e1.record(stream)
         e1.synchronize()
         t64 += e0.elapsed_time(e1)
+    t64 = max_over_ranks(t64, dev)
     value64 = Ntot * steps64 / (t64 * 1e-3)
     relE = (E.double() - E64).abs() / E64.abs()
     # energy error against the energy's own scale (1/2) sum |q_i phi_i|: the
@@ -375,10 +389,11 @@ def run_batched(args, wl, config, rank, world):
         p.close()
     if rank != 0:
         return
-    config = dict(config, N=Ntot, L=None, systems=len(systems))
+    config = dict(config, N=Ntot, L=None, systems=wl["batch"],
+                  parallelism="systems split over %d GPU(s), no exchange" % world)
     emit({"metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": world, "steps": steps,
           "warmup": args.warmup, "ms_per_step": t / steps, "higher_is_better": True,
-          "scaling": "weak", "vs_baseline": None,
+          "scaling": "strong", "vs_baseline": None,
           "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
           "config": config, "gpu_launches": launches, "clocks": clk,
           "plain_fp64_loop": {"value": value64, "unit": "particles/s",
@@ -460,8 +475,13 @@ def main():
         return
 
     if "batch" in wl:
-        if rank == 0 or world > 1:
-            run_batched(args, wl, config, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl")
+        run_batched(args, wl, config, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
 
     if world > 1:
