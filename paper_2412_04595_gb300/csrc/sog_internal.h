@@ -225,7 +225,7 @@ void release_graphs(sog_plan* p);
 cudaError_t enqueue_eval(sog_plan* p, const void* q, const void* r, void* phi, double* E, void* F,
                          cudaStream_t s);
 
-// Evaluation driver (sog_kernels.cu).
+// Host side of one evaluation (sog_kernels.cu).
 sog_status eval_device(sog_plan* p, const void* q, const void* r, void* phi, double* E, void* F,
                        double* phi_parts, double* grad_parts, cudaStream_t s);
 

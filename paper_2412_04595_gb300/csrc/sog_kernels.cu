@@ -1,4 +1,4 @@
-// Device kernels and the evaluation driver of the spectral SOG method.
+// Device kernels of the spectral SOG method and the host code that enqueues them.
 //
 // One evaluation (sog_eval) runs, on one stream:
 //   1. binning: every particle gets a near-field cell (cells >= r_c, Sec. 2.2
@@ -1977,7 +1977,7 @@ __global__ void k_energy(const double* __restrict__ part, int nblk, double* __re
 }
 
 // ---------------------------------------------------------------------------
-// driver
+// host side of one evaluation: the launch sequence
 // ---------------------------------------------------------------------------
 
 // Window supports with dedicated (unrolled) kernels; others use the generic

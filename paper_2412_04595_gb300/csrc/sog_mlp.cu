@@ -2,7 +2,7 @@
 // (hence r_c and the rest of the split) from features of a system, with its
 // own forward, backward and Adam kernels (sog_mlp_* and sog_features in
 // sog.h).  The paper selects parameters analytically (Sec. 4.3); that
-// selection stays the fallback and the judge of feasibility.
+// selection stays the fallback and decides feasibility.
 //
 // Network: x (n_in) -> tanh(W1 x + b1) (H) -> tanh(W2 h1 + b2) (H) ->
 // y = w3 . h2 + b3.  Parameters in one FP32 array:
