@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -63,3 +64,26 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(_build, "LIB", os.path.join(ROOT, "no_such_dir", "libsog.so"))
     with pytest.raises(RuntimeError, match="not built"):
         binding.load()
+
+
+@pytest.mark.parametrize("N,L,tol", [
+    (1000, (10.0, 10.0, 10.0), 1e-6),
+    (100000, (100.0, 100.0, 100.0), 1e-4),
+    (1000000, (1000.0, 1000.0, 10.0), 1e-6),
+    (1000000, (50.0, 50.0, 2000.0), 1e-6),
+    (4000000, (400.0, 400.0, 100.0), 1e-5),
+    (20000, (37.0, 41.0, 9.0), 1e-6),
+    (5000, (12.0, 12.0, 80.0), 1e-5),
+])
+def test_library_selection_equals_the_oracle_on_every_workload(oracle_mod, N, L, tol):
+    """The host selection of the library and the oracle's selection agree
+    on the workloads of the benchmark and on off-cube boxes: same integers,
+    same reals to rounding, same choice between Algorithms 2 and 3."""
+    from paper_2412_04595_gb300 import _build, binding
+    _build.build()
+    a = binding.sog_select_params(N, *L, tol)
+    b = oracle_mod.select_params(N, *L, tol)
+    for k in ("M", "m", "I", "P_win", "I_long", "P_long", "P_cheb", "long_direct"):
+        assert tuple(np.atleast_1d(a[k]).astype(int)) == tuple(np.atleast_1d(b[k]).astype(int)), k
+    for k in ("rc", "sigma", "hz", "shape", "shape_long"):
+        assert abs(a[k] - b[k]) <= 1e-12 * max(abs(b[k]), 1e-300), k
