@@ -283,13 +283,18 @@ sog_status sog_features(int64_t N, double Lx, double Ly, double Lz, double tol, 
  *   N           number of charges, 1 <= N <= 715827882 (else SOG_ERR_ARG)
  *   precision   SOG_PREC_FP64 or SOG_PREC_MIXED: element type of q, phi, F
  *   prm         host; b, sigma, omega, M give the self-term coefficient
- *               sum_l w_l (Eq. 2.22, 2.25)
- *   q           [N]          device, plan type
+ *               sum_l w_l (Eq. 2.22, 2.25); b > 1, sigma > 0, omega > 0
+ *               finite and 0 <= M <= 4000, else SOG_ERR_ARG
+ *   q           [N]          device, plan type; a non-finite charge counts
+ *                            as 0 (no status is latched here: the plan whose
+ *                            sog_eval_components produced the parts reports
+ *                            it through sog_plan_check)
  *   phi_parts   [4 x N]      device, double, as from sog_eval_components
  *   grad_parts  [4 x N x 3]  device, double; may be NULL when F is NULL
  *   phi, E, F   outputs as in sog_eval; any may be NULL
  * Enqueued on `stream`; returns without waiting.  The energy's partial sums
- * go to a fixed device array of 304 doubles inside the library (any N uses
+ * go to a fixed device array of 1024 doubles (8 KB) inside the library, one
+ * per block of the assembly (two blocks per SM, at most 1024; any N uses
  * it; nothing in it has to start at zero).  Its address is looked up on the
  * first call on each device, which should come before any stream capture is
  * begun on that device.  Calls that may run at the same time on one device

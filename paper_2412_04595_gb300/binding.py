@@ -165,25 +165,51 @@ def sog_select_params(N, Lx, Ly, Lz, tol, window=SOG_WIN_ES, n_nb=None) -> dict:
     return out.to_dict()
 
 
+def _require(*specs, cuda=True):
+    """Check tensor arguments before their pointers reach the C ABI.  Each
+    spec is (tensor or None, name, dtype, numel[, at_least]): dtype, element
+    count (exact, or at least ``numel``) and contiguity of every tensor are
+    checked first, then (``cuda``) that all are on a CUDA device.  A tensor
+    of the wrong size would otherwise be read or written out of bounds by the
+    library."""
+    for spec in specs:
+        t, name, dtype, numel = spec[:4]
+        at_least = len(spec) > 4 and spec[4]
+        if t is None:
+            continue
+        if t.dtype != dtype:
+            raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+        n = t.numel()
+        if (n < numel) if at_least else (n != numel):
+            raise ValueError("%s must have %s%d elements, got %d"
+                             % (name, "at least " if at_least else "", numel, n))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    if cuda:
+        for spec in specs:
+            if spec[0] is not None and not spec[0].is_cuda:
+                raise ValueError("%s must be a CUDA tensor" % spec[1])
+
+
 def sog_assemble_noalloc(params, q, phi_parts, grad_parts=None, phi=None, E=None, F=None,
                          stream=None):
     """sog_assemble_noalloc: Phi, U and F from the four parts of
     ``Plan.eval_components`` without a plan or any device allocation.
     ``params`` is a dict or SogParams; q, phi, F are contiguous CUDA tensors of
-    one dtype (float64: FP64, float32: mixed); the parts are float64."""
+    one dtype (float64: FP64, float32: mixed) with N, N and 3N elements; the
+    parts are float64 with 4N and 12N elements; E float64 with at least one."""
     import torch
     prec = {torch.float64: SOG_PREC_FP64, torch.float32: SOG_PREC_MIXED}.get(q.dtype)
     if prec is None:
         raise ValueError("q must be float32 or float64")
-    for t in (q, phi_parts, grad_parts, phi, E, F):
-        if t is not None and (not t.is_cuda or not t.is_contiguous()):
-            raise ValueError("expected contiguous CUDA tensors")
-    for t in (phi, F):
-        if t is not None and t.dtype != q.dtype:
-            raise ValueError("phi and F must have the dtype of q")
-    for t in (phi_parts, grad_parts, E):
-        if t is not None and t.dtype != torch.float64:
-            raise ValueError("parts and E must be float64")
+    N = q.numel()
+    if phi_parts is None:
+        raise ValueError("phi_parts is required")
+    if F is not None and grad_parts is None:
+        raise ValueError("grad_parts is required for F")
+    _require((q, "q", q.dtype, N), (phi_parts, "phi_parts", torch.float64, 4 * N),
+             (grad_parts, "grad_parts", torch.float64, 12 * N), (phi, "phi", q.dtype, N),
+             (F, "F", q.dtype, 3 * N), (E, "E", torch.float64, 1, True))
     prm = params if isinstance(params, SogParams) else SogParams.from_dict(params)
     _check(load().sog_assemble_noalloc(int(q.numel()), prec, ctypes.byref(prm), _ptr(q),
                                        _ptr(phi_parts), _ptr(grad_parts), _ptr(phi), _ptr(E),
@@ -228,35 +254,53 @@ class Plan:
     def device_bytes(self) -> int:
         return int(self._lib.sog_plan_device_bytes(self._h))
 
-    def _check_in(self, *ts):
-        for t in ts:
-            if t is None:
-                continue
-            if not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous():
-                raise ValueError("expected contiguous CUDA %s tensors" % self.dtype)
+    def _io_specs(self, q, r, phi=None, E=None, F=None):
+        import torch
+        if q is None or r is None:
+            raise ValueError("q and r are required")
+        N, dt = self.N, self.dtype
+        return [(q, "q", dt, N), (r, "r", dt, 3 * N), (phi, "phi", dt, N), (F, "F", dt, 3 * N),
+                (E, "E", torch.float64, 1, True)]
+
+    def _check_io(self, q, r, phi=None, E=None, F=None, cuda=True):
+        _require(*self._io_specs(q, r, phi, E, F), cuda=cuda)
 
     def eval(self, q, r, phi=None, E=None, F=None, stream=None):
-        """sog_eval: enqueue the evaluation; outputs are written in place."""
-        self._check_in(q, r, phi, F)
-        if E is not None and (not E.is_cuda or E.dtype.itemsize != 8):
-            raise ValueError("E must be a CUDA float64 tensor")
+        """sog_eval: enqueue the evaluation; outputs are written in place.
+        q, phi: N elements; r, F: 3N (N x 3); E: float64, at least one."""
+        self._check_io(q, r, phi, E, F)
         _check(self._lib.sog_eval(self._h, _ptr(q), _ptr(r), _ptr(phi), _ptr(E), _ptr(F),
                                   _stream_ptr(stream)), "sog_eval")
 
     def eval_components(self, q, r, phi_parts, grad_parts, stream=None):
-        self._check_in(q, r)
+        """sog_eval_components: phi_parts float64 with 4N elements, grad_parts
+        float64 with 12N (either may be None)."""
+        import torch
+        _require(*self._io_specs(q, r), (phi_parts, "phi_parts", torch.float64, 4 * self.N),
+                 (grad_parts, "grad_parts", torch.float64, 12 * self.N))
         _check(self._lib.sog_eval_components(self._h, _ptr(q), _ptr(r), _ptr(phi_parts),
                                              _ptr(grad_parts), _stream_ptr(stream)),
                "sog_eval_components")
 
     def eval_host(self, q, r, phi=None, E=None, F=None):
-        """sog_eval_host on numpy arrays or CPU tensors (pinned for speed)."""
-        def hp(a):
+        """sog_eval_host on CPU tensors (pinned for speed) or numpy arrays of
+        the plan's dtype, with the sizes of ``eval``."""
+        import numpy as np
+        import torch
+
+        def ten(a):
             if a is None:
                 return None
-            if hasattr(a, "data_ptr"):
-                return ctypes.c_void_p(a.data_ptr())
-            return ctypes.c_void_p(a.ctypes.data)
+            return a if hasattr(a, "data_ptr") else torch.from_numpy(np.asarray(a))
+
+        q, r, phi, E, F = map(ten, (q, r, phi, E, F))
+        self._check_io(q, r, phi, E, F, cuda=False)
+        for name, t in (("q", q), ("r", r), ("phi", phi), ("E", E), ("F", F)):
+            if t is not None and t.is_cuda:
+                raise ValueError("%s must be a host tensor or array" % name)
+
+        def hp(a):
+            return None if a is None else ctypes.c_void_p(a.data_ptr())
         return self._lib.sog_eval_host(self._h, hp(q), hp(r), hp(phi), hp(E), hp(F))
 
     STAGES = ("binning", "near", "mid_spread", "mid_fft", "mid_gather", "long_spread",
@@ -317,6 +361,7 @@ class Batch:
             _check(self._lib.sog_plan_get_params(self._lib.sog_batch_plan(h, i), ctypes.byref(out)),
                    "sog_plan_get_params")
             self.params.append(out.to_dict())
+        self.sizes = [int(sy[0]) for sy in systems]
 
     @property
     def dtype(self):
@@ -326,20 +371,26 @@ class Batch:
     def eval(self, q, r, phi=None, E=None, F=None, stream=None):
         """sog_batch_eval: q, r, phi, F are lists of per-system tensors; E one
         float64 CUDA tensor of size nsys (or None)."""
+        import torch
         n = self.size
 
-        def arr(ts):
+        def arr(ts, name, per):
             if ts is None:
                 return None
-            for t in ts:
-                if t is not None and (not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous()):
-                    raise ValueError("expected contiguous CUDA %s tensors" % self.dtype)
+            if len(ts) != n:
+                raise ValueError("%s must hold %d tensors" % (name, n))
+            _require(*[(t, "%s[%d]" % (name, i), self.dtype, per * self.sizes[i])
+                       for i, t in enumerate(ts)])
             return (ctypes.c_void_p * n)(*[t.data_ptr() if t is not None else None for t in ts])
 
-        if E is not None and (not E.is_cuda or E.dtype.itemsize != 8 or E.numel() < n):
-            raise ValueError("E must be a CUDA float64 tensor of size nsys")
-        _check(self._lib.sog_batch_eval(self._h, arr(q), arr(r), arr(phi), _ptr(E), arr(F),
-                                        _stream_ptr(stream)), "sog_batch_eval")
+        if q is None or r is None:
+            raise ValueError("q and r are required")
+        qa, ra, pa, fa = arr(q, "q", 1), arr(r, "r", 3), arr(phi, "phi", 1), arr(F, "F", 3)
+        if any(t is None for t in q) or any(t is None for t in r):
+            raise ValueError("every system needs q and r")
+        _require((E, "E", torch.float64, n, True))
+        _check(self._lib.sog_batch_eval(self._h, qa, ra, pa, _ptr(E), fa, _stream_ptr(stream)),
+               "sog_batch_eval")
 
     def check(self):
         bad = ctypes.c_int32(-1)

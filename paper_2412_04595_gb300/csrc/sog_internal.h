@@ -18,7 +18,7 @@ constexpr int kMaxCheb = 64;
 constexpr int kMaxWin = 16;
 constexpr int kNearD = 8;  // degree of the near-field table polynomials
 constexpr int kMaxHalfModes = 256;  // long range by direct sums: half-plane modes
-constexpr int kModeBlocks = 608;    // CTAs of its moment sums (4 per SM)
+constexpr int kModeBlocksPerSm = 4;  // CTAs of its moment sums per SM
 constexpr int kMaxHalfModeCoefs = 8192;  // half-plane modes x P_cheb (on-chip table)
 
 // Half-plane mode idx of the direct long range: n_x = 0 with n_y = 1..Ky,
@@ -110,8 +110,10 @@ __host__ __device__ inline int gather_plane_stride(int rp, int W1, int P) {
   return rp * W1 + mod32(P * rp - rp * W1);
 }
 
-// Sizes of one evaluation's reduction scratch.
-constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+// Blocks of the grid-stride reductions (binning sums, assembly / energy)
+// and of the k = 0 moments, per SM of the plan's device.
+constexpr int kRedBlocksPerSm = 2;
+constexpr int kK0BlocksPerSm = 1;
 // Largest dynamic shared memory of one CTA on sm_100-class GPUs (227 KB).
 constexpr int kMaxDynSmem = 232448;
 // Captured evaluations kept per plan (keyed by the caller's pointers).
@@ -139,6 +141,10 @@ struct sog_plan {
   int prec;
   int64_t N;
   int device;
+  int n_sm;           // SMs of the device; the block counts below follow it
+  int red_blocks;     // kRedBlocksPerSm x n_sm
+  int mode_blocks;    // kModeBlocksPerSm x n_sm
+  int k0_blocks;      // kK0BlocksPerSm x n_sm
   // derived geometry
   double h[3];        // mid grid spacing
   double Lzs;         // padded box Lz*
@@ -206,6 +212,12 @@ struct sog_plan {
 };
 
 namespace sogk {
+
+// SOG weight w_l of Eq. (2.22) (w_0 scaled by omega, Eq. 2.25), and the
+// weights and bandwidths s_l, l = 0..M, built from it (sog_plan.cpp).
+double sog_weight(double b, double sigma, double omega, int l);
+void sog_table(double b, double sigma, double omega, int M, std::vector<double>& w,
+               std::vector<double>& s);
 
 // Host-side launchers (sog_fft.cu).
 // Each adds the number of kernels it launched to `launches`.

@@ -1821,7 +1821,7 @@ __global__ void __launch_bounds__(kModeThreads) k_lmodes_eval(
 // its few particles (about N / 19,456) in the element type, warps and blocks
 // sum in FP64.  The moments are then combined with the FP64 kernel matrix
 // and the k = 0 potential is evaluated in FP64 (Clenshaw).
-constexpr int kK0Blocks = 152, kK0Threads = 128;
+constexpr int kK0Threads = 128;
 
 template <typename T, int PMAX>
 __global__ void __launch_bounds__(kK0Threads) k_k0_moments(const T* __restrict__ q,
@@ -2139,7 +2139,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   mark_begin(p, 0, s);
   SOG_CK(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * p->cnt_off[3], s));
   P4<T>* tmp = reinterpret_cast<P4<T>*>(p->d_rec_tmp);
-  k_bin_count<T><<<kRedBlocks, 256, 0, s>>>(g, q, r, N, p->d_key, p->d_rank, p->d_cnt, off, tmp,
+  k_bin_count<T><<<p->red_blocks, 256, 0, s>>>(g, q, r, N, p->d_key, p->d_rank, p->d_cnt, off, tmp,
                                            p->d_red, p->d_status);
   LAUNCH_CHECK();
   k_scan3<<<3, 1024, 0, s>>>(p->d_cnt, off, nb);
@@ -2225,15 +2225,15 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     T* lmom = reinterpret_cast<T*>(p->d_lmom);  // per-block moments in the element type
     mark_begin(p, 5, sl);
     if (pmax == 16)
-      k_lmodes_moments<T, 16><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
+      k_lmodes_moments<T, 16><<<p->mode_blocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
     else if (pmax == 32)
-      k_lmodes_moments<T, 32><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
+      k_lmodes_moments<T, 32><<<p->mode_blocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
     else
-      k_lmodes_moments<T, 64><<<kModeBlocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
+      k_lmodes_moments<T, 64><<<p->mode_blocks, kModeThreads, sm1, sl>>>(q, r, N, P, Kx, Ky, nh, nbt, mg, lmom);
     LAUNCH_CHECK();
     mark_end(p, 5, sl);
     mark_begin(p, 6, sl);
-    k_lmodes_coeffs<T><<<nh, kCoefThreads, 0, sl>>>(lmom, kModeBlocks, nh, P,
+    k_lmodes_coeffs<T><<<nh, kCoefThreads, 0, sl>>>(lmom, p->mode_blocks, nh, P,
                                                      reinterpret_cast<const T*>(p->d_kmat),
                                                      reinterpret_cast<T*>(p->d_lcoef));
     LAUNCH_CHECK();
@@ -2252,14 +2252,14 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   if (p->has_long) {
     mark_begin(p, 8, sl);
     const int P = m.P_cheb;
-    double* mpart = p->d_red + 2 * kRedBlocks;
+    double* mpart = p->d_red + 2 * p->red_blocks;
     const ModeGeom<T> mg0 = mode_geom<T>(m.L[0], m.L[1], m.L[2]);
     if (P <= 16)
-      k_k0_moments<T, 16><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+      k_k0_moments<T, 16><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
     else if (P <= 32)
-      k_k0_moments<T, 32><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+      k_k0_moments<T, 32><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
     else
-      k_k0_moments<T, 64><<<kK0Blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+      k_k0_moments<T, 64><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
     LAUNCH_CHECK();
   }
   if (p->has_long) {
@@ -2313,8 +2313,8 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     LAUNCH_CHECK();
     mark_end(p, 7, sl);
     }
-    k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, P, p->d_k0mat,
-                                     p->d_k0nu, p->d_red, kRedBlocks, p->d_status);
+    k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * p->red_blocks, p->k0_blocks, P, p->d_k0mat,
+                                     p->d_k0nu, p->d_red, p->red_blocks, p->d_status);
     LAUNCH_CHECK();
     k_k0_eval<T><<<(N + 255) / 256, 256, 0, sl>>>(r, N, P, 0.5 * m.L[2], p->d_k0nu,
                                                 pp + 3 * (size_t)N, pg + 9 * (size_t)N);
@@ -2323,8 +2323,8 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   } else {
     SOG_CK(cudaMemsetAsync(pp + 2 * (size_t)N, 0, sizeof(double) * 2 * N, sl));
     SOG_CK(cudaMemsetAsync(pg + 6 * (size_t)N, 0, sizeof(double) * 6 * N, sl));
-    k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * kRedBlocks, kK0Blocks, 0, p->d_k0mat,
-                                     p->d_k0nu, p->d_red, kRedBlocks, p->d_status);
+    k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * p->red_blocks, p->k0_blocks, 0, p->d_k0mat,
+                                     p->d_k0nu, p->d_red, p->red_blocks, p->d_status);
     LAUNCH_CHECK();
   }
 
@@ -2335,11 +2335,11 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   SOG_CK(cudaStreamWaitEvent(s, p->ev_join_long, 0));
   mark_begin(p, 9, s);
   if (phi || F || E) {
-    double* epart = p->d_red + 2 * kRedBlocks + (size_t)kRedBlocks * kMaxCheb;
-    k_assemble<T><<<kRedBlocks, 256, 0, s>>>(q, N, pp, pg, p->selfsum, phi, F, epart);
+    double* epart = p->d_red + 2 * p->red_blocks + (size_t)p->red_blocks * kMaxCheb;
+    k_assemble<T><<<p->red_blocks, 256, 0, s>>>(q, N, pp, pg, p->selfsum, phi, F, epart);
     LAUNCH_CHECK();
     if (E) {
-      k_energy<<<1, 32, 0, s>>>(epart, kRedBlocks, E);
+      k_energy<<<1, 32, 0, s>>>(epart, p->red_blocks, E);
       LAUNCH_CHECK();
     }
   }

@@ -288,7 +288,11 @@ sog_status sog_features(int64_t N, double Lx, double Ly, double Lz, double tol, 
     return SOG_ERR_NOMEM;
   }
   cudaMemset(d_hist, 0, 16 * sizeof(unsigned));
-  const int blocks = (int)std::min<int64_t>(304, (N + 255) / 256);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = 1;
+  const int blocks = (int)std::min<int64_t>(2 * (int64_t)sms, (N + 255) / 256);
   if (precision == SOG_PREC_FP64)
     k_zhist<double><<<blocks, 256>>>(static_cast<const double*>(r), N, Lz, d_hist);
   else

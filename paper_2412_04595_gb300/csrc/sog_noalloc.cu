@@ -12,13 +12,14 @@
 
 #include <mutex>
 
-#include "../../include/sog.h"
+#include "sog_internal.h"
 
 namespace {
 
-// Partial sums of q_i Phi_i: one per block, 2 blocks per SM of a 152-SM GPU.
-// 304 doubles = 2432 bytes; the grid-stride loop lets any N use them.
-constexpr int kNoAllocBlocks = 304;
+// Partial sums of q_i Phi_i: one per block, at most 1024 blocks (two per SM
+// of the device, capped); 1024 doubles = 8 KB.  The grid-stride loop lets any
+// N use them.
+constexpr int kNoAllocBlocks = 1024;
 constexpr int kNoAllocThreads = 256;
 // Element indices are 32-bit in the kernel (3 i + d < 2^31).
 constexpr int64_t kNoAllocMaxN = 715827882;
@@ -28,6 +29,7 @@ __device__ __align__(256) double g_energy_partials[kNoAllocBlocks];
 
 std::mutex g_setup_mu;
 double* g_partials_ptr[kMaxDevices] = {};
+int g_blocks[kMaxDevices] = {};
 
 __device__ __forceinline__ double warp_add(double v) {
 #pragma unroll
@@ -37,7 +39,9 @@ __device__ __forceinline__ double warp_add(double v) {
 
 // Phi_i = sum of the four parts - q_i sum_l w_l (self term), F_i = -q_i grad
 // Phi, and one partial sum of q_i Phi_i per block written to part[blockIdx.x]
-// (every block writes its slot, so nothing needs to start at zero).
+// (every block writes its slot, so nothing needs to start at zero).  A
+// non-finite charge counts as 0, as in the plans' own assembly; the plan whose
+// sog_eval_components produced the parts reports it through sog_plan_check.
 template <typename T>
 __global__ void __launch_bounds__(kNoAllocThreads)
     k_assemble_noalloc(const T* __restrict__ q, int N, const double* __restrict__ pp,
@@ -79,8 +83,10 @@ __global__ void k_energy_noalloc(const double* __restrict__ part, int nblk, doub
   if (lane == 0) *E = 0.5 * s;
 }
 
-// Device address of g_energy_partials on the current device, looked up once.
-sog_status partials_ptr(double** out) {
+// Device address of g_energy_partials on the current device and the block
+// count of the assembly there (two per SM, at most kNoAllocBlocks), looked
+// up once per device.
+sog_status partials_ptr(double** out, int* max_blocks) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return SOG_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return SOG_ERR_CUDA;
@@ -88,22 +94,24 @@ sog_status partials_ptr(double** out) {
   if (!g_partials_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_energy_partials) != cudaSuccess || !p) return SOG_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+      return SOG_ERR_CUDA;
+    g_blocks[dev] = 2 * sms < kNoAllocBlocks ? 2 * sms : kNoAllocBlocks;
     g_partials_ptr[dev] = static_cast<double*>(p);
   }
   *out = g_partials_ptr[dev];
+  *max_blocks = g_blocks[dev];
   return SOG_OK;
 }
 
 // sum_l w_l of Eq. (2.22) with w_0 scaled by omega (Eq. 2.25): the
-// coefficient of the self term.
+// coefficient of the self term, term by term from the weights the plans'
+// tables use (no host or device allocation).
 double self_coefficient(const sog_params& prm) {
-  const double c = pow(3.14159265358979323846 / 2.0, -0.5);
   double s = 0.0;
-  for (int l = 0; l <= prm.M; ++l) {
-    double w = c * pow(prm.b, -(double)l) / prm.sigma * log(prm.b);
-    if (l == 0) w *= prm.omega;
-    s += w;
-  }
+  for (int l = 0; l <= prm.M; ++l) s += sogk::sog_weight(prm.b, prm.sigma, prm.omega, l);
   return s;
 }
 
@@ -111,10 +119,11 @@ template <typename T>
 sog_status launch(int N, const void* q, const double* pp, const double* pg, double selfsum,
                   void* phi, double* E, void* F, cudaStream_t s) {
   double* part = nullptr;
-  const sog_status st = partials_ptr(&part);
+  int max_blocks = 0;
+  const sog_status st = partials_ptr(&part, &max_blocks);
   if (st != SOG_OK) return st;
   int blocks = (N + kNoAllocThreads - 1) / kNoAllocThreads;
-  if (blocks > kNoAllocBlocks) blocks = kNoAllocBlocks;
+  if (blocks > max_blocks) blocks = max_blocks;
   k_assemble_noalloc<T><<<blocks, kNoAllocThreads, 0, s>>>(
       static_cast<const T*>(q), N, pp, pg, selfsum, static_cast<T*>(phi), static_cast<T*>(F), part);
   if (cudaGetLastError() != cudaSuccess) return SOG_ERR_CUDA;
@@ -135,7 +144,9 @@ extern "C" sog_status sog_assemble_noalloc(int64_t N, int32_t precision, const s
   if (N < 1 || N > kNoAllocMaxN) return SOG_ERR_ARG;
   if (precision != SOG_PREC_FP64 && precision != SOG_PREC_MIXED) return SOG_ERR_ARG;
   if (F && !grad_parts) return SOG_ERR_ARG;
-  if (!(prm->b > 1.0) || !(prm->sigma > 0.0) || prm->M < 0) return SOG_ERR_ARG;
+  if (!(prm->b > 1.0) || !(prm->sigma > 0.0) || !(prm->omega > 0.0) || prm->M < 0 ||
+      prm->M > 4000 || !isfinite(prm->b) || !isfinite(prm->sigma) || !isfinite(prm->omega))
+    return SOG_ERR_ARG;
   const double selfsum = self_coefficient(*prm);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == SOG_PREC_FP64)

@@ -13,6 +13,29 @@
 
 #include "sog_internal.h"
 
+namespace sogk {
+
+// w_l of Eq. (2.22), w_0 scaled by omega (Eq. 2.25).
+double sog_weight(double b, double sigma, double omega, int l) {
+  const double w = pow(3.14159265358979323846 / 2.0, -0.5) * pow(b, -(double)l) / sigma * log(b);
+  return l == 0 ? w * omega : w;
+}
+
+// w_l and s_l of Eq. (2.22), w_0 scaled by omega (Eq. 2.25).
+void sog_table(double b, double sigma, double omega, int M, std::vector<double>& w,
+               std::vector<double>& s) {
+  w.resize(M + 1);
+  s.resize(M + 1);
+  for (int l = 0; l <= M; ++l) {
+    w[l] = sog_weight(b, sigma, omega, l);
+    s[l] = sqrt(2.0) * pow(b, (double)l) * sigma;
+  }
+}
+
+}  // namespace sogk
+
+using sogk::sog_table;
+
 namespace {
 
 const double kPi = 3.14159265358979323846;
@@ -26,19 +49,6 @@ const double kTable1[6][5] = {
     {1.21812525709410644, 5.6355288151271085, 1.0009014615603334, 7.14e-10, 166},
     {1.14878150173321925, 7.2956245490719404, 1.0000368348358225, 1.30e-15, 271},
 };
-
-// w_l and s_l of Eq. (2.22), w_0 scaled by omega (Eq. 2.25).
-void sog_table(double b, double sigma, double omega, int M, std::vector<double>& w,
-               std::vector<double>& s) {
-  w.resize(M + 1);
-  s.resize(M + 1);
-  const double c = pow(kPi / 2.0, -0.5);
-  for (int l = 0; l <= M; ++l) {
-    w[l] = c * pow(b, -(double)l) / sigma * log(b);
-    s[l] = sqrt(2.0) * pow(b, (double)l) * sigma;
-  }
-  w[0] *= omega;
-}
 
 int fft_size(long n) {
   if (n < 8) n = 8;
@@ -543,6 +553,15 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   p->prec = prec;
   p->N = N;
   cudaGetDevice(&p->device);
+  if (cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess ||
+      p->n_sm < 1) {
+    cudaGetLastError();
+    delete p;
+    return SOG_ERR_CUDA;
+  }
+  p->red_blocks = sogk::kRedBlocksPerSm * p->n_sm;
+  p->mode_blocks = sogk::kModeBlocksPerSm * p->n_sm;
+  p->k0_blocks = sogk::kK0BlocksPerSm * p->n_sm;
   const size_t es = prec == SOG_PREC_FP64 ? sizeof(double) : sizeof(float);
   const double* L = prm.L;
 
@@ -617,7 +636,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     // copies per CTA plus a reduction instead of atomics on a few addresses
     p->long_small = (g.nt[0] == 1 && g.nt[1] == 1 &&
                      (size_t)P * (Ilx * Ily + 1) * es <= 64 * 1024) ? 1 : 0;
-    p->long_small_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sogk::kRedBlocks, N / 128));
+    p->long_small_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->red_blocks, N / 128));
     const double per_tile = (double)N / p->n_tiles_long;
     int ch = (int)ceil(600.0 / p->n_tiles_long);
     ch = std::max(1, std::min(ch, (int)(per_tile / 32.0)));
@@ -854,7 +873,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   const size_t o_cnt = ar.take((size_t)p->cnt_off[3] * sizeof(int));
   const size_t o_pp = ar.take((size_t)4 * N * sizeof(double));
   const size_t o_pg = ar.take((size_t)12 * N * sizeof(double));
-  const size_t o_red = ar.take((size_t)sogk::kRedBlocks * (3 + sogk::kMaxCheb) * sizeof(double));
+  const size_t o_red = ar.take((size_t)p->red_blocks * (3 + sogk::kMaxCheb) * sizeof(double));
   const size_t o_nu = ar.take(sogk::kMaxCheb * sizeof(double));
   const size_t o_st = ar.take(sizeof(int));
   const size_t o_host = ar.take((size_t)N * 8 * es + sizeof(double));
@@ -862,7 +881,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
                                      ? (size_t)p->long_small_blocks * P * Ilx * Ily * es : 0);
   // direct long range: per-block partial moments (FP64) and the coefficients
   const size_t o_lmom = ar.take(p->long_direct
-                                    ? (size_t)sogk::kModeBlocks * p->n_half * P * 2 * sizeof(double)
+                                    ? (size_t)p->mode_blocks * p->n_half * P * 2 * sizeof(double)
                                     : 0);
   const size_t o_lcoef = ar.take(p->long_direct ? (size_t)p->n_half * P * 2 * es : 0);
   void* base = nullptr;

@@ -40,18 +40,27 @@ def test_argument_errors_without_device_work():
     # forces asked for without their gradient parts
     assert L.sog_assemble_noalloc(10, 1, ctypes.byref(prm), dummy, dummy, None, None, None,
                                   dummy, None) == SOG_ERR_ARG
+    # parameters a plan would reject: omega <= 0 or not finite, sigma <= 0, b <= 1
+    for field, value in (("omega", 0.0), ("omega", -1.0), ("omega", float("nan")),
+                         ("sigma", 0.0), ("b", 1.0), ("b", float("inf"))):
+        bad = B.SogParams.from_dict(B.sog_select_params(1000, 10.0, 10.0, 10.0, 1e-6))
+        setattr(bad, field, value)
+        assert L.sog_assemble_noalloc(10, 1, ctypes.byref(bad), dummy, dummy, None, None, None,
+                                      None, None) == SOG_ERR_ARG, (field, value)
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_matches_sog_eval_on_two_calls_in_a_row(precision):
+@pytest.mark.parametrize("precision,N", [("fp64", 20000), ("mixed", 20000), ("mixed", 100000)])
+def test_matches_sog_eval_on_two_calls_in_a_row(precision, N):
+    """N = 1e5 needs more blocks than the assembly launches (two per SM), so
+    the grid-stride loop and the full set of energy partials are used."""
     B = _lib()
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     fp64 = precision == "fp64"
     dt = torch.float64 if fp64 else torch.float32
     prec = B.SOG_PREC_FP64 if fp64 else B.SOG_PREC_MIXED
-    N, L = 20000, (30.0, 30.0, 30.0)
+    L = (30.0 * (N / 20000) ** (1.0 / 3.0),) * 3
     q, r = workloads.uniform_neutral(N, L, seed=11, dtype=np.float64)
     dev = torch.device("cuda:0")
     qt = torch.tensor(q, dtype=dt, device=dev)
@@ -90,3 +99,30 @@ def test_matches_sog_eval_on_two_calls_in_a_row(precision):
     assert torch.equal(outs[0][0], outs[1][0])
     assert torch.equal(outs[0][2], outs[1][2])
     assert outs[0][1].item() == outs[1][1].item()
+
+
+@pytest.mark.gpu
+def test_energy_only_call():
+    """phi and F left out (NULL): only the energy is written, and it equals
+    the energy of sog_eval."""
+    B = _lib()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    N, L = 30000, (40.0, 40.0, 40.0)
+    q, r = workloads.uniform_neutral(N, L, seed=12, dtype=np.float64)
+    dev = torch.device("cuda:0")
+    qt = torch.tensor(q, dtype=torch.float64, device=dev)
+    rt = torch.tensor(r, dtype=torch.float64, device=dev)
+    plan = B.Plan(N, L, 1e-6, precision=B.SOG_PREC_FP64)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    plan.eval(qt, rt, None, E, None)
+    pp = torch.empty(4, N, dtype=torch.float64, device=dev)
+    plan.eval_components(qt, rt, pp, None)
+    torch.cuda.synchronize()
+    assert plan.check() == SOG_OK
+    for _ in range(2):
+        E_a = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
+        B.sog_assemble_noalloc(plan.params, qt, pp, None, None, E_a, None)
+        torch.cuda.synchronize()
+        assert abs(E_a.item() - E.item()) <= 1e-12 * abs(E.item())
+    plan.close()
