@@ -5,11 +5,21 @@ One step = one sog_eval call over the whole hot path (binning, near field,
 mid range, long range and its k = 0 mode, assembly) on the workload below,
 with inputs resident on the device.  Prints one JSON line.
 
-Workload (default "c2"): N = 1e5 neutral +-1 charges, uniform positions in a
-100 x 100 x 100 box, periodic in x and y and free in z, relative tolerance
-1e-6, mixed precision (FP32 bulk, FP64 tables / k = 0 mode / reductions).
+Default workload ("c3_slab"): a thin slab, N = 1e6 neutral +-1 charges at
+uniform positions in a 1000 x 1000 x 10 box, periodic in x and y and free in
+z, relative tolerance 1e-6, mixed precision (FP32 bulk; FP64 tables, k = 0
+mode and reductions).  It is the largest configuration at the 1e-6 error of
+the metric; its long range takes the gridded form (Algorithm 2).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--precision mixed|fp64]
+
+Besides the timed value the line reports: the same workload through an FP64
+plan (plain_fp64); accuracy against the FP64 oracle on sampled targets and
+against Ewald2D (the true quasi-2D sum) on a few targets; isolated per-stage
+times and their rooflines against measured peaks; the end-to-end rate through
+the host entry point; and the oracle's rate on a bounded sample of the
+workload on the host cores.
 
 With --gpus N > 1 (launched by torch.distributed.run) every rank evaluates
 its own replica of the workload; there is no collective on the data path.
@@ -30,33 +40,47 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particles/s (energy+forces) at rel. error 1e-6 vs FP64 oracle; % HBM roofline"
 WORKLOADS = {
-    "c2": dict(N=100000, L=(100.0, 100.0, 100.0), tol=1e-6, seed=1,
-               desc="uniform neutral +-1 charges, N=1e5, box 100x100x100 (periodic x,y, free z), tol 1e-6"),
-    "c2_1e4": dict(N=100000, L=(100.0, 100.0, 100.0), tol=1e-4, seed=1,
+    "c3_slab": dict(N=1000000, L=(1000.0, 1000.0, 10.0), tol=1e-6, seed=3, kind="uniform",
+                    keep_z=True,
+                    desc="thin slab: 1e6 uniform neutral +-1 charges, box 1000x1000x10 "
+                         "(periodic x,y, free z), tol 1e-6"),
+    "c3_tall": dict(N=1000000, L=(50.0, 50.0, 2000.0), tol=1e-6, seed=3, kind="uniform",
+                    keep_z=False,
+                    desc="tall cell: 1e6 uniform neutral +-1 charges, box 50x50x2000, tol 1e-6"),
+    "c4": dict(N=4000000, L=(400.0, 400.0, 100.0), tol=1e-5, seed=3, kind="edl", keep_z=True,
+               desc="electric double layer: 4e6 charges, cations ~exp(-z/2) at one wall, anions at "
+                    "the other, half uniform bulk, box 400x400x100, tol 1e-5"),
+    "c2": dict(N=100000, L=(100.0, 100.0, 100.0), tol=1e-6, seed=1, kind="uniform", keep_z=False,
+               desc="uniform neutral +-1 charges, N=1e5, box 100x100x100, tol 1e-6"),
+    "c2_1e4": dict(N=100000, L=(100.0, 100.0, 100.0), tol=1e-4, seed=1, kind="uniform",
+                   keep_z=False,
                    desc="uniform neutral +-1 charges, N=1e5, box 100x100x100, tol 1e-4"),
-    "c1": dict(N=1000, L=(10.0, 10.0, 10.0), tol=1e-6, seed=1,
+    "c1": dict(N=1000, L=(10.0, 10.0, 10.0), tol=1e-6, seed=1, kind="uniform", keep_z=False,
                desc="uniform neutral +-1 charges, N=1e3, box 10x10x10, tol 1e-6"),
     "c5": dict(batch=256, seed=5, tol=1e-6, N=None, L=(0.0, 0.0, 0.0),
                desc="256 independent neutral +-1 systems, N log-uniform in [500, 50000], "
                     "density 0.1, Lz/Lx uniform in [0.05, 10], tol 1e-6, one graph launch"),
 }
+DEFAULT_WORKLOAD = "c3_slab"
 FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2, written between steps
-# FP32 operations of the near field: 8 per candidate of the 27-cell
-# neighbourhood (3 differences, squared distance, comparison) and 60 per pair
-# inside r_c (distance again, reciprocal square root, degree-8 table
-# polynomial with its derivative, compensated potential sum, force).
+N_ORACLE_TARGETS = 2000          # sampled targets compared with the FP64 oracle
+N_TRUTH_TARGETS = 16             # targets compared with Ewald2D
+CPU_SAMPLE_SECONDS = 15.0        # oracle work of the CPU baseline's bounded sample
+# FP32 operations the near field must do (the per-unit counts of the method,
+# not of this implementation): 8 per candidate of the 27-cell neighbourhood
+# (3 differences, squared distance, comparison) and 30 per pair inside r_c
+# (distance, reciprocal, kernel value and derivative, potential and force).
 CAND_FLOP = 8
-PAIR_FLOP = 60
-DOMINANT = "near"   # largest share of GPU time in the kernel launch list
+PAIR_FLOP = 30
 
 
-def peaks():
+def hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
-        return 6800.0, 2070.0, "fallback"
+        return 6800.0, "fallback"
 
 
 class ClockSampler:
@@ -105,89 +129,144 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def stage_units(prm, N, stage):
+def make_system(wl, N=None, seed=None):
+    """Charges and positions of the workload (FP32-rounded positions, as both
+    the mixed plan and the oracle see them).  With N below the workload's,
+    a system of the same kind: same density, the slab and double layer keep
+    their height, the others their aspect ratio."""
+    import numpy as np
+    from paper_2412_04595_gb300 import workloads
+    N0, L0 = wl["N"], wl["L"]
+    N = N0 if N is None else N
+    if N == N0:
+        L = tuple(L0)
+    elif wl["keep_z"]:
+        f = (N / N0) ** 0.5
+        L = (L0[0] * f, L0[1] * f, L0[2])
+    else:
+        f = (N / N0) ** (1.0 / 3.0)
+        L = tuple(x * f for x in L0)
+    gen = workloads.uniform_neutral if wl["kind"] == "uniform" else workloads.edl_neutral
+    q, r = gen(N, L, wl["seed"] if seed is None else seed, dtype=np.float32)
+    return q, r, L
+
+
+def stage_work(prm, N, stage, es):
     """Algorithmic work of one launch of a stage and the resource bounding it:
-    ("alu", FP32 operations) or ("hbm", bytes), with a description."""
+    ("alu", FP32 operations), ("hbm", bytes) or (None, None), with its
+    description.  es: bytes per element of the plan's type."""
     Ix, Iy, Iz = prm["I"]
-    P = prm["P_win"]
+    P, Pc, Pl = prm["P_win"], prm["P_cheb"], prm["P_long"]
     L = prm["L"]
     rho = N / (L[0] * L[1] * L[2])
-    pairs = N * 4.0 / 3.0 * math.pi * prm["rc"] ** 3 * rho
-    ncell = [max(1, int(math.floor(L[d] / prm["rc"]))) for d in range(3)]
-    cand = N * 27.0 * N / (ncell[0] * ncell[1] * ncell[2])
     if stage == "near":
+        pairs = N * 4.0 / 3.0 * math.pi * prm["rc"] ** 3 * rho
+        nc = [max(1, int(math.floor(L[d] / prm["rc"]))) for d in range(3)]
+        ext = [min(3, nc[d]) for d in range(3)]
+        cand = N * ext[0] * ext[1] * ext[2] * N / (nc[0] * nc[1] * nc[2])
         return ("alu", cand * CAND_FLOP + pairs * PAIR_FLOP,
-                "FP32 flop: %.3g candidates x %d + %.3g pairs x %d" % (cand, CAND_FLOP, pairs, PAIR_FLOP))
+                "FP32 flop: %.3g candidates x %d + %.3g pairs x %d"
+                % (cand, CAND_FLOP, pairs, PAIR_FLOP))
+    if stage == "binning":
+        sets = 1 + (prm["m"] >= 0) + (prm["m"] < prm["M"] and not prm["long_direct"])
+        return ("hbm", N * (4 * es + sets * 17 * es),
+                "bytes: q, r read; per bin set key, rank, record written and read, sorted record "
+                "and permutation written (%d sets)" % sets)
     if stage == "mid_spread":
         return "alu", N * P ** 3 * 2.0, "FP32 flop: N x P^3 x 2"
     if stage == "mid_gather":
         return "alu", N * P ** 3 * 4.0, "FP32 flop: N x P^3 x 4 (value and x-derivative sums)"
     if stage == "mid_fft":
         half = Iz * Iy * (Ix // 2 + 1)
-        return ("hbm", 3 * 2 * half * 8 + half * 4,
+        return ("hbm", 3 * 2 * half * 2 * es + half * es,
                 "bytes: 3 passes x (read + write) of the complex half spectrum + scaling table")
-    if stage == "long_gather":
-        Pl, Pc = prm["P_long"], prm["P_cheb"]
-        return "alu", N * Pc * Pl ** 2 * 4.0, "FP32 flop: N x P_cheb x P_long^2 x 4"
     if stage == "long_spread":
-        Pc = prm["P_cheb"]
+        return "alu", N * Pc * Pl * Pl * 2.0, "FP32 flop: N x P_cheb x P_long^2 x 2"
+    if stage == "long_gather":
+        return "alu", N * Pc * Pl * Pl * 4.0, "FP32 flop: N x P_cheb x P_long^2 x 4"
+    if stage == "long_fft":
         Ilx, Ily = prm["I_long"]
-        return "alu", N * Pc * Ilx * Ily * 2.0, "FP32 flop: N x P_cheb x I_long^2 x 2 (dense planes)"
+        planes = Pc * Ily * (Ilx + 2) * es
+        return ("hbm", 6 * planes,
+                "bytes: x pass, fused y pass with contraction, backward x pass: "
+                "3 x (read + write) of the %d proxy planes" % Pc)
     if stage in ("long_moments", "long_eval"):
-        Pc = prm["P_cheb"]
         Kx, Ky = (prm["I_long"][0] - 1) // 2, (prm["I_long"][1] - 1) // 2
         nh = Ky + Kx * (2 * Ky + 1)
         k = 4.0 if stage == "long_moments" else 8.0
-        return ("alu", N * nh * Pc * k,
-                "FP32 flop: N x half-plane modes x P_cheb x %d" % k)
+        return ("alu", N * nh * Pc * k, "FP32 flop: N x half-plane modes x P_cheb x %d" % k)
+    if stage == "assemble":
+        return ("hbm", N * (16 * 8 + 5 * es),
+                "bytes: four parts and their gradients (FP64) read, q read, phi and F written")
     return None, None, None
 
 
-def roofline_entry(prm, N, stage, t_s, hbm, fp32_peak, smax, src):
-    bound, work, desc = stage_units(prm, N, stage)
+def roofline_entry(prm, N, stage, t_s, es, peaks):
+    bound, work, desc = stage_work(prm, N, stage, es)
     if bound == "alu":
+        peak, src = peaks["fp32_tflops"] if es == 4 else peaks["fp64_tflops"], peaks["alu_src"]
         ach = work / t_s / 1e12
-        return {"bound": "alu", "kernel": stage, "achieved": ach, "peak": fp32_peak,
-                "unit": "TFLOP/s", "frac": ach / fp32_peak, "work_per_launch": desc,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
+        return {"bound": "alu", "kernel": stage, "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "work_per_launch": desc,
+                "launch_ms": t_s * 1e3, "peak_source": src + (" FP32" if es == 4 else " FP64")}
     if bound == "hbm":
         ach = work / t_s / 1e9
-        return {"bound": "hbm", "kernel": stage, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "work_per_launch": desc, "peak_source": src}
+        return {"bound": "hbm", "kernel": stage, "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "work_per_launch": desc,
+                "launch_ms": t_s * 1e3, "peak_source": peaks["hbm_src"]}
     return None
 
 
-def recorded_traffic(stage):
+def recorded_traffic(stage, workload):
     """DRAM bytes per launch recorded by an ncu capture of the current kernel
-    source (profiles/<stage>_traffic.txt: 'source_sha256 <hex>' and
-    'dram_bytes <n>'); None when absent or taken on another version."""
+    sources (profiles/traffic_<stage>_<workload>.txt: 'source_sha256 <hex>'
+    and 'dram_bytes <n>'); None when absent or taken on other sources."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "%s_traffic.txt" % stage)
+    path = os.path.join(ROOT, "profiles", "traffic_%s_%s.txt" % (stage, workload))
     try:
         rec = dict(line.split(None, 1) for line in open(path).read().splitlines() if line.strip()
                    and not line.startswith("#"))
-        src = os.path.join(ROOT, "paper_2412_04595_gb300", "csrc", "sog_kernels.cu")
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("source_sha256", "").strip() != sha:
+        h = hashlib.sha256()
+        for f in ("sog_kernels.cu", "sog_fft.cu"):
+            h.update(open(os.path.join(ROOT, "paper_2412_04595_gb300", "csrc", f), "rb").read())
+        if rec.get("source_sha256", "").strip() != h.hexdigest():
             return None
         return float(rec["dram_bytes"])
     except Exception:
         return None
 
 
+def timed_steps(fn, steps, stream, flush):
+    """Device milliseconds of each of `steps` calls of fn, L2 flushed before
+    each, CUDA events on `stream`."""
+    import torch
+    out = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
 def run_ours(args, wl, rank, world):
     import numpy as np
     import torch
     import __graft_entry__ as g
-    from paper_2412_04595_gb300 import binding as B, workloads
+    from paper_2412_04595_gb300 import binding as B
 
     g.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     N, L, tol = wl["N"], wl["L"], wl["tol"]
     prec = B.SOG_PREC_FP64 if args.precision == "fp64" else B.SOG_PREC_MIXED
-    np_dt = np.float64 if prec == B.SOG_PREC_FP64 else np.float32
-    q, r = workloads.uniform_neutral(N, L, wl["seed"], dtype=np_dt)
+    q, r, _ = make_system(wl)
+    q = q.astype(np.float64) if prec == B.SOG_PREC_FP64 else q
+    r = r.astype(np.float64) if prec == B.SOG_PREC_FP64 else r
     plan = B.Plan(N, L, tol, precision=prec, n_nb=args.n_nb)
     dt = plan.dtype
     qt = torch.tensor(q, device=dev)
@@ -197,10 +276,13 @@ def run_ours(args, wl, rank, world):
     E = torch.zeros(1, dtype=torch.float64, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    plan.set_timing(True)
+
+    def step():
+        plan.eval(qt, rt, phi, E, F, stream=stream)
+
     for _ in range(args.warmup):
         flush.fill_(1)
-        plan.eval(qt, rt, phi, E, F, stream=stream)
+        step()
     torch.cuda.synchronize()
     if plan.check() != 0:
         raise RuntimeError("evaluation reported a data error")
@@ -210,29 +292,31 @@ def run_ours(args, wl, rank, world):
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index)
     clocks.start()
-    times = []
-    stages = {}
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plan.eval(qt, rt, phi, E, F, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1))
-        for k, v in plan.timing().items():
-            stages.setdefault(k, []).append(v)
+    times = timed_steps(step, args.steps, stream, flush)
     torch.cuda.synchronize()
-    launches = plan.launches() * args.steps
     clk = clocks.stop()
+    launches = plan.launches() * args.steps
     total_ms = max_over_ranks(sum(times), dev)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     value = world * N * args.steps / (total_ms * 1e-3)
-    stage_ms = {k: sum(v) / len(v) for k, v in stages.items()}
+    phi_h = phi.double().cpu().numpy()
+    F_h = F.double().cpu().numpy()
+    E_h = float(E.item())
+
+    # isolated stage durations: every stage on this stream, one after another
+    plan.set_timing(2)
+    stages = {}
+    for _ in range(max(3, min(args.steps, 20))):
+        flush.fill_(1)
+        step()
+        torch.cuda.synchronize()
+        for k, v in plan.timing().items():
+            stages.setdefault(k, []).append(v)
+    plan.set_timing(0)
+    stage_ms = {k: float(np.median(v)) for k, v in stages.items()}
 
     # end to end through the host entry point (pinned buffers, H2D + D2H inside)
     qh = torch.tensor(q).pin_memory()
@@ -240,7 +324,6 @@ def run_ours(args, wl, rank, world):
     phih = torch.empty(N, dtype=dt).pin_memory()
     Fh = torch.empty(N, 3, dtype=dt).pin_memory()
     Eh = torch.empty(1, dtype=torch.float64).pin_memory()
-    plan.set_timing(False)
     for _ in range(2):
         plan.eval_host(qh, rh, phih, Eh, Fh)
     e2e_s = 0.0
@@ -255,20 +338,124 @@ def run_ours(args, wl, rank, world):
     es = q.dtype.itemsize
     e2e = {"value": N * args.steps / e2e_s, "unit": "particles/s",
            "h2d_bytes_per_step": int(N * 4 * es), "d2h_bytes_per_step": int(N * 4 * es + 8)}
+    prm = plan.params
 
-    out = dict(plan=plan, stage_ms=stage_ms, value=value, total_ms=total_ms, times=times,
-               launches=launches, clocks=clk, e2e=e2e, E=float(Eh[0]), F=Fh.numpy().astype(np.float64),
-               phi=phih.numpy().astype(np.float64), q=q, r=r)
-    return out
+    # the plain FP64 form: the same workload and parameters through an FP64 plan
+    plain = None
+    if prec != B.SOG_PREC_FP64 and not args.no_plain_fp64:
+        p64 = B.Plan(N, L, tol, precision=B.SOG_PREC_FP64, manual=prm)
+        q64 = torch.tensor(q.astype(np.float64), device=dev)
+        r64 = torch.tensor(r.astype(np.float64), device=dev)
+        phi64 = torch.empty(N, dtype=torch.float64, device=dev)
+        F64 = torch.empty(N, 3, dtype=torch.float64, device=dev)
+        E64 = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def step64():
+            p64.eval(q64, r64, phi64, E64, F64, stream=stream)
+
+        for _ in range(2):
+            flush.fill_(1)
+            step64()
+        torch.cuda.synchronize()
+        s64 = max(3, min(args.steps, 10))
+        t64 = sum(timed_steps(step64, s64, stream, flush))
+        if p64.check() != 0:
+            raise RuntimeError("FP64 evaluation reported a data error")
+        plain = {"value": N * s64 / (t64 * 1e-3), "unit": "particles/s", "ms_per_step": t64 / s64,
+                 "steps": s64, "dtype": "f64",
+                 "desc": "the same workload, inputs and parameters through an FP64 plan",
+                 "phi": phi64.cpu().numpy(), "F": F64.cpu().numpy(), "E": float(E64.item())}
+        p64.close()
+    plan.close()
+    return dict(prm=prm, stage_ms=stage_ms, value=value, total_ms=total_ms, launches=launches,
+                clocks=clk, e2e=e2e, E=E_h, F=F_h, phi=phi_h, q=q, r=r, plain=plain, es=es)
 
 
-def oracle_run(prm, q, r):
+def rel_errors(phi, F, ref_phi, ref_F):
+    """The paper's measure (largest potential error over the largest
+    potential) and the RMS force error relative to the RMS force."""
+    import numpy as np
+    linf = float(np.max(np.abs(phi - ref_phi)) / np.max(np.abs(ref_phi)))
+    rmsF = float(math.sqrt(np.mean(np.sum((F - ref_F) ** 2, 1)) / np.mean(np.sum(ref_F ** 2, 1))))
+    return linf, rmsF
+
+
+def sampled_targets(r, n, seed=7):
+    """n random targets plus the particles nearest the walls and box edges."""
+    import numpy as np
+    N = r.shape[0]
+    pick = set(np.random.default_rng(seed).choice(N, min(n, N), replace=False).tolist())
+    for col in range(3):
+        o = np.argsort(r[:, col])
+        pick.update(o[:4].tolist())
+        pick.update(o[-4:].tolist())
+    return np.array(sorted(pick), dtype=np.int64)
+
+
+def accuracy(res, wl):
+    """Errors of the GPU results against the FP64 oracle (same parameters,
+    sampled targets) and against Ewald2D (the true quasi-2D sum)."""
+    import numpy as np
     import oracle
     from oracle import sog as osog
     oracle.build_oracle()
+    q = res["q"].astype(np.float64)
+    r = res["r"].astype(np.float64)
+    tgt = sampled_targets(r, N_ORACLE_TARGETS)
     t0 = time.perf_counter()
-    ref = osog.sog_eval(prm, q.astype("float64"), r.astype("float64"))
-    return ref, time.perf_counter() - t0, oracle.num_threads()
+    ref = osog.sog_eval(res["prm"], q, r, tgt)
+    t_or = time.perf_counter() - t0
+    linf, rmsF = rel_errors(res["phi"][tgt], res["F"][tgt], ref["phi"], ref["F"])
+    out = {"vs_oracle": {"targets": int(tgt.size), "rel_linf_potential": linf, "rms_force": rmsF,
+                         "oracle_seconds": t_or,
+                         "desc": "FP64 oracle with the plan's parameters on sampled targets "
+                                 "(random plus those nearest the walls and box edges)"}}
+    if res["plain"] is not None:
+        l64, f64 = rel_errors(res["plain"]["phi"][tgt], res["plain"]["F"][tgt], ref["phi"], ref["F"])
+        out["vs_oracle"]["plain_fp64_rel_linf_potential"] = l64
+        out["vs_oracle"]["plain_fp64_rms_force"] = f64
+        out["rel_energy_vs_plain_fp64"] = abs(res["E"] - res["plain"]["E"]) / abs(res["plain"]["E"])
+    tt = tgt[:: max(1, tgt.size // N_TRUTH_TARGETS)][:N_TRUTH_TARGETS]
+    L = res["prm"]["L"]
+    t0 = time.perf_counter()
+    ph_true, g_true = osog.ewald2d(q, r, L, tt, alpha=1.5 / min(L[0], L[1]))
+    t_ew = time.perf_counter() - t0
+    lt, ft = rel_errors(res["phi"][tt], res["F"][tt], ph_true, -q[tt, None] * g_true)
+    out["vs_truth"] = {"targets": int(tt.size), "rel_linf_potential": lt, "rms_force": ft,
+                       "ewald_seconds": t_ew, "tol": wl["tol"],
+                       "desc": "Ewald2D (Parry's sum, the paper's reference) on sampled targets; "
+                               "rel_linf_potential is the paper's error measure"}
+    return out
+
+
+def cpu_baseline(wl, args):
+    """The FP64 oracle on the host cores on a bounded sample: one evaluation
+    of a system of the same kind (same density and shape) with N_s charges,
+    N_s chosen from a calibration run so that it takes about
+    CPU_SAMPLE_SECONDS."""
+    import oracle
+    from oracle import sog as osog
+    oracle.build_oracle()
+
+    def run(ns):
+        q, r, L = make_system(wl, ns)
+        prm = osog.select_params(ns, *L, wl["tol"], n_nb=args.n_nb)
+        t0 = time.perf_counter()
+        osog.sog_eval(prm, q.astype("float64"), r.astype("float64"))
+        return time.perf_counter() - t0
+
+    # calibrate twice: the grid work grows like N, the oracle's direct near
+    # field like N^2, so the second estimate is taken from a larger system
+    ns = min(wl["N"], 4000)
+    t = run(ns)
+    for _ in range(2):
+        nxt = int(max(1000, min(wl["N"], ns * CPU_SAMPLE_SECONDS / max(t, 1e-9))))
+        nxt -= nxt % 2
+        if abs(nxt - ns) < 0.2 * ns:
+            break
+        ns = nxt
+        t = run(ns)
+    return ns, t, oracle.num_threads()
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -409,102 +596,118 @@ def run_batched(args, wl, config, rank, world):
                                            "path matches the FP64 oracle to 1e-10"}})
 
 
+def measured_peaks():
+    from paper_2412_04595_gb300 import binding as B
+    hbm, hsrc = hbm_peak()
+    return {"hbm_gbs": hbm, "hbm_src": hsrc,
+            "fp32_tflops": B.sog_measure_fma_peak(B.SOG_PREC_MIXED),
+            "fp64_tflops": B.sog_measure_fma_peak(B.SOG_PREC_FP64),
+            "alu_src": "measured on this GPU by sog_measure_fma_peak (independent FMA chains)"}
+
+
+def run_reference(args, wl, config, rank):
+    """The oracle on the host cores (rank 0 only): each step one evaluation
+    of a bounded sample of the workload, a system of the same kind with N_s
+    charges, N_s chosen so that the whole run takes about two minutes."""
+    if rank != 0:
+        return
+    import oracle
+    from oracle import sog as osog
+    oracle.build_oracle()
+    if "batch" in wl:
+        wl = dict(WORKLOADS["c2"], desc=wl["desc"])
+
+    def sample(ns):
+        q, r, L = make_system(wl, ns)
+        return osog.select_params(ns, *L, wl["tol"], n_nb=args.n_nb), q, r
+
+    def run(prm, q, r):
+        t0 = time.perf_counter()
+        osog.sog_eval(prm, q.astype("float64"), r.astype("float64"))
+        return time.perf_counter() - t0
+
+    budget = 120.0 / (args.steps + args.warmup)
+    ns = min(wl["N"], 4000)
+    t = run(*sample(ns))
+    for _ in range(2):
+        nxt = int(max(500, min(wl["N"], ns * budget / max(t, 1e-9))))
+        nxt -= nxt % 2
+        if abs(nxt - ns) < 0.2 * ns:
+            break
+        ns = nxt
+        t = run(*sample(ns))
+    prm, q, r = sample(ns)
+    for _ in range(args.warmup):
+        run(prm, q, r)
+    t = sum(run(prm, q, r) for _ in range(args.steps))
+    value = ns * args.steps / t
+    cores = oracle.num_threads()
+    desc = ("FP64 oracle, one evaluation of a %d-charge system of the same kind "
+            "(same density and shape) per step" % ns)
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s",
+          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+          "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                           "sample": desc},
+          "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                  "d2h_bytes_per_step": 0}})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--n-nb", dest="n_nb", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-plain-fp64", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    config = {"workload": wl["desc"], "N": wl["N"], "L": list(wl["L"]), "tol": wl["tol"],
-              "precision": args.precision, "n_nb": args.n_nb,
-              "l2": "flushed between steps (%d MiB write)" % (FLUSH_BYTES >> 20),
+    config = {"workload": wl["desc"], "name": args.workload, "N": wl["N"],
+              "L": list(wl["L"]), "tol": wl["tol"], "precision": args.precision,
+              "n_nb": args.n_nb, "l2": "flushed between steps (%d MiB write)" % (FLUSH_BYTES >> 20),
               "parallelism": "replicas x%d" % world}
 
     if args.impl == "reference":
-        # the oracle on the host cores, rank 0 only.  Each step evaluates a
-        # bounded sample of the workload: a system of the same kind (uniform
-        # neutral charges at the same density and box aspect) with N_s
-        # particles, N_s chosen from a calibration run so that the whole
-        # warm-up + timed run takes about two minutes.
-        if rank != 0:
-            return
-        import numpy as np
-        from oracle import sog as osog
-        from paper_2412_04595_gb300 import workloads
-        N, L = wl["N"], wl["L"]
-
-        def sample(ns):
-            f = (ns / N) ** (1.0 / 3.0)
-            Ls = tuple(x * f for x in L)
-            q, r = workloads.uniform_neutral(ns, Ls, wl["seed"])
-            return osog.select_params(ns, *Ls, wl["tol"], n_nb=args.n_nb), q, r
-
-        n_cal = min(N, 4000)
-        prm, q, r = sample(n_cal)
-        _, t_cal, cores = oracle_run(prm, q, r)
-        budget = 120.0 / (args.steps + args.warmup)
-        ns = int(max(500, min(N, n_cal * budget / max(t_cal, 1e-9))))
-        ns -= ns % 2
-        prm, q, r = sample(ns)
-        for _ in range(args.warmup):
-            oracle_run(prm, q, r)
-        t = 0.0
-        for _ in range(args.steps):
-            _, dt, cores = oracle_run(prm, q, r)
-            t += dt
-        value = ns * args.steps / t
-        desc = ("FP64 oracle, one evaluation of a %d-particle system of the same kind "
-                "(same density and box aspect) per step" % ns)
-        emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "particles/s",
-              "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-              "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-              "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
-                               "sample": desc},
-              "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
-                      "d2h_bytes_per_step": 0}})
+        run_reference(args, wl, config, rank)
         return
 
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     if "batch" in wl:
-        if world > 1:
-            import torch.distributed as dist
-            dist.init_process_group("nccl")
         run_batched(args, wl, config, rank, world)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
 
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
     res = run_ours(args, wl, rank, world)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    import numpy as np
-    plan = res["plan"]
-    prm = plan.params
+    prm = res["prm"]
     N = wl["N"]
-    hbm, smax, src = peaks()
-    fp32_peak = 152 * 128 * 2 * smax * 1e6 / 1e12          # TFLOP/s at the max SM clock
-    dom = DOMINANT if DOMINANT in res["stage_ms"] else max(res["stage_ms"], key=res["stage_ms"].get)
-    roof = roofline_entry(prm, N, dom, res["stage_ms"][dom] * 1e-3, hbm, fp32_peak, smax, src)
+    peaks = measured_peaks()
+    rooflines = [roofline_entry(prm, N, k, v * 1e-3, res["es"], peaks)
+                 for k, v in res["stage_ms"].items() if v > 0]
+    rooflines = [x for x in rooflines if x is not None]
+    # the dominant kernel: the stage with the longest isolated duration
+    roof = max(rooflines, key=lambda x: x["launch_ms"]) if rooflines else None
     if roof is not None:
-        roof["traffic"] = recorded_traffic(dom)
-    others = [roofline_entry(prm, N, k, v * 1e-3, hbm, fp32_peak, smax, src)
-              for k, v in res["stage_ms"].items() if k != dom and v > 0]
+        roof["traffic"] = recorded_traffic(roof["kernel"], args.workload)
+        roof["timing"] = ("isolated stage duration: CUDA events around the stage's kernels, "
+                          "stages run one after another on the bench's stream, median of steps")
     line = {"metric": METRIC, "value": res["value"], "unit": "particles/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["total_ms"] / args.steps, "higher_is_better": True,
@@ -512,25 +715,23 @@ def main():
             "dtype": "f32" if args.precision == "mixed" else "f64",
             "data": "synthetic", "config": config, "e2e": res["e2e"],
             "gpu_launches": res["launches"], "clocks": res["clocks"], "roofline": roof,
-            "roofline_stages": [o for o in others if o is not None],
-            "stage_ms": {k: round(v, 5) for k, v in res["stage_ms"].items()},
-            "params": {k: prm[k] for k in ("rc", "M", "m", "I", "P_win", "I_long", "P_cheb",
-                                           "long_direct")}}
+            "roofline_stages": [x for x in rooflines if x is not roof],
+            "stage_ms_isolated": {k: round(v, 5) for k, v in res["stage_ms"].items()},
+            "peaks": {k: v for k, v in peaks.items()},
+            "params": {k: prm[k] for k in ("rc", "M", "m", "I", "P_win", "I_long", "P_long",
+                                           "P_cheb", "long_direct")}}
+    if res["plain"] is not None:
+        line["plain_fp64"] = {k: v for k, v in res["plain"].items() if k not in ("phi", "F", "E")}
+        line["speedup_vs_plain_fp64"] = res["value"] / (world * res["plain"]["value"])
+    if not args.no_accuracy:
+        line["accuracy"] = accuracy(res, wl)
     if not args.no_cpu_baseline:
-        from oracle import sog as osog
-        oprm = osog.select_params(N, *wl["L"], wl["tol"], n_nb=args.n_nb)
-        ref, t_or, cores = oracle_run(oprm, res["q"], res["r"])
-        line["cpu_baseline"] = {"value": N / t_or, "unit": "particles/s", "cores": cores,
+        ns, t, cores = cpu_baseline(wl, args)
+        line["cpu_baseline"] = {"value": ns / t, "unit": "particles/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": "the full workload once (FP64 oracle, same inputs and parameters)"}
-        Fr = ref["F"]
-        line["accuracy_vs_oracle"] = {
-            "rel_energy": abs(res["E"] - ref["E"]) / abs(ref["E"]),
-            "rms_force": float(math.sqrt(np.mean(np.sum((res["F"] - Fr) ** 2, 1)) /
-                                         np.mean(np.sum(Fr ** 2, 1)))),
-            # the paper's measure: largest potential error relative to the largest potential
-            "rel_linf_potential": float(np.max(np.abs(res["phi"] - ref["phi"])) /
-                                        np.max(np.abs(ref["phi"])))}
+                                "sample": "one FP64 oracle evaluation of a %d-charge system of the "
+                                          "same kind (same density and shape), %.1f s; the "
+                                          "oracle's near field is a direct O(N^2) sum" % (ns, t)}
     emit(line)
     if world > 1:
         import torch.distributed as dist

@@ -50,7 +50,9 @@ typedef enum {
   SOG_ERR_OUT_OF_BOX = 3,   /* a z outside [-Lz/2, Lz/2] or a non-finite coordinate; from sog_plan_check */
   SOG_ERR_NOMEM = 4,        /* device or host allocation failed */
   SOG_ERR_CUDA = 5,         /* a CUDA call or kernel launch failed */
-  SOG_ERR_PARAMS = 6        /* no feasible or an inconsistent parameter set */
+  SOG_ERR_PARAMS = 6,       /* no feasible or an inconsistent parameter set */
+  SOG_ERR_TIMEOUT = 7       /* a kernel's bounded wait for its own asynchronous copies ran out;
+                               from sog_plan_check (the outputs of that call are unspecified) */
 } sog_status;
 
 enum { SOG_PREC_FP64 = 0, SOG_PREC_MIXED = 1 };
@@ -179,15 +181,19 @@ sog_status sog_eval_host(sog_plan* plan, const void* q, const void* r, void* phi
 /*
  * Wait for the plan's last stream, then return and clear the data status
  * latched by the device since the previous check (SOG_ERR_NONNEUTRAL,
- * SOG_ERR_OUT_OF_BOX), or SOG_ERR_CUDA if a launch failed.
+ * SOG_ERR_OUT_OF_BOX, SOG_ERR_TIMEOUT), or SOG_ERR_CUDA if a launch failed.
  */
 sog_status sog_plan_check(sog_plan* plan);
 
 /*
- * Stage timers.  With timing enabled, every evaluation records CUDA events on
- * its stream at the start of each stage; sog_plan_get_timing waits for the
- * last evaluation and writes the device time of each stage in milliseconds
- * to ms[SOG_NSTAGES] (host memory; 0 for stages that did not run):
+ * Stage timers.  With timing enabled (enable = 1), every evaluation records
+ * CUDA events on its stream at the start and end of each stage; the stages
+ * run concurrently as usual, so a stage's time includes any wait for SMs held
+ * by the others.  With enable = 2 every stage runs on the caller's stream one
+ * after another (no concurrency), so each time is the isolated duration of
+ * that stage's kernels.  sog_plan_get_timing waits for the last evaluation
+ * and writes the device time of each stage in milliseconds to
+ * ms[SOG_NSTAGES] (host memory; 0 for stages that did not run):
  *   0 binning and sorts        1 near field (Eq. 2.28)
  *   2 mid gridding (Eq. 3.7)   3 mid FFT / scaling / inverse FFT (Eq. 3.8)
  *   4 mid gathering (Eq. 3.10) 5 long gridding onto proxy planes
@@ -202,6 +208,17 @@ sog_status sog_plan_get_timing(sog_plan* plan, float* ms);
 
 /* Number of kernels the last evaluation launched. */
 int64_t sog_plan_launches(const sog_plan* plan);
+
+/*
+ * Measured fused multiply-add rate of the current device (a measurement
+ * utility; the paper has no counterpart): FP32 (precision SOG_PREC_MIXED) or
+ * FP64 (SOG_PREC_FP64) FMAs in independent chains on every SM, timed with
+ * CUDA events, in TFLOP/s (2 flop per FMA), written to host *tflops.  It is
+ * the peak that the ALU-bound steps (near field, gridding, gathering) are
+ * reported against.  Synchronous; allocates 8 bytes of device memory for the
+ * duration of the call.
+ */
+sog_status sog_measure_fma_peak(int32_t precision, double* tflops);
 
 /*
  * Batches of independent systems (row "batching" of the hot path; the paper

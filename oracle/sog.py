@@ -237,28 +237,33 @@ def cheb_nodes(P: int, Lz: float):
     return 0.5 * Lz * np.cos((c - 0.5) * PI / P)
 
 
-def lagrange(zc, z):
+def lagrange(zc, z, deriv=True):
     """Lagrange basis L_c(z) on the nodes zc and its z-derivative, from the
     product formula L_c(z) = prod_{k != c} (z - z_k)/(z_c - z_k); at a point
-    that is not a node, L_c'(z) = L_c(z) sum_{k != c} 1/(z - z_k)."""
+    that is not a node, L_c'(z) = L_c(z) sum_{k != c} 1/(z - z_k).  Returns
+    (n, P) arrays (views of per-node rows); the derivative is None unless
+    ``deriv``."""
     zc = np.asarray(zc, dtype=np.float64)
     z = np.asarray(z, dtype=np.float64)
     P = zc.size
-    L = np.ones((z.size, P))
-    dL = np.zeros((z.size, P))
-    diff = z[:, None] - zc[None, :]                       # (n, P)
+    L = np.ones((P, z.size))
+    diff = z[None, :] - zc[:, None]                       # (P, n)
     for c in range(P):
         for k in range(P):
             if k != c:
-                L[:, c] *= diff[:, k] / (zc[c] - zc[k])
-    on_node = np.any(diff == 0.0, axis=1)
+                L[c] *= diff[k] / (zc[c] - zc[k])
+    if not deriv:
+        return L.T, None
+    dL = np.zeros((P, z.size))
+    on_node = np.any(diff == 0.0, axis=0)
     with np.errstate(divide="ignore", invalid="ignore"):
         for c in range(P):
             acc = np.zeros(z.size)
             for k in range(P):
                 if k != c:
-                    acc += 1.0 / diff[:, k]
-            dL[:, c] = L[:, c] * acc
+                    acc += 1.0 / diff[k]
+            dL[c] = L[c] * acc
+    L, dL = L.T, dL.T
     # derivative exactly at a node: sum over the product rule explicitly
     for i in np.nonzero(on_node)[0]:
         for c in range(P):
@@ -450,6 +455,21 @@ def select_params(N: int, Lx: float, Ly: float, Lz: float, tol: float,
 # Near field (Eq. 2.28) and self term
 # ---------------------------------------------------------------------------
 
+def _wrap_xy(prm, r):
+    """READING: the box of Sec. 2.1 is half-open in x and y; a coordinate
+    outside [-L/2, L/2) is taken modulo one period (x = +Lx/2 becomes
+    -Lx/2).  Periodic sums do not depend on it, but the grid coordinate a
+    window is centred on does, to the last bit."""
+    r = np.array(r, dtype=np.float64, copy=True)
+    for d in (0, 1):
+        h = 0.5 * prm["L"][d]
+        hi = r[:, d] >= h
+        r[hi, d] -= prm["L"][d]
+        lo = r[:, d] < -h
+        r[lo, d] += prm["L"][d]
+    return r
+
+
 def _targets(r, tgt):
     N = r.shape[0]
     if tgt is None:
@@ -550,7 +570,7 @@ def mid_range(prm, q, r, tgt=None):
     """Algorithm 1: gridding, forward FFT, scaling, backward FFT, gathering
     (Eq. 3.7, 3.8, 3.10).  Returns Phi^mid and its gradient at the targets."""
     q = np.asarray(q, dtype=np.float64)
-    r = np.asarray(r, dtype=np.float64)
+    r = _wrap_xy(prm, r)
     tgt, tr = _targets(r, tgt)
     if prm["m"] < 0:
         return np.zeros(tgt.size), np.zeros((tgt.size, 3))
@@ -603,7 +623,7 @@ def long_range(prm, q, r, tgt=None):
     if prm.get("long_direct", False):
         return long_range_direct(prm, q, r, tgt)
     q = np.asarray(q, dtype=np.float64)
-    r = np.asarray(r, dtype=np.float64)
+    r = _wrap_xy(prm, r)
     tgt, tr = _targets(r, tgt)
     if prm["m"] >= prm["M"]:
         return np.zeros(tgt.size), np.zeros((tgt.size, 3))
@@ -614,7 +634,7 @@ def long_range(prm, q, r, tgt=None):
     zc = cheb_nodes(P, Lz)
     win = make_window(prm["window"], prm["P_long"], prm["shape_long"])
     # gridding with anterpolation weights q_j L_c(z_j)
-    Ls, _ = lagrange(zc, r[:, 2])
+    Ls, _ = lagrange(zc, r[:, 2], deriv=False)
     gx, wx, _ = win.weights((r[:, 0] + Lx / 2) / hx)
     gy, wy, _ = win.weights((r[:, 1] + Ly / 2) / hy)
     gx %= Ilx
@@ -634,8 +654,27 @@ def long_range(prm, q, r, tgt=None):
     W2 = Wx[:, None] * Wy[None, :]
     mu = np.fft.fft2(Q) * (hx * hy) / W2[None]               # mu_c(k)
     k2 = kx[:, None] ** 2 + ky[None, :] ** 2
-    Kmat = long_kernel(prm, k2[:, :, None, None], zc[None, None, :, None] - zc[None, None, None, :])
-    nu = np.einsum("xyab,bxy->axy", Kmat, mu)
+    # nu_c(k) = sum_c' K_k(z_c - z_c') mu_c'(k), K_k of Eq. 4.40 (long_kernel),
+    # summed Gaussian by Gaussian: term l is w_l s_l^2 e^{-s_l^2 k^2/4} times
+    # the P x P matrix e^{-(z_c - z_c')^2/s_l^2} applied to mu(k) (the same sum,
+    # without forming one P x P matrix per mode)
+    w, s = sog_weights(prm["b"], prm["sigma"], prm["omega"], prm["M"])
+    d = zc[:, None] - zc[None, :]
+    # modes in order of |k|^2: the modes where a Gaussian's factor has not
+    # underflowed to 0 are then a prefix, and the rest (exact zeros) is skipped
+    order = np.argsort(k2.ravel(), kind="stable")
+    k2s = k2.ravel()[order]
+    mus = mu.reshape(P, -1)[:, order]
+    nus = np.zeros_like(mus)
+    for l in range(prm["m"] + 1, prm["M"] + 1):
+        Ez = np.exp(-d * d / s[l] ** 2)
+        a = w[l] * s[l] ** 2 * np.exp(-s[l] ** 2 * k2s / 4.0)
+        nz = np.flatnonzero(a)
+        cnt = nz[-1] + 1 if nz.size else 0
+        nus[:, :cnt] += a[:cnt][None] * (Ez @ mus[:, :cnt])
+    nu = np.empty_like(nus)
+    nu[:, order] = nus
+    nu = nu.reshape(mu.shape)
     nu[:, 0, 0] = 0.0
     A = Lx * Ly
     u = np.fft.ifft2(nu * (PI / A) * (hx * hy) / W2[None]).real * (Ilx * Ily)
@@ -671,7 +710,7 @@ def long_range_direct(prm, q, r, tgt=None):
         nu_c(k) = (pi/A) sum_c' K_k(z_c - z_c') mu_c'(k)      (Eq. 3.13 / 4.40)
         Phi_i   = Re sum_k e^{ik.rho_i} sum_c L_c(z_i) nu_c(k)  (gathering)."""
     q = np.asarray(q, dtype=np.float64)
-    r = np.asarray(r, dtype=np.float64)
+    r = _wrap_xy(prm, r)
     tgt, tr = _targets(r, tgt)
     if prm["m"] >= prm["M"]:
         return np.zeros(tgt.size), np.zeros((tgt.size, 3))
@@ -683,7 +722,7 @@ def long_range_direct(prm, q, r, tgt=None):
     ky = 2 * PI * ny[keep] / Ly
     P = prm["P_cheb"]
     zc = cheb_nodes(P, Lz)
-    Ls, _ = lagrange(zc, r[:, 2])
+    Ls, _ = lagrange(zc, r[:, 2], deriv=False)
     phase = np.exp(-1j * (np.outer(r[:, 0], kx) + np.outer(r[:, 1], ky)))   # (N, modes)
     mu = (phase * q[:, None]).T @ Ls                                         # (modes, P)
     Kmat = long_kernel(prm, (kx ** 2 + ky ** 2)[:, None, None],
@@ -728,7 +767,7 @@ def long_k0(prm, q, r, tgt=None):
     K0 = np.zeros((P, P))
     for l in range(prm["m"] + 1, prm["M"] + 1):
         K0 -= w[l] * d * d * phi1(d * d / s[l] ** 2)
-    Ls, _ = lagrange(zc, r[:, 2])
+    Ls, _ = lagrange(zc, r[:, 2], deriv=False)
     mu = np.array([math.fsum(q * Ls[:, c]) for c in range(P)])
     nu = (PI / (Lx * Ly)) * (K0 @ mu)
     Lt, dLt = lagrange(zc, tr[:, 2])

@@ -16,7 +16,7 @@ SOG_WIN_ES, SOG_WIN_GAUSS, SOG_WIN_KB = 0, 1, 2
 _WIN_NAMES = {SOG_WIN_ES: "es", SOG_WIN_GAUSS: "gauss", SOG_WIN_KB: "kb"}
 
 STATUS = {0: "SOG_OK", 1: "SOG_ERR_ARG", 2: "SOG_ERR_NONNEUTRAL", 3: "SOG_ERR_OUT_OF_BOX",
-          4: "SOG_ERR_NOMEM", 5: "SOG_ERR_CUDA", 6: "SOG_ERR_PARAMS"}
+          4: "SOG_ERR_NOMEM", 5: "SOG_ERR_CUDA", 6: "SOG_ERR_PARAMS", 7: "SOG_ERR_TIMEOUT"}
 
 
 class SogParams(ctypes.Structure):
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = False):
     L.sog_plan_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.sog_plan_launches.argtypes = [vp]
     L.sog_plan_launches.restype = i64
+    L.sog_measure_fma_peak.argtypes = [i32, ctypes.POINTER(d)]
     L.sog_status_str.argtypes = [ctypes.c_int]
     L.sog_status_str.restype = ctypes.c_char_p
     L.sog_assemble_noalloc.argtypes = [i64, i32, ctypes.POINTER(SogParams), vp, vp, vp, vp, vp,
@@ -216,6 +217,14 @@ def sog_assemble_noalloc(params, q, phi_parts, grad_parts=None, phi=None, E=None
                                        _ptr(F), _stream_ptr(stream)), "sog_assemble_noalloc")
 
 
+def sog_measure_fma_peak(precision=SOG_PREC_MIXED) -> float:
+    """Measured FMA rate of the current device in TFLOP/s (FP32 for
+    SOG_PREC_MIXED, FP64 for SOG_PREC_FP64)."""
+    out = ctypes.c_double()
+    _check(load().sog_measure_fma_peak(int(precision), ctypes.byref(out)), "sog_measure_fma_peak")
+    return float(out.value)
+
+
 def _stream_ptr(stream):
     import torch
     if stream is None:
@@ -308,8 +317,11 @@ class Plan:
     # long range by direct sums (Algorithm 3): moments, coefficients, evaluation
     STAGES_DIRECT = STAGES[:5] + ("long_moments", "long_coeffs", "long_eval") + STAGES[8:]
 
-    def set_timing(self, enable: bool):
-        _check(self._lib.sog_plan_set_timing(self._h, int(bool(enable))), "sog_plan_set_timing")
+    def set_timing(self, enable):
+        """False/0: off; True/1: stage events in the concurrent evaluation;
+        2: stages run one after another on the caller's stream (isolated
+        durations)."""
+        _check(self._lib.sog_plan_set_timing(self._h, int(enable)), "sog_plan_set_timing")
 
     def timing(self) -> dict:
         """Device milliseconds of each stage of the last evaluation."""

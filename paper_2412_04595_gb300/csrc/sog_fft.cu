@@ -39,6 +39,9 @@ template <typename T> struct C2;
 template <> struct C2<float> { using t = float2; using tw = TwF; };
 template <> struct C2<double> { using t = double2; using tw = TwD; };
 
+// Threads of the fused y pass of Algorithm 2 (one CTA per SM).
+constexpr int kYpassThreads = 1024;
+
 // Threads per CTA, complex values a thread holds in a stage, and CTAs per
 // SM the register budget is sized for: FP32 runs two CTAs of 512 threads per
 // SM (one CTA's barriers overlap the other's work), FP64 one of 1024.
@@ -72,6 +75,79 @@ __device__ __forceinline__ float2 cmul_tw(float2 a, TwF w, bool inv) {
 __device__ __forceinline__ double2 cmul_tw(double2 a, TwD w, bool inv) {
   const double sh = inv ? -w.y : w.y;
   return double2{a.x * w.x - a.y * sh, a.x * sh + a.y * w.x};
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous copies.  cp.async moves 4, 8 or 16 bytes per thread without
+// blocking, so a CTA keeps its whole tile's loads in flight at once;
+// cp.async.bulk (the TMA's bulk copy) moves a contiguous block, completing on
+// an mbarrier (loads) or a bulk group (stores).
+// ---------------------------------------------------------------------------
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else if constexpr (BYTES == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+// Bulk copy global -> shared of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completing on bar.
+__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned bytes,
+                                         unsigned long long* bar) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const unsigned ba = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(sa), "l"(gmem), "r"(bytes), "r"(ba)
+      : "memory");
+}
+// Wait for phase `phase` of bar to complete, at most kMbarSpins polls; false
+// when the limit ran out.
+constexpr long kMbarSpins = 1L << 24;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned phase) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  for (long it = 0; it < kMbarSpins; ++it) {
+    unsigned done = 0;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// Bulk copy shared -> global (sizes and alignment as bulk_g2s), then wait
+// until the shared memory has been read (the issuing thread only).
+__device__ __forceinline__ void bulk_s2g_wait(void* gmem, const void* smem, unsigned bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gmem),
+               "r"(sa), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// Make this thread's generic-proxy shared-memory writes visible to the bulk
+// copies (the async proxy).
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
 // floor(a / b) for 0 <= a < 2^22 from rb = 1/b rounded to float: the
@@ -212,8 +288,48 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
 #pragma unroll
       for (int k2 = 0; k2 < 5; ++k2) x[k1 + 3 * k2] = v[k2];
     }
+  } else if constexpr (R == 7) {
+    // w = e^(-2 pi i / 7): with t_k = x_k + x_(7-k), d_k = x_k - x_(7-k) and
+    // c_k = cos(2 pi k / 7), s_k = sin(2 pi k / 7),
+    //   y_1 = x_0 + c1 t1 + c2 t2 + c3 t3 - i (s1 d1 + s2 d2 + s3 d3),
+    //   y_2 = x_0 + c2 t1 + c3 t2 + c1 t3 - i (s2 d1 - s3 d2 - s1 d3),
+    //   y_3 = x_0 + c3 t1 + c1 t2 + c2 t3 - i (s3 d1 - s1 d2 + s2 d3),
+    //   y_(7-k) the same with + i (constants as value plus rounding error)
+    const T2 t1 = cadd(x[1], x[6]), t2 = cadd(x[2], x[5]), t3 = cadd(x[3], x[4]);
+    const T2 d1 = csub(x[1], x[6]), d2 = csub(x[2], x[5]), d3 = csub(x[3], x[4]);
+#define SOG_C1(v) mulc(v, 6.234897971e-01f, 4.743407445e-09f, 0.6234898018587336)
+#define SOG_C2(v) mulc(v, -2.225209326e-01f, -1.401115668e-09f, -0.22252093395631434)
+#define SOG_C3(v) mulc(v, -9.009688497e-01f, -1.824345297e-08f, -0.900968867902419)
+#define SOG_S1(v) mulc(v, 7.818315029e-01f, -2.044639835e-08f, 0.7818314824680298)
+#define SOG_S2(v) mulc(v, 9.749279022e-01f, 9.960143821e-09f, 0.9749279121818236)
+#define SOG_S3(v) mulc(v, 4.338837266e-01f, 1.252072579e-08f, 0.43388373911755823)
+    const T2 a1 = T2{x[0].x + SOG_C1(t1.x) + SOG_C2(t2.x) + SOG_C3(t3.x),
+                     x[0].y + SOG_C1(t1.y) + SOG_C2(t2.y) + SOG_C3(t3.y)};
+    const T2 a2 = T2{x[0].x + SOG_C2(t1.x) + SOG_C3(t2.x) + SOG_C1(t3.x),
+                     x[0].y + SOG_C2(t1.y) + SOG_C3(t2.y) + SOG_C1(t3.y)};
+    const T2 a3 = T2{x[0].x + SOG_C3(t1.x) + SOG_C1(t2.x) + SOG_C2(t3.x),
+                     x[0].y + SOG_C3(t1.y) + SOG_C1(t2.y) + SOG_C2(t3.y)};
+    const T2 b1 = T2{SOG_S1(d1.x) + SOG_S2(d2.x) + SOG_S3(d3.x),
+                     SOG_S1(d1.y) + SOG_S2(d2.y) + SOG_S3(d3.y)};
+    const T2 b2 = T2{SOG_S2(d1.x) - SOG_S3(d2.x) - SOG_S1(d3.x),
+                     SOG_S2(d1.y) - SOG_S3(d2.y) - SOG_S1(d3.y)};
+    const T2 b3 = T2{SOG_S3(d1.x) - SOG_S1(d2.x) + SOG_S2(d3.x),
+                     SOG_S3(d1.y) - SOG_S1(d2.y) + SOG_S2(d3.y)};
+#undef SOG_C1
+#undef SOG_C2
+#undef SOG_C3
+#undef SOG_S1
+#undef SOG_S2
+#undef SOG_S3
+    x[0] = cadd(x[0], cadd(cadd(t1, t2), t3));
+    x[1] = pm_i(a1, b1, inv);
+    x[6] = pm_i(a1, b1, !inv);
+    x[2] = pm_i(a2, b2, inv);
+    x[5] = pm_i(a2, b2, !inv);
+    x[3] = pm_i(a3, b3, inv);
+    x[4] = pm_i(a3, b3, !inv);
   } else {
-    // other odd radix (7): y_q = sum_p x_p w^(qp), w = exp(-+2 pi i / R) from
+    // other odd radix: y_q = sum_p x_p w^(qp), w = exp(-+2 pi i / R) from
     // the length-n table (entry (qp mod R) n / R)
     const int step = n / R;
     T2 y[R];
@@ -409,15 +525,18 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
     for (int id = threadIdx.x; id < np * Ix; id += blockDim.x) {
       const int p = fdiv(id, rI), x = id - p * Ix;
       const T* r0 = pl + (size_t)(2 * p) * pitch + x;
-      buf[id] = T2{r0[0], r0[pitch]};
+      cp_async<sizeof(T)>(&buf[id].x, r0);
+      cp_async<sizeof(T)>(&buf[id].y, r0 + pitch);
     }
+    cp_async_wait();
     __syncthreads();
     fft_lines<T2, CAP>(buf, xs, fx, twx, false);
     split_pairs<T2, CAP>(buf, Ix, np);
     fft_lines<T2, CAP>(buf, ys, fy, twy, false);
     for (int id = threadIdx.x; id < Iy * C; id += blockDim.x) plc[id] = buf[id];
   } else {
-    for (int id = threadIdx.x; id < Iy * C; id += blockDim.x) buf[id] = plc[id];
+    for (int id = threadIdx.x; id < Iy * C; id += blockDim.x) cp_async<sizeof(T2)>(buf + id, plc + id);
+    cp_async_wait();
     __syncthreads();
     fft_lines<T2, CAP>(buf, ys, fy, twy, true);
     join_pairs<T2, CAP>(buf, Ix, np);
@@ -434,10 +553,15 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
 }
 
 // x pass alone: rows 2p, 2p+1 (pitch Ix + 2) of pairs p0 .. p0 + B - 1.
+// With tdata, the half spectrum lives there transposed instead of in place:
+// column f of row y of plane n at tdata[f * NR + R'], R' = (i + par np0) Iy
+// + y for n = 2 i + par (planes of each parity contiguous within a column),
+// written by the forward pass and read by the backward pass.
 template <typename T>
 __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
     k_fft_rows(T* __restrict__ data, FftLen fx, const typename C2<T>::tw* __restrict__ twg,
-               int npairs, int B, bool inv) {
+               int npairs, int B, bool inv, typename C2<T>::t* __restrict__ tdata, long NR,
+               int Iy, int np0) {
   using T2 = typename C2<T>::t;
   constexpr int CAP = FftCfg<T>::cap;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -455,20 +579,44 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
     for (int id = threadIdx.x; id < nl * Ix; id += blockDim.x) {
       const int p = fdiv(id, rI), x = id - p * Ix;
       const T* r0 = base + (size_t)(2 * p) * pitch + x;
-      buf[id] = T2{r0[0], r0[pitch]};
+      cp_async<sizeof(T)>(&buf[id].x, r0);
+      cp_async<sizeof(T)>(&buf[id].y, r0 + pitch);
     }
+    cp_async_wait();
     __syncthreads();
     fft_lines<T2, CAP>(buf, xs, fx, twx, false);
     split_pairs<T2, CAP>(buf, Ix, nl);
+    if (tdata) {
+      // consecutive threads take consecutive rows of one column: runs of
+      // contiguous elements in the transposed layout
+      const float r2 = 1.f / (float)(2 * nl), rIy = 1.f / (float)Iy;
+      for (int id = threadIdx.x; id < 2 * nl * C; id += blockDim.x) {
+        const int f = fdiv(id, r2), y = id - f * 2 * nl;
+        const int R = 2 * p0 + y, n = fdiv(R, rIy), yy = R - n * Iy;
+        tdata[(size_t)f * NR + (size_t)((n >> 1) + (n & 1) * np0) * Iy + yy] = buf[y * C + f];
+      }
+      return;
+    }
     for (int id = threadIdx.x; id < 2 * nl * C; id += blockDim.x) {
       const int y = fdiv(id, rC), f = id - y * C;
       reinterpret_cast<T2*>(base + (size_t)y * pitch)[f] = buf[id];
     }
   } else {
-    for (int id = threadIdx.x; id < 2 * nl * C; id += blockDim.x) {
-      const int y = fdiv(id, rC), f = id - y * C;
-      buf[id] = reinterpret_cast<const T2*>(base + (size_t)y * pitch)[f];
+    if (tdata) {
+      const float r2 = 1.f / (float)(2 * nl), rIy = 1.f / (float)Iy;
+      for (int id = threadIdx.x; id < 2 * nl * C; id += blockDim.x) {
+        const int f = fdiv(id, r2), y = id - f * 2 * nl;
+        const int R = 2 * p0 + y, n = fdiv(R, rIy), yy = R - n * Iy;
+        cp_async<sizeof(T2)>(buf + y * C + f,
+                             tdata + (size_t)f * NR + (size_t)((n >> 1) + (n & 1) * np0) * Iy + yy);
+      }
+    } else {
+      for (int id = threadIdx.x; id < 2 * nl * C; id += blockDim.x) {
+        const int y = fdiv(id, rC), f = id - y * C;
+        cp_async<sizeof(T2)>(buf + id, reinterpret_cast<const T2*>(base + (size_t)y * pitch) + f);
+      }
     }
+    cp_async_wait();
     __syncthreads();
     join_pairs<T2, CAP>(buf, Ix, nl);
     fft_lines<T2, CAP>(buf, xs, fx, twx, true);
@@ -506,8 +654,9 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
   const float rl = 1.f / (float)nl;
   for (int id = threadIdx.x; id < nl * n; id += blockDim.x) {
     const int i = fdiv(id, rl), c = id - i * nl;
-    buf[id] = base[(size_t)i * es + c];
+    cp_async<sizeof(T2)>(buf + id, base + (size_t)i * es + c);
   }
+  cp_async_wait();
   __syncthreads();
   const LineSet cs{n, nl, 1, nl, true};
   fft_lines<T2, CAP>(buf, cs, f, tw, mult ? false : inv);
@@ -525,6 +674,166 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
     const int i = fdiv(id, rl), c = id - i * nl;
     base[(size_t)i * es + c] = buf[id];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2, z-contraction (Eq. 3.13 / 4.40 in the Chebyshev basis of the
+// proxy planes), factorised over the long-range Gaussians l = m+1..M:
+//   nu_n(k) = fx(kx) fy(ky) sum_l c1_l e^{-c2_l |k|^2} sum_n' B_l[n][n'] mu_n'(k)
+// with B_l = C^T E_l C, E_l[c][c'] = e^{-(z_c - z_c')^2 / s_l^2}.  B_l[n][n']
+// is zero when n + n' is odd (the proxy points are symmetric about z = 0),
+// so orders of each parity form their own block (row stride pst, zero
+// padded).  s_l grows with l: once c2_l |k|^2 > 80 that term and every later
+// one is below e^-80 of the earlier ones, and the sum stops.  No per-mode
+// matrix is stored.
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T dexp_(T x);
+template <>
+__device__ __forceinline__ float dexp_(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double dexp_(double x) { return exp(x); }
+
+// One mode, one parity block: orders n = 2 i + par, i < np; get(i) returns
+// mu_n, put(i, v) stores nu_n.  PH bounds np; the outputs are computed OH at
+// a time (inputs held in registers, the exponentials recomputed per chunk).
+template <typename T, int PH, int OH, typename GET, typename PUT>
+__device__ __forceinline__ void long_contract_parity(GET get, PUT put, int np, int par, int ps,
+                                                     int pst, int nl, const T* __restrict__ lbl,
+                                                     const typename C2<T>::t* __restrict__ lcl,
+                                                     T k2, T fac) {
+  using T2 = typename C2<T>::t;
+  T2 v[PH];
+#pragma unroll
+  for (int i = 0; i < PH; ++i) v[i] = i < np ? get(i) : T2{T(0), T(0)};
+#pragma unroll 1
+  for (int i0 = 0; i0 < np; i0 += OH) {
+    T2 acc[OH];
+#pragma unroll
+    for (int o = 0; o < OH; ++o) acc[o] = T2{T(0), T(0)};
+#pragma unroll 1
+    for (int l = 0; l < nl; ++l) {
+      const T2 c = lcl[l];
+      const T x = c.y * k2;
+      if (x > T(80)) break;
+      const T a = fac * c.x * dexp_(-x);
+      const T* B = lbl + ((size_t)l * 2 + par) * ps * pst + (size_t)i0 * pst;
+#pragma unroll
+      for (int o = 0; o < OH; ++o) {
+        if (i0 + o < np) {
+          const T* Bi = B + o * pst;
+          T tx = T(0), ty = T(0);
+#pragma unroll
+          for (int j = 0; j < PH; ++j) {
+            if (j < np) {
+              const T b = __ldg(Bi + j);
+              tx = fma(b, v[j].x, tx);
+              ty = fma(b, v[j].y, ty);
+            }
+          }
+          acc[o].x = fma(a, tx, acc[o].x);
+          acc[o].y = fma(a, ty, acc[o].y);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < OH; ++o)
+      if (i0 + o < np) put(i0 + o, acc[o]);
+  }
+}
+
+// Contraction in place on the half spectra of the P proxy planes (layout
+// [n][y][c], plane stride Iy C complex): a thread per mode (y, c); the k = 0
+// mode is zeroed (it is the separate FP64 step).
+template <typename T, int PH>
+__global__ void __launch_bounds__(128)
+    k_long_contract(typename C2<T>::t* __restrict__ A, int P, int Iy, int C,
+                    const T* __restrict__ lbl, const typename C2<T>::t* __restrict__ lcl,
+                    const typename C2<T>::t* __restrict__ lfx,
+                    const typename C2<T>::t* __restrict__ lfy, int nl, int ps, int pst) {
+  using T2 = typename C2<T>::t;
+  const int mode = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mode >= Iy * C) return;
+  const int y = mode / C, c = mode - y * C;
+  const size_t pstr = (size_t)Iy * C;
+  T2* a = A + mode;
+  if (mode == 0) {
+    for (int n = 0; n < P; ++n) a[n * pstr] = T2{T(0), T(0)};
+    return;
+  }
+  const T2 fx = lfx[c], fy = lfy[y];
+#pragma unroll 1
+  for (int par = 0; par < 2; ++par)
+    long_contract_parity<T, PH, PH>([&](int i) { return a[(2 * i + par) * pstr]; },
+                                [&](int i, T2 v) { a[(2 * i + par) * pstr] = v; },
+                                (P + 1 - par) / 2, par, ps, pst, nl, lbl, lcl, fx.x + fy.x,
+                                fx.y * fy.y);
+}
+
+// Fused y pass of Algorithm 2 for one half-spectrum column c and one parity
+// par of the Chebyshev order (orders of different parity do not couple in the
+// contraction): the np planes n = 2 i + par of the column (transposed layout
+// [c][par][i][y], written by the x pass) are brought into shared memory by
+// bulk copies, the np forward y FFTs run in one pass of the engine, then the
+// contraction (a thread per mode y, four outputs at a time), the backward y
+// FFTs, and one bulk copy writes the block back in place.  A bulk copy that
+// does not complete within the bounded wait sets bit 2 of *status and the
+// CTA returns.
+template <typename T, int PH>
+__global__ void __launch_bounds__(kYpassThreads, 1)
+    k_long_ypass(typename C2<T>::t* __restrict__ data, FftLen fy,
+                 const typename C2<T>::tw* __restrict__ twg, int P,
+                 const T* __restrict__ lbl, const typename C2<T>::t* __restrict__ lcl,
+                 const typename C2<T>::t* __restrict__ lfx,
+                 const typename C2<T>::t* __restrict__ lfy, int nl, int ps, int pst,
+                 int* __restrict__ status) {
+  using T2 = typename C2<T>::t;
+  using T4 = typename C2<T>::tw;
+  constexpr int CAP = FftCfg<T>::cap;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  __shared__ __align__(8) unsigned long long bar;
+  T2* buf = reinterpret_cast<T2*>(smraw);
+  const int c = blockIdx.x >> 1, par = blockIdx.x & 1, Iy = fy.n;
+  const int np0 = (P + 1) / 2, np = par ? P / 2 : np0;
+  const int tot = np * Iy;
+  T4* tw = reinterpret_cast<T4*>(buf + (size_t)np0 * Iy);
+  T2* blk = data + (size_t)c * P * Iy + (size_t)(par ? np0 : 0) * Iy;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    const unsigned bytes = (unsigned)(tot * sizeof(T2));
+    mbar_expect_tx(&bar, bytes);
+    for (unsigned o = 0; o < bytes; o += 32768u)
+      bulk_g2s(reinterpret_cast<char*>(buf) + o, reinterpret_cast<const char*>(blk) + o,
+               bytes - o < 32768u ? bytes - o : 32768u, &bar);
+  }
+  for (int i = threadIdx.x; i < Iy; i += blockDim.x) tw[i] = twg[fy.tw_off + i];
+  __syncthreads();
+  if (!mbar_wait(&bar, 0)) {
+    if (threadIdx.x == 0) atomicOr(status, 4);
+    // the copy may still land in this CTA's shared memory: wait once more, bounded
+    mbar_wait(&bar, 0);
+    return;
+  }
+  const LineSet ls{Iy, np, Iy, 1, false};
+  fft_lines<T2, CAP>(buf, ls, fy, tw, false);
+  const T2 fx = lfx[c];
+  for (int y = threadIdx.x; y < Iy; y += blockDim.x) {
+    T2* a = buf + y;
+    if (c == 0 && y == 0) {
+      for (int i = 0; i < np; ++i) a[i * Iy] = T2{T(0), T(0)};
+      continue;
+    }
+    const T2 fyv = lfy[y];
+    long_contract_parity<T, PH, 4>([&](int i) { return a[i * Iy]; },
+                                   [&](int i, T2 v) { a[i * Iy] = v; }, np, par, ps, pst, nl, lbl,
+                                   lcl, fx.x + fyv.x, fx.y * fyv.y);
+  }
+  __syncthreads();
+  fft_lines<T2, CAP>(buf, ls, fy, tw, true);
+  fence_async_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) bulk_s2g_wait(blk, buf, (unsigned)(tot * sizeof(T2)));
 }
 
 // True when a whole Ix x Iy plane fits one CTA of k_fft_plane with nt
@@ -564,7 +873,8 @@ static cudaError_t launch_plane(T* data, const FftLen& fx, const FftLen& fy, con
 
 template <typename T>
 static cudaError_t launch_rows(T* data, const FftLen& fx, const void* tw, int nrows, bool inv,
-                               cudaStream_t s) {
+                               cudaStream_t s, typename C2<T>::t* tdata = nullptr, int Iy = 1,
+                               int np0 = 0) {
   using T2 = typename C2<T>::t;
   constexpr int CAP = FftCfg<T>::cap;
   const int npairs = nrows / 2;
@@ -576,7 +886,7 @@ static cudaError_t launch_rows(T* data, const FftLen& fx, const void* tw, int nr
   const size_t sm = (size_t)fx.n * sizeof(T4) + (size_t)B * std::max(fx.n, 2 * C) * sizeof(T2);
   const int grid = (npairs + B - 1) / B;
   k_fft_rows<T><<<grid, NT, sm, s>>>(data, fx, reinterpret_cast<const T4*>(tw), npairs,
-                                              B, inv);
+                                              B, inv, tdata, (long)nrows, Iy, np0);
   return cudaGetLastError();
 }
 
@@ -635,16 +945,74 @@ cudaError_t fft_mid_forward_conv_inverse(const sog_plan* p, cudaStream_t s, int&
 template cudaError_t fft_mid_forward_conv_inverse<float>(const sog_plan*, cudaStream_t, int&);
 template cudaError_t fft_mid_forward_conv_inverse<double>(const sog_plan*, cudaStream_t, int&);
 
-// Algorithm 2 steps 2 and 4: 2D FFTs of the Chebyshev proxy planes (layout
-// [n][y][x], pitch Ix_long + 2), forward on d_lA (inv = false) or backward
-// on d_lB.
-template <typename T>
-cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s, int& launches) {
-  T* g = reinterpret_cast<T*>(inv ? p->d_lB : p->d_lA);
-  return fft_planes<T>(g, p->flx, p->fly, p->d_tw, p->prm.P_cheb, inv, s, launches);
+// FP32 plans: one parity block of a column (ceil(P/2) Iy complex values) and
+// the y twiddles must fit the shared memory of one CTA, the block's lines one
+// pass of the engine, and the block the register budget (P <= 32).  FP64
+// plans use the separate passes.
+bool long_fused_fits(int P, const FftLen& fy, size_t es) {
+  const int np0 = (P + 1) / 2;
+  return es == sizeof(float) && P <= 32 &&
+         (size_t)np0 * fy.n * sizeof(float2) + (size_t)fy.n * sizeof(TwF) + 64 <=
+             (size_t)kMaxDynSmem &&
+         max_lines(fy, FftCfg<float>::cap, kYpassThreads) >= np0;
 }
-template cudaError_t fft_long_pass<float>(const sog_plan*, bool, cudaStream_t, int&);
-template cudaError_t fft_long_pass<double>(const sog_plan*, bool, cudaStream_t, int&);
+
+template <typename T, int PH>
+static void launch_contract(const sog_plan* p, T* A, cudaStream_t s) {
+  using T2 = typename C2<T>::t;
+  const int P = p->prm.P_cheb, Iy = p->prm.I_long[1], C = p->prm.I_long[0] / 2 + 1;
+  const int modes = Iy * C;
+  k_long_contract<T, PH><<<(modes + 127) / 128, 128, 0, s>>>(
+      reinterpret_cast<T2*>(A), P, Iy, C, reinterpret_cast<const T*>(p->d_lbl),
+      reinterpret_cast<const T2*>(p->d_lcl), reinterpret_cast<const T2*>(p->d_lfx),
+      reinterpret_cast<const T2*>(p->d_lfy), p->n_lg, p->lps, p->lpst);
+}
+
+template <typename T, int PH>
+static void launch_ypass(const sog_plan* p, typename C2<T>::t* col, cudaStream_t s) {
+  using T2 = typename C2<T>::t;
+  using T4 = typename C2<T>::tw;
+  const int P = p->prm.P_cheb, C = p->prm.I_long[0] / 2 + 1;
+  const int np0 = (P + 1) / 2;
+  const size_t sm = (size_t)np0 * p->fly.n * sizeof(T2) + (size_t)p->fly.n * sizeof(T4);
+  k_long_ypass<T, PH><<<2 * C, kYpassThreads, sm, s>>>(
+      col, p->fly, reinterpret_cast<const T4*>(p->d_tw), P,
+      reinterpret_cast<const T*>(p->d_lbl), reinterpret_cast<const T2*>(p->d_lcl),
+      reinterpret_cast<const T2*>(p->d_lfx), reinterpret_cast<const T2*>(p->d_lfy), p->n_lg,
+      p->lps, p->lpst, p->d_status);
+}
+
+// Algorithm 2 steps 2-4 on the proxy planes in d_lA.  Fused: x pass with the
+// half spectrum written transposed to d_lB, the y pass / contraction /
+// backward y pass per column, backward x pass back into d_lA.  Otherwise:
+// forward 2D FFTs, the contraction kernel and backward 2D FFTs, in place.
+template <typename T>
+cudaError_t fft_long_solve(const sog_plan* p, cudaStream_t s, int& launches) {
+  using T2 = typename C2<T>::t;
+  T* A = reinterpret_cast<T*>(p->d_lA);
+  const int P = p->prm.P_cheb, Iy = p->prm.I_long[1];
+  const int ph = (P + 1) / 2;
+  cudaError_t e;
+  if constexpr (sizeof(T) == 4) if (p->long_fused) {
+    T2* col = reinterpret_cast<T2*>(p->d_lB);
+    if ((e = launch_rows<T>(A, p->flx, p->d_tw, Iy * P, false, s, col, Iy, ph))) return e;
+    if (ph <= 8) launch_ypass<T, 8>(p, col, s);
+    else launch_ypass<T, 16>(p, col, s);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = launch_rows<T>(A, p->flx, p->d_tw, Iy * P, true, s, col, Iy, ph))) return e;
+    launches += 3;
+    return cudaSuccess;
+  }
+  if ((e = fft_planes<T>(A, p->flx, p->fly, p->d_tw, P, false, s, launches))) return e;
+  if (ph <= 8) launch_contract<T, 8>(p, A, s);
+  else if (ph <= 16) launch_contract<T, 16>(p, A, s);
+  else launch_contract<T, 32>(p, A, s);
+  if ((e = cudaGetLastError())) return e;
+  launches += 1;
+  return fft_planes<T>(A, p->flx, p->fly, p->d_tw, P, true, s, launches);
+}
+template cudaError_t fft_long_solve<float>(const sog_plan*, cudaStream_t, int&);
+template cudaError_t fft_long_solve<double>(const sog_plan*, cudaStream_t, int&);
 
 // True when transforms of this length fit the engine (at least one line per
 // CTA; the x pass also needs its half spectrum to fit one CTA).
@@ -655,6 +1023,16 @@ bool fft_len_ok(int prec, const FftLen& f) {
   const size_t twe = prec == SOG_PREC_FP64 ? sizeof(TwD) : sizeof(TwF);
   return f.n >= 2 && max_lines(f, cap, nt) >= 1 && (f.n / 2 + 1) <= nt * (cap / 2) &&
          (size_t)f.n * twe + (size_t)(f.n + 2) * elem <= (size_t)kMaxDynSmem;
+}
+
+// The largest dynamic shared memory a kernel's static shared memory leaves.
+template <typename K>
+static cudaError_t allow_dyn_smem(K* kernel) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kMaxDynSmem - (int)a.sharedSizeBytes);
 }
 
 // Allow the FFT kernels the dynamic shared memory they may need (set once per
@@ -669,6 +1047,11 @@ cudaError_t fft_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fft_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kMaxDynSmem);
+  if constexpr (sizeof(T) == 4) {
+    // the y pass holds its mbarrier in static shared memory
+    if (e == cudaSuccess) e = allow_dyn_smem(k_long_ypass<T, 8>);
+    if (e == cudaSuccess) e = allow_dyn_smem(k_long_ypass<T, 16>);
+  }
   return e;
 }
 template cudaError_t fft_prepare<float>();

@@ -93,6 +93,7 @@ struct TileGeom {
 constexpr int kTileThreads = 256;  // 8 warps; the spread's row ownership relies on it
 constexpr int kTileBatch = 32;     // particles whose window weights are staged at once
 constexpr int kTileHeader = 896;   // bytes of row tables and per-particle offsets
+constexpr int kLongSpreadHeader = 1024;  // the same for the long-range gridding (P_cheb planes)
 constexpr int kGatherBatch = 128;  // particles per batch of the gathers (two threads each)
 constexpr int kGatherHeader = 1280;
 
@@ -165,7 +166,17 @@ struct sog_plan {
   void* d_tw;          // twiddles, T2
   void* d_near_tab;    // near table, T
   void* d_mult;        // mid scaling factors, T
-  void* d_kmat;        // long z-kernels per mode, T
+  void* d_kmat;        // long z-kernels per half-plane mode (Algorithm 3), T
+  // Algorithm 2 z-kernel in factorised form (no per-mode table):
+  //   K_k = fx(kx) fy(ky) sum_l c1_l e^{-c2_l |k|^2} B_l
+  void* d_lbl;         // B_l, l = m+1..M: even and odd parity blocks [2][lps][lps], T
+  void* d_lcl;         // (c1_l, c2_l) = ((pi/A) w_l s_l^2, s_l^2 / 4), T pairs
+  void* d_lfx;         // (kx^2, hx^2 / What_x(kx)^2) per half-spectrum column, T pairs
+  void* d_lfy;         // (ky^2, hy^2 / What_y(ky)^2) per row, T pairs
+  int n_lg;            // long-range Gaussians M - m
+  int lps;             // parity block edge ceil(P_cheb / 2)
+  int lpst;            // row stride of a parity block (lps rounded up to 4)
+  int long_fused;      // y pass, contraction and inverse y pass in one kernel
   double* d_k0mat;     // k = 0 z-kernel, P x P, double
   void* d_grid;        // mid grid, T
   void* d_lA;          // long planes, T
@@ -183,7 +194,7 @@ struct sog_plan {
   double* d_parts_grad;  // 4 x N x 3
   double* d_red;         // reduction partials
   double* d_k0nu;        // P
-  int* d_status;         // latched data errors (bit 0 non-neutral, bit 1 out of box)
+  int* d_status;         // latched errors (bit 0 non-neutral, bit 1 out of box, bit 2 timeout)
   void* d_host_stage;    // device copies of q, r, phi, F, E for sog_eval_host
   int long_small;        // long planes small enough for one private copy per CTA
   int long_small_blocks;
@@ -223,11 +234,17 @@ void sog_table(double b, double sigma, double omega, int M, std::vector<double>&
 // Each adds the number of kernels it launched to `launches`.
 template <typename T>
 cudaError_t fft_mid_forward_conv_inverse(const sog_plan* p, cudaStream_t s, int& launches);
+// Algorithm 2 steps 2-4 on the proxy planes d_lA (layout [n][y][x], pitch
+// Ix_long + 2): forward 2D FFTs, the factorised z-contraction, backward 2D
+// FFTs; the result is left in d_lA (d_lB is scratch).
 template <typename T>
-cudaError_t fft_long_pass(const sog_plan* p, bool inv, cudaStream_t s, int& launches);
+cudaError_t fft_long_solve(const sog_plan* p, cudaStream_t s, int& launches);
 template <typename T>
 cudaError_t fft_prepare();
 bool fft_len_ok(int prec, const FftLen& f);
+// Whether the fused y pass (all P_cheb planes of one half-spectrum column in
+// one CTA's shared memory) fits, for element size es.
+bool long_fused_fits(int P, const FftLen& fy, size_t es);
 
 // One-time kernel attributes for the plan's element type (sog_kernels.cu).
 cudaError_t prepare_kernels(int prec);

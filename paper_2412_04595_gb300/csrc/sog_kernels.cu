@@ -39,6 +39,7 @@ struct PrepGeom {
   int Tm[3], ntm[3];
   double iTm[3];
   double ihl[2];     // 1 / long grid spacing
+  double h[3], hl[2];  // grid spacings (FP64 plans divide by them, as the oracle does)
   int Tl[2], ntl[2];
   double iTl[2];
   double ihalfLz;
@@ -108,6 +109,14 @@ __host__ WinT<T> wint(const WinPar& w) {
   for (int k = 0; k < kKbTerms; ++k) o.kbc[k] = T(0);
   if (w.kind == SOG_WIN_KB) o.kbn = kb_series<T>((double)o.shape, o.kbc, kKbTerms);
   return o;
+}
+
+// Window argument v = offset / half-width: FP64 divides (bit for bit the
+// oracle's value), FP32 multiplies by the rounded reciprocal.
+template <typename T>
+__device__ __forceinline__ T win_arg(T d, const WinT<T>& w) {
+  if constexpr (sizeof(T) == 8) return d / w.half;
+  else return d * w.inv_half;
 }
 
 __device__ __forceinline__ float dexp(float x) { return expf(x); }
@@ -295,9 +304,12 @@ __device__ void prep_particle(const PrepGeom& g, const T* __restrict__ q, const 
   kl = 0;
   if (g.has_mid) {
     double t[3];
-    t[0] = ((double)c[0] + g.halfL[0]) * g.ih[0];
-    t[1] = ((double)c[1] + g.halfL[1]) * g.ih[1];
-    t[2] = ((double)c[2] + g.Lzs_half) * g.ih[2];
+    // grid coordinates by IEEE division: a particle on a grid line gets
+    // exactly the coordinate the FP64 oracle computes (the ES window's
+    // derivative is unbounded at its support edge, so the last bit matters)
+    t[0] = ((double)c[0] + g.halfL[0]) / g.h[0];
+    t[1] = ((double)c[1] + g.halfL[1]) / g.h[1];
+    t[2] = ((double)c[2] + g.Lzs_half) / g.h[2];
     int tt[3];
     double loc[3];
     for (int d = 0; d < 3; ++d) {
@@ -309,8 +321,8 @@ __device__ void prep_particle(const PrepGeom& g, const T* __restrict__ q, const 
   }
   if (g.has_long) {
     double t[2];
-    t[0] = ((double)c[0] + g.halfL[0]) * g.ihl[0];
-    t[1] = ((double)c[1] + g.halfL[1]) * g.ihl[1];
+    t[0] = ((double)c[0] + g.halfL[0]) / g.hl[0];
+    t[1] = ((double)c[1] + g.halfL[1]) / g.hl[1];
     int tt[2];
     double loc[2];
     for (int d = 0; d < 2; ++d) {
@@ -1013,7 +1025,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
       const P4<T> a = rec[p0 + j];
       const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
       const int g0 = (int)dceil(c - w.half);
-      const T v = win_val<T, PW == 0>(w, ((T)(g0 + k) - c) * w.inv_half);
+      const T v = win_val<T, PW == 0>(w, win_arg(((T)(g0 + k) - c), w));
       wgt[(j * 3 + ax) * kMaxWin + k] = ax == 0 ? v * a.q : v;
       if (r == 0) {
         const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
@@ -1185,13 +1197,13 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
       if (ax0 < 3) {
         const T c = ax0 == 0 ? a.x : (ax0 == 1 ? a.y : a.z);
         const int g0 = ax0 == 0 ? gx0 : (ax0 == 1 ? gy0 : gz0);
-        win_eval<T, PW == 0>(w, ((T)(g0 + k0) - c) * w.inv_half, v, dv);
+        win_eval<T, PW == 0>(w, win_arg(((T)(g0 + k0) - c), w), v, dv);
         wsm[ax0 * kMaxWin + k0] = Cx<T>{v, -dv * w.inv_half};
       }
       if (3 * P > 32 && ax1 < 3) {
         const T c = ax1 == 0 ? a.x : (ax1 == 1 ? a.y : a.z);
         const int g0 = ax1 == 0 ? gx0 : (ax1 == 1 ? gy0 : gz0);
-        win_eval<T, PW == 0>(w, ((T)(g0 + k1) - c) * w.inv_half, v, dv);
+        win_eval<T, PW == 0>(w, win_arg(((T)(g0 + k1) - c), w), v, dv);
         wsm[ax1 * kMaxWin + k1] = Cx<T>{v, -dv * w.inv_half};
       }
     }
@@ -1247,68 +1259,147 @@ __device__ __forceinline__ void cheb_all(T x, int P, T* t) {
 }
 
 // Spread q_j T_n(x_j) W2(rho_g - rho_j) onto the P proxy planes (layout
-// [n][y][x], pitch Ix + 2) through padded tiles; planes zero on entry.  A
-// warp per particle, a lane per Chebyshev index n.
+// [n][y][x], pitch Ix + 2) through padded tiles (Algorithm 2, gridding in the
+// anterpolation reading); planes zero on entry.  As in the mid-range
+// gridding: the padded tile of all P planes is held in shared memory in fixed
+// point (scale from sum |q| of the CTA's charges, so no partial sum
+// overflows; |T_n| <= 1 and the window is at most 1), window values and
+// T_n(x_j) are staged per batch of kTileBatch charges, and a warp takes one
+// charge with its lanes over the (n, dy) rows of the window, P_cheb x P rows
+// in all, 32 at a time; lane s writes word s x RP + dx (mod 32), so a step's
+// 32 rows fall in 32 banks.  The tile is then added to the planes.
 template <typename T, int PW>
-__global__ void __launch_bounds__(256) k_long_spread(TileGeom g, WinT<T> w, int P,
-                                                     const P4<T>* __restrict__ rec,
-                                                     const int* __restrict__ start,
-                                                     T* __restrict__ planes) {
+__global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T> w, int P,
+                                                              const P4<T>* __restrict__ rec,
+                                                              const int* __restrict__ start,
+                                                              T* __restrict__ planes) {
+  using A = typename FixAcc<T>::t;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int tile = blockIdx.x;
-  const int b = start[tile], e = start[tile + 1];
-  const int chunk = blockIdx.y;
-  if (b + chunk >= e) return;
+  int b = start[tile], e = start[tile + 1];
+  if (!chunk_range(b, e, g.chunks)) return;
   const int W0 = g.W[0], W1 = g.W[1];
-  const int ps = W0 * W1 + 1;  // odd plane stride in shared memory
-  const int Wn = P * ps;
-  T* st = reinterpret_cast<T*>(smraw);
-  for (int i = threadIdx.x; i < Wn; i += blockDim.x) st[i] = T(0);
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* ws = st + Wn + warp * (2 * kMaxWin + kMaxCheb);
-  T *wsx = ws, *wsy = ws + kMaxWin, *tn = ws + 2 * kMaxWin;
   const int Pw = PW > 0 ? PW : w.P;
   constexpr int PR = PW > 0 ? PW : kMaxWin;
-  for (int pi = b + chunk + warp * g.chunks; pi < e; pi += nw * g.chunks) {
-    const P4<T> a = rec[pi];
-    const int gx0 = (int)dceil(a.x - w.half), gy0 = (int)dceil(a.y - w.half);
-    if (lane < Pw) {
-      T v, dv;
-      win_eval<T, PW == 0>(w, ((T)(gx0 + lane) - a.x) * w.inv_half, v, dv);
-      wsx[lane] = v;
-      win_eval<T, PW == 0>(w, ((T)(gy0 + lane) - a.y) * w.inv_half, v, dv);
-      wsy[lane] = v * a.q;
-    }
-    if (lane == 0) cheb_all(a.z, P, tn);
-    __syncwarp();
-    T rwx[PR];
-#pragma unroll
-    for (int dx = 0; dx < PR; ++dx) rwx[dx] = dx < Pw ? wsx[dx] : T(0);
-    T* base = st + (gy0 + g.pad_lo) * W0 + gx0 + g.pad_lo;
-    for (int n = lane; n < P; n += 32) {
-      const T t = tn[n];
-      T* pl = base + n * ps;
-      for (int dy = 0; dy < Pw; ++dy) {
-        const T cy = wsy[dy] * t;
-        if (cy == T(0)) continue;
-        T* rp = pl + dy * W0;
-#pragma unroll
-        for (int dx = 0; dx < PR; ++dx)
-          if (dx < Pw) atomicAdd(rp + dx, cy * rwx[dx]);
-      }
-    }
-    __syncwarp();
-  }
-  __shared__ long long zoff[kMaxCheb];
-  __shared__ int yoff[32];
+  const int RP = gather_row_pitch(W0);
+  const int PS = gather_plane_stride(RP, W1, Pw);
+  long long* zoff = reinterpret_cast<long long*>(smraw);            // [kMaxCheb]
+  int* yoff = reinterpret_cast<int*>(zoff + kMaxCheb);             // [32]
+  int* bofs = yoff + 32;                                           // [kTileBatch]
+  T* red = reinterpret_cast<T*>(bofs + kTileBatch);                // [8]
+  T* wgt = reinterpret_cast<T*>(smraw + kLongSpreadHeader);        // [j][2][kMaxWin]
+  T* tnb = wgt + kTileBatch * 2 * kMaxWin;                         // [j][kMaxCheb]
+  A* st = reinterpret_cast<A*>(tnb + kTileBatch * kMaxCheb);
   const int ty = tile / g.nt[0], tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
+  {
+    constexpr int V = 16 / sizeof(A);
+    const int nv = P * PS / V;
+    int4* st4 = reinterpret_cast<int4*>(st);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) st4[i] = make_int4(0, 0, 0, 0);
+    for (int i = nv * V + threadIdx.x; i < P * PS; i += blockDim.x) st[i] = A(0);
+  }
   tile_tables(g, oy, 0, P, true, yoff, zoff);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T qa = 0;
+  for (int i = b + threadIdx.x; i < e; i += blockDim.x) qa += fabs(rec[i].q);
+  qa = warp_sum(qa);
+  if (lane == 0) red[warp] = qa;
   __syncthreads();
+  T qsum = 0;
+  for (int k = 0; k < nw; ++k) qsum += red[k];
+  int ex = 0;
+  frexp(qsum > T(0) ? qsum : T(1), &ex);  // qsum < 2^ex
+  const T S = ldexp(T(1), FixAcc<T>::bits - ex), iS = ldexp(T(1), ex - FixAcc<T>::bits);
+  const int nrows = P * Pw, nit = (nrows + 31) >> 5;
+  for (int p0 = b; p0 < e; p0 += kTileBatch) {
+    const int nb = min(kTileBatch, e - p0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * 2 * Pw; idx += blockDim.x) {
+      const int j = idx / (2 * Pw);
+      const int r = idx - j * 2 * Pw;
+      const int ax = r / Pw, k = r - ax * Pw;
+      const P4<T> a = rec[p0 + j];
+      const T c = ax == 0 ? a.x : a.y;
+      const int g0 = (int)dceil(c - w.half);
+      const T v = win_val<T, PW == 0>(w, win_arg(((T)(g0 + k) - c), w));
+      wgt[(j * 2 + ax) * kMaxWin + k] = ax == 0 ? v * a.q : v;
+      if (r == 0) {
+        const int gy0 = (int)dceil(a.y - w.half);
+        bofs[j] = (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
+      }
+    }
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      // T_n(x_j) by the three-term recurrence (|x_j| <= 1)
+      const T x = rec[p0 + j].z;
+      T t0 = T(1), t1 = x;
+      T* tj = tnb + j * kMaxCheb;
+      for (int n = 0; n < P; ++n) {
+        tj[n] = t0;
+        const T t2 = T(2) * x * t1 - t0;
+        t0 = t1;
+        t1 = t2;
+      }
+    }
+    __syncthreads();
+    for (int j = warp; j < nb; j += nw) {
+      const T* wj = wgt + j * 2 * kMaxWin;
+      const T* tj = tnb + j * kMaxCheb;
+      T rwx[PR];
+#pragma unroll
+      for (int dx = 0; dx < PR; ++dx) rwx[dx] = dx < Pw ? wj[dx] : T(0);
+      A* bj = st + bofs[j];
+      for (int it = 0; it < nit; ++it) {
+        const int s2 = lane + 32 * it;
+        if (s2 < nrows) {
+          const int n = s2 / Pw, dy = s2 - n * Pw;
+          const T c = wj[kMaxWin + dy] * tj[n] * S;
+          A* rp = bj + n * PS + dy * RP;
+#pragma unroll
+          for (int dx = 0; dx < PR; ++dx)
+            if (dx < Pw) fix_add(rp + dx, FixAcc<T>::cvt(c * rwx[dx]));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // add the padded tile to the planes (tiles overlap in their halos)
+  const int nt = blockDim.x;
+  if (sizeof(T) == 4 && ((g.I[0] | g.pitch) & 1) == 0) {
+    // FP32: pairs of columns (x even, x + 1) with one 8-byte atomic, as in
+    // the mid-range gridding; columns outside the tile add zero
+    const int ox0 = ox & ~1;
+    const int W0h = (ox + W0 - ox0 + 1) >> 1, tot = W0h * W1 * P;
+    int lx = threadIdx.x % W0h, rr = threadIdx.x / W0h;
+    int ly = rr % W1, n = rr / W1;
+    const int sx = nt % W0h, sr = nt / W0h, sy = sr % W1, sn = sr / W1;
+    for (int i = threadIdx.x; i < tot; i += nt) {
+      const int c0 = ox0 + 2 * lx - ox;
+      const A* sp = st + n * PS + ly * RP;
+      const A v0 = c0 >= 0 ? sp[c0] : A(0), v1 = c0 + 1 < W0 ? sp[c0 + 1] : A(0);
+      if ((v0 | v1) != 0) {
+        float* gp = reinterpret_cast<float*>(planes) + zoff[n] + yoff[ly] + pmod(ox0 + 2 * lx, g.I[0]);
+        atomicAdd(reinterpret_cast<float2*>(gp), make_float2((float)v0 * (float)iS, (float)v1 * (float)iS));
+      }
+      lx += sx;
+      ly += sy;
+      n += sn;
+      if (lx >= W0h) { lx -= W0h; ++ly; }
+      if (ly >= W1) { ly -= W1; ++n; }
+    }
+    return;
+  }
   const int xw = lane < W0 ? pmod(ox + lane, g.I[0]) : 0;
-  tile_rows<T, false>(planes, st, W0, W1, P, W0, ps, yoff, zoff, xw);
+  int ly = warp, n = 0;
+  while (ly >= W1) { ly -= W1; ++n; }
+  for (int row = warp; row < W1 * P; row += nw) {
+    if (lane < W0) {
+      const A v = st[n * PS + ly * RP + lane];
+      if (v != A(0)) atomicAdd(planes + zoff[n] + yoff[ly] + xw, (T)v * iS);
+    }
+    ly += nw;
+    while (ly >= W1) { ly -= W1; ++n; }
+  }
 }
 
 // Small long-range grids (I_long <= 16, one tile): each CTA takes a slice
@@ -1347,7 +1438,7 @@ __global__ void __launch_bounds__(256) k_long_spread_small(int I0, int I1, WinT<
           T d = (T)k - (ax ? a.y : a.x);
           d -= (T)Id * drint(d * (ax ? iI1 : iI0));
           T v, dv;
-          win_eval<T, true>(w, d * w.inv_half, v, dv);
+          win_eval<T, true>(w, win_arg(d, w), v, dv);
           if (ax) wy[j][k] = v;
           else wx[j][k] = v * a.q;
         }
@@ -1409,37 +1500,14 @@ __global__ void k_long_reduce(const T* __restrict__ partial, int nblk, int I0, i
   }
 }
 
-// Per-mode z-contraction (Eq. 3.17 in the Chebyshev basis): for every 2D
-// mode (fy, fx) with k != 0, out_n = sum_n' K[mode][n][n'] in_n'.
-template <typename T>
-__global__ void k_long_contract(const T* __restrict__ A, T* __restrict__ B, const T* __restrict__ K,
-                                int P, int Iy, int C) {
-  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-  const int mode = blockIdx.x * (blockDim.x / P) + threadIdx.x / P;
-  const int n = threadIdx.x % P;
-  if (threadIdx.x >= (blockDim.x / P) * P) return;
-  if (mode >= Iy * C) return;
-  const T2* a = reinterpret_cast<const T2*>(A);
-  T2* bo = reinterpret_cast<T2*>(B);
-  const size_t ps = (size_t)Iy * C;
-  T2 acc{T(0), T(0)};
-  if (mode != 0) {
-    const T* k = K + ((size_t)mode * P + n) * P;
-    for (int m = 0; m < P; ++m) {
-      const T2 v = a[(size_t)m * ps + mode];
-      const T kk = k[m];
-      acc.x += kk * v.x;
-      acc.y += kk * v.y;
-    }
-  }
-  bo[(size_t)n * ps + mode] = acc;
-}
-
-// Gathering, Eq. (3.19) discretised: Phi_i = sum_n T_n(x_i) sum_g W2 u_n[g].
-// The padded tile of all P proxy planes is loaded into shared memory; 2D
-// window values are staged per batch of particles; two threads per particle
-// each take half of the planes n, with T_n and T_n' from the Chebyshev
-// recurrence, and combine with one shuffle.
+// Gathering, Eq. (3.19) discretised: Phi_i = sum_n T_n(x_i) sum_g W2 u_n[g],
+// with the gradient from W2' in x, y and T_n' in z.  The padded tile of all P
+// planes is loaded into shared memory (odd row pitch RP, plane stride =
+// P_win x RP mod 32).  Window values and T_n, T_n' (three-term recurrences)
+// are staged per batch of kTileBatch charges; a warp takes one charge, its
+// lanes over the (n, dy) rows of the window (lane s reads word s x RP + dx
+// mod 32, 32 banks per step), each lane summing whole x rows; the four sums
+// are combined over the warp at the end.
 template <typename T, int PW>
 __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T> w, int P,
                                                               const P4<T>* __restrict__ rec,
@@ -1454,105 +1522,102 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
   if (!chunk_range(b, e, g.chunks)) return;
   const int W0 = g.W[0], W1 = g.W[1];
   const int Pw = PW > 0 ? PW : w.P;
-  const int PS = W0 * W1;
   constexpr int PR = PW > 0 ? PW : kMaxWin;
-  long long* zoff = reinterpret_cast<long long*>(smraw);
-  int* yoff = reinterpret_cast<int*>(zoff + 64);
-  int* xoff = yoff + 32;
-  int* bofs = xoff + 32;
-  T* wgt = reinterpret_cast<T*>(smraw + kGatherHeader);  // [j][4][Pw]: w, w' for x, y
-  T* st = wgt + kGatherBatch * 4 * Pw;
+  const int RP = gather_row_pitch(W0);
+  const int PS = gather_plane_stride(RP, W1, Pw);
+  long long* zoff = reinterpret_cast<long long*>(smraw);   // [kMaxCheb]
+  int* yoff = reinterpret_cast<int*>(zoff + kMaxCheb);    // [32]
+  int* xoff = yoff + 32;                                  // [32]
+  int* bofs = xoff + 32;                                  // [kTileBatch]
+  T* wgt = reinterpret_cast<T*>(smraw + kLongSpreadHeader);  // [j][4][kMaxWin]: w_x, w_x', w_y, w_y'
+  T* tnb = wgt + kTileBatch * 4 * kMaxWin;                   // [j][2][kMaxCheb]: T_n, T_n'
+  T* st = tnb + kTileBatch * 2 * kMaxCheb;
   const int ty = tile / g.nt[0], tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
   tile_tables(g, oy, 0, P, true, yoff, zoff);
   for (int i = threadIdx.x; i < W0; i += blockDim.x) xoff[i] = pmod(ox + i, g.I[0]);
   __syncthreads();
-  tile_load(planes, st, W0, W1, P, W0, PS, xoff, yoff, zoff);
-  const int j = threadIdx.x >> 1, sl = threadIdx.x & 1;
-  const int n0 = sl ? (P + 1) / 2 : 0, n1 = sl ? P : (P + 1) / 2;
-  for (int p0 = b; p0 < e; p0 += kGatherBatch) {
-    const int nb = min(kGatherBatch, e - p0);
+  tile_load(planes, st, W0, W1, P, RP, PS, xoff, yoff, zoff);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T sc_lane = (T)((lane >> 3) == 1 ? sc.x : ((lane >> 3) == 2 ? sc.y : sc.z));
+  const int nrows = P * Pw, nit = (nrows + 31) >> 5;
+  OutSlots<T> out{T(0), 0, 0};
+  for (int p0 = b; p0 < e; p0 += kTileBatch) {
+    const int nb = min(kTileBatch, e - p0);
     __syncthreads();
     for (int idx = threadIdx.x; idx < nb * 2 * Pw; idx += blockDim.x) {
-      const int jj = idx / (2 * Pw);
-      const int r = idx - jj * 2 * Pw;
+      const int j = idx / (2 * Pw);
+      const int r = idx - j * 2 * Pw;
       const int ax = r / Pw, k = r - ax * Pw;
-      const P4<T> a = rec[p0 + jj];
+      const P4<T> a = rec[p0 + j];
       const T c = ax == 0 ? a.x : a.y;
       const int g0 = (int)dceil(c - w.half);
       T v, dv;
-      win_eval<T, PW == 0>(w, ((T)(g0 + k) - c) * w.inv_half, v, dv);
-      T* wj = wgt + jj * 4 * Pw + 2 * ax * Pw;
+      win_eval<T, PW == 0>(w, win_arg(((T)(g0 + k) - c), w), v, dv);
+      T* wj = wgt + (j * 4 + 2 * ax) * kMaxWin;
       wj[k] = v;
-      wj[Pw + k] = -dv * w.inv_half;
+      wj[kMaxWin + k] = -dv * w.inv_half;  // d/dt of phi((g - t)/half)
       if (r == 0) {
         const int gy0 = (int)dceil(a.y - w.half);
-        bofs[jj] = (gy0 + g.pad_lo) * W0 + g0 + g.pad_lo;
+        bofs[j] = (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
+      }
+    }
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      // T_n(x) and T_n'(x) by the three-term recurrences
+      const T x = rec[p0 + j].z;
+      T* tj = tnb + j * 2 * kMaxCheb;
+      T t0 = T(1), t1 = x, d0 = T(0), d1 = T(1);
+      for (int n = 0; n < P; ++n) {
+        tj[n] = t0;
+        tj[kMaxCheb + n] = d0;
+        const T t2 = T(2) * x * t1 - t0, d2 = T(2) * t1 + T(2) * x * d1 - d0;
+        t0 = t1;
+        t1 = t2;
+        d0 = d1;
+        d1 = d2;
       }
     }
     __syncthreads();
-    T f = 0, fx = 0, fy = 0, fz = 0;
-    if (j < nb) {
-      const T* wj = wgt + j * 4 * Pw;
-      T wx[PR], dwx[PR], wy[PR], dwy[PR];
+    for (int j = warp; j < nb; j += nw) {
+      const T* wj = wgt + j * 4 * kMaxWin;
+      const T* tj = tnb + j * 2 * kMaxCheb;
+      T rwx[PR], rdwx[PR];
 #pragma unroll
-      for (int k = 0; k < PR; ++k) {
-        wx[k] = k < Pw ? wj[k] : T(0);
-        dwx[k] = k < Pw ? wj[Pw + k] : T(0);
-        wy[k] = k < Pw ? wj[2 * Pw + k] : T(0);
-        dwy[k] = k < Pw ? wj[3 * Pw + k] : T(0);
+      for (int dx = 0; dx < PR; ++dx) {
+        rwx[dx] = dx < Pw ? wj[dx] : T(0);
+        rdwx[dx] = dx < Pw ? wj[kMaxWin + dx] : T(0);
       }
       const T* bj = st + bofs[j];
-      const T x = rec[p0 + j].z;
-      // T_n(x), T_n'(x) by the three-term recurrence
-      T tm1 = 0, tc = 1, dm1 = 0, dc = 0;
-      for (int n = 0; n < n1; ++n) {
-        if (n >= n0) {
-          const T* pl = bj + n * PS;
-          T Sx = 0, Sd = 0, Sy = 0;
+      T f = 0, fx = 0, fy = 0, fz = 0;
+      for (int it = 0; it < nit; ++it) {
+        const int s2 = lane + 32 * it;
+        if (s2 < nrows) {
+          const int n = s2 / Pw, dy = s2 - n * Pw;
+          const T* rp = bj + n * PS + dy * RP;
+          T sx = 0, sd = 0;
 #pragma unroll
-          for (int dy = 0; dy < PR; ++dy) {
-            if (dy < Pw) {
-              const T* rp = pl + dy * W0;
-              T sx = 0, sd = 0;
-#pragma unroll
-              for (int dx = 0; dx < PR; ++dx) {
-                if (dx < Pw) {
-                  const T u = rp[dx];
-                  sx += u * wx[dx];
-                  sd += u * dwx[dx];
-                }
-              }
-              Sx += wy[dy] * sx;
-              Sd += wy[dy] * sd;
-              Sy += dwy[dy] * sx;
+          for (int dx = 0; dx < PR; ++dx) {
+            if (dx < Pw) {
+              const T u = rp[dx];
+              sx += u * rwx[dx];
+              sd += u * rdwx[dx];
             }
           }
-          f += tc * Sx;
-          fx += tc * Sd;
-          fy += tc * Sy;
-          fz += dc * Sx;
+          const T wy = wj[2 * kMaxWin + dy], dwy = wj[3 * kMaxWin + dy];
+          const T tn = tj[n], dtn = tj[kMaxCheb + n];
+          const T tw = tn * wy;
+          f += tw * sx;
+          fx += tw * sd;
+          fy += tn * dwy * sx;
+          fz += dtn * wy * sx;
         }
-        const T tn = n == 0 ? x : T(2) * x * tc - tm1;
-        const T dn = n == 0 ? T(1) : T(2) * tc + T(2) * x * dc - dm1;
-        tm1 = tc;
-        tc = tn;
-        dm1 = dc;
-        dc = dn;
       }
-    }
-    f += __shfl_xor_sync(0xffffffffu, f, 1);
-    fx += __shfl_xor_sync(0xffffffffu, fx, 1);
-    fy += __shfl_xor_sync(0xffffffffu, fy, 1);
-    fz += __shfl_xor_sync(0xffffffffu, fz, 1);
-    if (j < nb && sl == 0) {
-      const int o = perm[p0 + j];
-      phi_out[o] = (double)f;
-      grad_out[3 * o] = (double)fx * sc.x;
-      grad_out[3 * o + 1] = (double)fy * sc.y;
-      grad_out[3 * o + 2] = (double)fz * sc.z;
+      const T tot = warp_sum4(f, fx, fy, fz);
+      out.put(lane < 8 ? tot : tot * sc_lane, perm[p0 + j]);
+      if (out.n == 8) out.flush(phi_out, grad_out, false);
     }
   }
+  out.flush(phi_out, grad_out, false);
 }
 
 // ---------------------------------------------------------------------------
@@ -1910,36 +1975,88 @@ __global__ void k_k0_finalize(const double* __restrict__ part, int nblk, int P,
   }
 }
 
+// Float-pair arithmetic with ~48-bit significands (value + error term).
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return FF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF ff_add2(FF a, FF b) {
+  const FF s = ff_two_sum(a.h, b.h);
+  return ff_fast2(s.h, s.l + (a.l + b.l));
+}
+__device__ __forceinline__ FF ff_mul2(FF a, FF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return ff_fast2(p, e);
+}
+__device__ __forceinline__ FF ff_of(double v) {
+  const float h = (float)v;
+  return FF{h, (float)(v - (double)h)};
+}
+
+// The k = 0 potential and its z-derivative at every charge, Clenshaw sums of
+// sum_n nu_n T_n(x) and sum_n (n+1) nu_(n+1) U_n(x), x = 2 z / Lz.  FP64
+// plans sum in double; FP32 plans in float pairs (about 48-bit precision on
+// the FP32 pipe, which this GPU runs at 64 times the FP64 rate): the k = 0
+// part can be much larger than the total potential (in a thin slab it
+// carries most of each charge's self-interaction), so FP32 alone would not do.
 template <typename T>
-__global__ void k_k0_eval(const T* __restrict__ r, int N, int P, double halfLz,
+__global__ void k_k0_eval(const T* __restrict__ r, int N, int P, double halfLz, float2 ihp,
                           const double* __restrict__ nu, double* __restrict__ phi_out,
                           double* __restrict__ grad_out) {
   __shared__ double snu[kMaxCheb], scd[kMaxCheb];
+  __shared__ FF fnu[kMaxCheb], fcd[kMaxCheb];
   for (int n = threadIdx.x; n < P; n += blockDim.x) {
     snu[n] = nu[n];
     scd[n] = n + 1 < P ? (double)(n + 1) * nu[n + 1] : 0.0;  // T_n' = n U_(n-1)
+    fnu[n] = ff_of(snu[n]);
+    fcd[n] = ff_of(scd[n]);
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  double z = (double)r[3 * i + 2];
-  if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
-  const double ih = 1.0 / halfLz;
-  const double x = z * ih, x2 = 2.0 * x;
-  // Clenshaw: sum nu_n T_n(x) and sum (n+1) nu_(n+1) U_n(x)
-  double b1 = 0.0, b2 = 0.0, d1 = 0.0, d2 = 0.0;
-  for (int k = P - 1; k >= 1; --k) {
-    const double b0 = fma(x2, b1, snu[k] - b2);
-    b2 = b1;
-    b1 = b0;
-    const double d0 = fma(x2, d1, scd[k - 1] - d2);
-    d2 = d1;
-    d1 = d0;
+  if constexpr (sizeof(T) == 4) {
+    const float z = r[3 * i + 2];
+    FF x = ff_mul2(FF{z, 0.0f}, FF{ihp.x, ihp.y});
+    if (!(x.h >= -1.0f && x.h <= 1.0f)) x = isfinite(z) ? FF{x.h < 0.0f ? -1.0f : 1.0f, 0.0f} : FF{0.0f, 0.0f};
+    const FF x2{2.0f * x.h, 2.0f * x.l};
+    FF b1{0.0f, 0.0f}, b2{0.0f, 0.0f}, d1{0.0f, 0.0f}, d2{0.0f, 0.0f};
+    for (int k = P - 1; k >= 1; --k) {
+      const FF b0 = ff_add2(ff_add2(ff_mul2(x2, b1), FF{-b2.h, -b2.l}), fnu[k]);
+      b2 = b1;
+      b1 = b0;
+      const FF d0 = ff_add2(ff_add2(ff_mul2(x2, d1), FF{-d2.h, -d2.l}), fcd[k - 1]);
+      d2 = d1;
+      d1 = d0;
+    }
+    const FF ph = ff_add2(ff_add2(ff_mul2(x, b1), FF{-b2.h, -b2.l}), fnu[0]);
+    const FF gz = ff_mul2(d1, FF{ihp.x, ihp.y});
+    phi_out[i] = (double)ph.h + (double)ph.l;
+    grad_out[3 * i] = 0.0;
+    grad_out[3 * i + 1] = 0.0;
+    grad_out[3 * i + 2] = (double)gz.h + (double)gz.l;
+  } else {
+    double z = (double)r[3 * i + 2];
+    if (!(z >= -halfLz && z <= halfLz)) z = isfinite(z) ? (z < 0 ? -halfLz : halfLz) : 0.0;
+    const double ih = 1.0 / halfLz;
+    const double x = z * ih, x2 = 2.0 * x;
+    // Clenshaw: sum nu_n T_n(x) and sum (n+1) nu_(n+1) U_n(x)
+    double b1 = 0.0, b2 = 0.0, d1 = 0.0, d2 = 0.0;
+    for (int k = P - 1; k >= 1; --k) {
+      const double b0 = fma(x2, b1, snu[k] - b2);
+      b2 = b1;
+      b1 = b0;
+      const double d0 = fma(x2, d1, scd[k - 1] - d2);
+      d2 = d1;
+      d1 = d0;
+    }
+    phi_out[i] = fma(x, b1, snu[0] - b2);
+    grad_out[3 * i] = 0.0;
+    grad_out[3 * i + 1] = 0.0;
+    grad_out[3 * i + 2] = d1 * ih;
   }
-  phi_out[i] = fma(x, b1, snu[0] - b2);
-  grad_out[3 * i] = 0.0;
-  grad_out[3 * i + 1] = 0.0;
-  grad_out[3 * i + 2] = d1 * ih;
 }
 
 // ---------------------------------------------------------------------------
@@ -2030,10 +2147,14 @@ static size_t mid_smem(const sog_plan* p, size_t es, bool gather) {
 static size_t long_smem(const sog_plan* p, size_t es, bool gather) {
   const TileGeom& g = p->gl;
   const int P = p->prm.P_cheb;
+  const int rp = gather_row_pitch(g.W[0]);
+  const size_t tile = (size_t)P * gather_plane_stride(rp, g.W[1], p->wl.P);
+  // gathering: staged window values and derivatives, T_n and T_n', the tile
   if (gather)
-    return kGatherHeader + ((size_t)kGatherBatch * 4 * p->wl.P + (size_t)P * g.W[0] * g.W[1]) * es;
-  const size_t pl = (size_t)P * (g.W[0] * g.W[1] + 1);
-  return (pl + 8 * (2 * kMaxWin + kMaxCheb)) * es;
+    return kLongSpreadHeader + ((size_t)kTileBatch * (4 * kMaxWin + 2 * kMaxCheb) + tile) * es;
+  // gridding: staged window values and T_n, then the fixed-point tile (int32
+  // for FP32, int64 for FP64: the size of T)
+  return kLongSpreadHeader + ((size_t)kTileBatch * (2 * kMaxWin + kMaxCheb) + tile) * es;
 }
 
 #define SOG_CK(x)                      \
@@ -2093,6 +2214,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     g.nc[d] = p->nc[d];
     g.icell[d] = 1.0 / p->cell[d];
     g.ih[d] = p->has_mid ? 1.0 / p->h[d] : 0.0;
+    g.h[d] = p->has_mid ? p->h[d] : 1.0;
     g.Tm[d] = p->gm.T[d];
     g.ntm[d] = p->gm.nt[d];
     g.iTm[d] = p->has_mid ? 1.0 / p->gm.T[d] : 0.0;
@@ -2103,6 +2225,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   g.Lzs_half = 0.5 * p->Lzs;
   for (int d = 0; d < 2; ++d) {
     g.ihl[d] = p->has_long ? 1.0 / p->hl[d] : 0.0;
+    g.hl[d] = long_bins ? p->hl[d] : 1.0;
     g.Tl[d] = p->gl.T[d];
     g.ntl[d] = p->gl.nt[d];
     g.iTl[d] = p->has_long ? 1.0 / p->gl.T[d] : 0.0;
@@ -2165,7 +2288,9 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   near_consts<float>(ng, ng.cf);
   near_consts<double>(ng, ng.cd);
   // the near field depends only on the binning: fork it onto the side stream
-  const cudaStream_t sn = p->side_stream;
+  // timing mode 2: every stage on the caller's stream, one after another
+  const bool serial = p->timing == 2;
+  const cudaStream_t sn = serial ? s : p->side_stream;
   SOG_CK(cudaEventRecord(p->ev_fork, s));
   SOG_CK(cudaStreamWaitEvent(sn, p->ev_fork, 0));
   mark_begin(p, 1, sn);
@@ -2208,7 +2333,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   // (the direct sums and the k = 0 moments could start with the evaluation,
   // but measured no faster: they compete with the binning that every other
   // part waits for)
-  const cudaStream_t sl = p->long_stream;
+  const cudaStream_t sl = serial ? s : p->long_stream;
   SOG_CK(cudaStreamWaitEvent(sl, p->ev_fork, 0));
   if (p->has_long && p->long_direct) {
     const int P = m.P_cheb, Kx = (m.I_long[0] - 1) / 2, Ky = (m.I_long[1] - 1) / 2;
@@ -2250,24 +2375,10 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     mark_end(p, 7, sl);
   }
   if (p->has_long) {
-    mark_begin(p, 8, sl);
-    const int P = m.P_cheb;
-    double* mpart = p->d_red + 2 * p->red_blocks;
-    const ModeGeom<T> mg0 = mode_geom<T>(m.L[0], m.L[1], m.L[2]);
-    if (P <= 16)
-      k_k0_moments<T, 16><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
-    else if (P <= 32)
-      k_k0_moments<T, 32><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
-    else
-      k_k0_moments<T, 64><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
-    LAUNCH_CHECK();
-  }
-  if (p->has_long) {
     const int P = m.P_cheb;
     if (!p->long_direct) {
     mark_begin(p, 5, sl);
     T* A = reinterpret_cast<T*>(p->d_lA);
-    T* B = reinterpret_cast<T*>(p->d_lB);
     const WinT<T> w = wint<T>(p->wl);
     if (p->long_small) {
       const int I0 = m.I_long[0], I1 = m.I_long[1];
@@ -2294,14 +2405,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     mark_end(p, 5, sl);
     mark_begin(p, 6, sl);
     int nl = 0;
-    SOG_CK(fft_long_pass<T>(p, false, sl, nl));
-    const int C = m.I_long[0] / 2 + 1;
-    const int modes = m.I_long[1] * C;
-    const int per = 256 / P;
-    k_long_contract<T><<<(modes + per - 1) / per, 256, 0, sl>>>(
-        A, B, reinterpret_cast<const T*>(p->d_kmat), P, m.I_long[1], C);
-    LAUNCH_CHECK();
-    SOG_CK(fft_long_pass<T>(p, true, sl, nl));
+    SOG_CK(fft_long_solve<T>(p, sl, nl));
     p->launches += nl;
     mark_end(p, 6, sl);
     mark_begin(p, 7, sl);
@@ -2309,15 +2413,28 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     const double3 sc = make_double3(1.0 / p->hl[0], 1.0 / p->hl[1], 2.0 / m.L[2]);
     const dim3 lgrid2(p->n_tiles_long, p->gl.chunks);
     SOG_DISPATCH_PW(pw_dispatch(p->wl), k_long_gather, lgrid2, sm2, sl, p->gl, w, P, rl, p->d_cnt + off.z,
-                    p->d_perm + 2 * (size_t)N, B, sc, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
+                    p->d_perm + 2 * (size_t)N, A, sc, pp + 2 * (size_t)N, pg + 6 * (size_t)N);
     LAUNCH_CHECK();
     mark_end(p, 7, sl);
+    }
+    {
+    mark_begin(p, 8, sl);
+    const int P = m.P_cheb;
+    double* mpart = p->d_red + 2 * p->red_blocks;
+    const ModeGeom<T> mg0 = mode_geom<T>(m.L[0], m.L[1], m.L[2]);
+    if (P <= 16)
+      k_k0_moments<T, 16><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+    else if (P <= 32)
+      k_k0_moments<T, 32><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+    else
+      k_k0_moments<T, 64><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+    LAUNCH_CHECK();
     }
     k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * p->red_blocks, p->k0_blocks, P, p->d_k0mat,
                                      p->d_k0nu, p->d_red, p->red_blocks, p->d_status);
     LAUNCH_CHECK();
-    k_k0_eval<T><<<(N + 255) / 256, 256, 0, sl>>>(r, N, P, 0.5 * m.L[2], p->d_k0nu,
-                                                pp + 3 * (size_t)N, pg + 9 * (size_t)N);
+    k_k0_eval<T><<<(N + 255) / 256, 256, 0, sl>>>(r, N, P, 0.5 * m.L[2], float_pair(2.0 / m.L[2]),
+                                                p->d_k0nu, pp + 3 * (size_t)N, pg + 9 * (size_t)N);
     LAUNCH_CHECK();
     mark_end(p, 8, sl);
   } else {

@@ -8,7 +8,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <thread>
 #include <vector>
 
 #include "sog_internal.h"
@@ -501,6 +500,7 @@ const char* sog_status_str(sog_status s) {
     case SOG_ERR_NOMEM: return "out of memory";
     case SOG_ERR_CUDA: return "CUDA error";
     case SOG_ERR_PARAMS: return "no feasible or an inconsistent parameter set";
+    case SOG_ERR_TIMEOUT: return "a kernel's bounded wait for its asynchronous copies ran out";
   }
   return "unknown status";
 }
@@ -670,6 +670,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   if (p->has_long && !p->long_direct) {
     add_len(Ilx, p->flx);
     add_len(Ily, p->fly);
+    p->long_fused = sogk::long_fused_fits(P, p->fly, es) ? 1 : 0;
   }
   if (tw.empty()) tw.assign(4, 0.0);
   if ((p->has_mid && !(sogk::fft_len_ok(prec, p->fx) && sogk::fft_len_ok(prec, p->fy) &&
@@ -715,7 +716,8 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   }
 
   // long range: per-mode z-kernel in the Chebyshev basis and the k = 0 kernel
-  std::vector<double> kmat, k0mat((size_t)std::max(P, 1) * std::max(P, 1), 0.0);
+  std::vector<double> kmat, lbl, lcl, lfx, lfy,
+      k0mat((size_t)std::max(P, 1) * std::max(P, 1), 0.0);
   if (p->has_long) {
     const double A = L[0] * L[1];
     std::vector<double> zc(P), Cm((size_t)P * P);
@@ -778,47 +780,45 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
         }
       }
     }
-    const int C = Ilx / 2 + 1;
-    const size_t kbytes = p->long_direct ? 0 : (size_t)Ily * C * P * P * es;
-    // per-mode P x P kernels: up to 32 GB (a 1176^2 long grid with P = 24,
-    // the 1000 x 1000 x 10 slab at 1e6 particles, needs 1.6 GB in FP32)
-    if (kbytes > ((size_t)32 << 30)) {
-      delete p;
-      return SOG_ERR_PARAMS;
-    }
     if (!p->long_direct) {
-    const double shp = eff_shape(prm.shape_long, prec), hw = eff_half(p->wl.half, prec);
-    WinFT fx(prm.window, shp, hw * p->hl[0], prec);
-    WinFT fy(prm.window, shp, hw * p->hl[1], prec);
-    std::vector<double> Wx(C), Wy(Ily), kx(C), ky(Ily);
-    for (int f = 0; f < C; ++f) { kx[f] = 2.0 * kPi * f / L[0]; Wx[f] = fx(kx[f]); }
-    for (int f = 0; f < Ily; ++f) { ky[f] = 2.0 * kPi * std::min(f, Ily - f) / L[1]; Wy[f] = fy(ky[f]); }
-    kmat.assign((size_t)Ily * C * P * P, 0.0);
-    // rows of modes on host threads; s_l grows with l, so once
-    // s_l^2 k^2 / 4 > 80 this and every later term is below e^-80 of the
-    // earlier ones and the sum stops
-    auto rows = [&](int y0, int ystep) {
-      for (int y = y0; y < Ily; y += ystep)
-        for (int x = 0; x < C; ++x) {
-          if (x == 0 && y == 0) continue;
-          const double k2 = kx[x] * kx[x] + ky[y] * ky[y];
-          const double fac = kPi / A * pow(p->hl[0] * p->hl[1], 2) / pow(Wx[x] * Wy[y], 2);
-          double* K = &kmat[((size_t)y * C + x) * P * P];
-          for (int li = 0; li < nl; ++li) {
-            const int l = prm.m + 1 + li;
-            const double ex = s[l] * s[l] * k2 / 4.0;
-            if (ex > 80.0) break;
-            const double al = w[l] * s[l] * s[l] * exp(-ex);
-            const double* B = &Bl[(size_t)li * P * P];
-            for (int i = 0; i < P * P; ++i) K[i] += fac * al * B[i];
-          }
-        }
-    };
-    const int nthr = std::max(1, std::min(Ily, (int)std::min(16u, std::thread::hardware_concurrency())));
-    std::vector<std::thread> pool;
-    for (int t = 1; t < nthr; ++t) pool.emplace_back(rows, t, nthr);
-    rows(0, nthr);
-    for (auto& th : pool) th.join();
+      // Algorithm 2: K_k = fx(kx) fy(ky) sum_l c1_l e^{-c2_l k^2} B_l, applied
+      // factor by factor in the contraction.  B_l[n][n'] vanishes when n + n'
+      // is odd (the proxy points are symmetric about z = 0 and T_n has the
+      // parity of n), so each B_l is stored as its even and odd blocks.
+      const int C = Ilx / 2 + 1;
+      const int ps = (P + 1) / 2, pst = (ps + 3) / 4 * 4;
+      p->n_lg = nl;
+      p->lps = ps;
+      p->lpst = pst;
+      lbl.assign((size_t)nl * 2 * ps * pst, 0.0);
+      for (int li = 0; li < nl; ++li)
+        for (int par = 0; par < 2; ++par)
+          for (int i = 0; 2 * i + par < P; ++i)
+            for (int j = 0; 2 * j + par < P; ++j)
+              lbl[(((size_t)li * 2 + par) * ps + i) * pst + j] =
+                  Bl[((size_t)li * P + 2 * i + par) * P + 2 * j + par];
+      lcl.resize((size_t)2 * nl);
+      for (int li = 0; li < nl; ++li) {
+        const int l = prm.m + 1 + li;
+        lcl[2 * li] = kPi / (L[0] * L[1]) * w[l] * s[l] * s[l];
+        lcl[2 * li + 1] = 0.25 * s[l] * s[l];
+      }
+      const double shp = eff_shape(prm.shape_long, prec), hw = eff_half(p->wl.half, prec);
+      WinFT fx(prm.window, shp, hw * p->hl[0], prec);
+      WinFT fy(prm.window, shp, hw * p->hl[1], prec);
+      lfx.resize((size_t)2 * C);
+      lfy.resize((size_t)2 * Ily);
+      for (int f = 0; f < C; ++f) {
+        const double k = 2.0 * kPi * f / L[0], W = fx(k);
+        lfx[2 * f] = k * k;
+        lfx[2 * f + 1] = p->hl[0] * p->hl[0] / (W * W);
+      }
+      for (int f = 0; f < Ily; ++f) {
+        const double k = 2.0 * kPi * std::min(f, Ily - f) / L[1], W = fy(k);
+        lfy[2 * f] = k * k;
+        lfy[2 * f + 1] = p->hl[1] * p->hl[1] / (W * W);
+      }
+
     }
     // k = 0: (pi/A) C^T K0 C, K0(d) = -sum_{l>m} w_l d^2 phi1(d^2/s_l^2)
     std::vector<double> K0((size_t)P * P, 0.0);
@@ -853,12 +853,16 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   const size_t o_near = ar.take(ntab.size() * es);
   const size_t o_mult = ar.take(mult.size() * es);
   const size_t o_kmat = ar.take(kmat.size() * es);
+  const size_t o_lbl = ar.take(lbl.size() * es);
+  const size_t o_lcl = ar.take(lcl.size() * es);
+  const size_t o_lfx = ar.take(lfx.size() * es);
+  const size_t o_lfy = ar.take(lfy.size() * es);
   const size_t o_k0 = ar.take(k0mat.size() * sizeof(double));
   const size_t tables_end = ar.size;
   const size_t o_grid = ar.take(p->has_mid ? (size_t)Iz * Iy * (Ix + 2) * es : 0);
   const size_t lbytes = p->has_long ? (size_t)P * Ily * (Ilx + 2) * es : 0;
   const size_t o_lA = ar.take(lbytes);
-  const size_t o_lB = ar.take(lbytes);
+  const size_t o_lB = ar.take(p->long_fused ? lbytes : 0);  // transposed spectrum of the fused path
   const size_t o_rn = ar.take((size_t)N * 4 * es);
   const size_t o_rm = ar.take(p->has_mid ? (size_t)N * 4 * es : 0);
   const size_t o_rl = ar.take(p->has_long ? (size_t)N * 4 * es : 0);
@@ -897,6 +901,10 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   p->d_near_tab = b + o_near;
   p->d_mult = b + o_mult;
   p->d_kmat = b + o_kmat;
+  p->d_lbl = b + o_lbl;
+  p->d_lcl = b + o_lcl;
+  p->d_lfx = b + o_lfx;
+  p->d_lfy = b + o_lfy;
   p->d_k0mat = reinterpret_cast<double*>(b + o_k0);
   p->d_grid = b + o_grid;
   p->d_lA = b + o_lA;
@@ -926,11 +934,19 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     put<double>(host, o_near, ntab);
     put<double>(host, o_mult, mult);
     put<double>(host, o_kmat, kmat);
+    put<double>(host, o_lbl, lbl);
+    put<double>(host, o_lcl, lcl);
+    put<double>(host, o_lfx, lfx);
+    put<double>(host, o_lfy, lfy);
   } else {
     put<float>(host, o_tw, tw);
     put<float>(host, o_near, ntab);
     put<float>(host, o_mult, mult);
     put<float>(host, o_kmat, kmat);
+    put<float>(host, o_lbl, lbl);
+    put<float>(host, o_lcl, lcl);
+    put<float>(host, o_lfx, lfx);
+    put<float>(host, o_lfy, lfy);
   }
   put<double>(host, o_k0, k0mat);
   cudaError_t e = cudaMemcpy(base, host.data(), tables_end, cudaMemcpyHostToDevice);
@@ -1023,6 +1039,7 @@ sog_status sog_plan_check(sog_plan* plan) {
     plan->launch_error = 0;
     return SOG_ERR_CUDA;
   }
+  if (st & 4) return SOG_ERR_TIMEOUT;
   if (st & 2) return SOG_ERR_OUT_OF_BOX;
   if (st & 1) return SOG_ERR_NONNEUTRAL;
   return SOG_OK;
@@ -1035,7 +1052,8 @@ sog_status sog_plan_set_timing(sog_plan* plan, int32_t enable) {
       if (cudaEventCreate(&plan->ev[i]) != cudaSuccess) return SOG_ERR_CUDA;
     plan->events_ready = 1;
   }
-  plan->timing = enable ? 1 : 0;
+  if (enable < 0 || enable > 2) return SOG_ERR_ARG;
+  plan->timing = enable;
   return SOG_OK;
 }
 
