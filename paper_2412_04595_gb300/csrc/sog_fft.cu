@@ -394,25 +394,28 @@ __device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T4*
   __syncthreads();
 }
 
-// All stages of one length.  The factorisation orders the radices 16..16,
-// 15..15 (engines holding at least 16 values per thread), 8..8, 4, 2, 3..3,
-// 5..5, 7..7; each group is a separate straight-line block so that the
-// registers of one stage are free for the next.
+// All stages of one length (a Stockham stage is correct in any order of the
+// radices, given L = the product of the earlier ones).  Odd radices run
+// first: with contiguous lines, a stage writes its outputs R elements apart
+// across consecutive threads while L is small, which for an even R maps a
+// warp onto few shared-memory banks; the even radices come once L is large.
+// Each group is a separate straight-line block so that the registers of one
+// stage are free for the next.
 template <typename T2, int CAP, typename T4>
 __device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T4* tw, bool inv) {
   const int n16 = f.n16, n15 = f.n15, n8 = f.n8, n4 = f.n4, n2 = f.n2, n3 = f.n3, n5 = f.n5,
             n7 = f.n7;
   int L = 1;
-  if constexpr (CAP >= 16) {
-    for (int i = 0; i < n16; ++i, L *= 16) stage<T2, CAP, 16>(buf, s, L, tw, inv);
+  if constexpr (CAP >= 16)
     for (int i = 0; i < n15; ++i, L *= 15) stage<T2, CAP, 15>(buf, s, L, tw, inv);
-  }
-  for (int i = 0; i < n8; ++i, L *= 8) stage<T2, CAP, 8>(buf, s, L, tw, inv);
-  if (n4) { stage<T2, CAP, 4>(buf, s, L, tw, inv); L *= 4; }
-  if (n2) { stage<T2, CAP, 2>(buf, s, L, tw, inv); L *= 2; }
   for (int i = 0; i < n3; ++i, L *= 3) stage<T2, CAP, 3>(buf, s, L, tw, inv);
   for (int i = 0; i < n5; ++i, L *= 5) stage<T2, CAP, 5>(buf, s, L, tw, inv);
   for (int i = 0; i < n7; ++i, L *= 7) stage<T2, CAP, 7>(buf, s, L, tw, inv);
+  if constexpr (CAP >= 16)
+    for (int i = 0; i < n16; ++i, L *= 16) stage<T2, CAP, 16>(buf, s, L, tw, inv);
+  for (int i = 0; i < n8; ++i, L *= 8) stage<T2, CAP, 8>(buf, s, L, tw, inv);
+  if (n4) { stage<T2, CAP, 4>(buf, s, L, tw, inv); L *= 4; }
+  if (n2) { stage<T2, CAP, 2>(buf, s, L, tw, inv); L *= 2; }
 }
 
 // Largest nl for which nl lines of length n fit the engine.
@@ -695,6 +698,39 @@ __device__ __forceinline__ float dexp_(float x) { return expf(x); }
 template <>
 __device__ __forceinline__ double dexp_(double x) { return exp(x); }
 
+// t = sum_j B[j] v[j], j < np, for a B row padded with zeros to a multiple
+// of four (the rows start 16-byte aligned): vector loads of four.
+template <int PH>
+__device__ __forceinline__ void brow_dot(const float* __restrict__ B, const float2 (&v)[PH], int np,
+                                         float& tx, float& ty) {
+  const float4* B4 = reinterpret_cast<const float4*>(B);
+#pragma unroll
+  for (int q = 0; q < PH / 4; ++q) {
+    if (4 * q < np) {
+      const float4 b = B4[q];
+      tx = fmaf(b.x, v[4 * q].x, tx);
+      ty = fmaf(b.x, v[4 * q].y, ty);
+      tx = fmaf(b.y, v[4 * q + 1].x, tx);
+      ty = fmaf(b.y, v[4 * q + 1].y, ty);
+      tx = fmaf(b.z, v[4 * q + 2].x, tx);
+      ty = fmaf(b.z, v[4 * q + 2].y, ty);
+      tx = fmaf(b.w, v[4 * q + 3].x, tx);
+      ty = fmaf(b.w, v[4 * q + 3].y, ty);
+    }
+  }
+}
+template <int PH>
+__device__ __forceinline__ void brow_dot(const double* __restrict__ B, const double2 (&v)[PH],
+                                         int np, double& tx, double& ty) {
+#pragma unroll
+  for (int j = 0; j < PH; ++j) {
+    if (j < np) {
+      tx = fma(B[j], v[j].x, tx);
+      ty = fma(B[j], v[j].y, ty);
+    }
+  }
+}
+
 // One mode, one parity block: orders n = 2 i + par, i < np; get(i) returns
 // mu_n, put(i, v) stores nu_n.  PH bounds np; the outputs are computed OH at
 // a time (inputs held in registers, the exponentials recomputed per chunk).
@@ -702,7 +738,7 @@ template <typename T, int PH, int OH, typename GET, typename PUT>
 __device__ __forceinline__ void long_contract_parity(GET get, PUT put, int np, int par, int ps,
                                                      int pst, int nl, const T* __restrict__ lbl,
                                                      const typename C2<T>::t* __restrict__ lcl,
-                                                     T k2, T fac) {
+                                                     T k2, T fac, T xmax) {
   using T2 = typename C2<T>::t;
   T2 v[PH];
 #pragma unroll
@@ -716,22 +752,14 @@ __device__ __forceinline__ void long_contract_parity(GET get, PUT put, int np, i
     for (int l = 0; l < nl; ++l) {
       const T2 c = lcl[l];
       const T x = c.y * k2;
-      if (x > T(80)) break;
+      if (x > xmax) break;
       const T a = fac * c.x * dexp_(-x);
       const T* B = lbl + ((size_t)l * 2 + par) * ps * pst + (size_t)i0 * pst;
 #pragma unroll
       for (int o = 0; o < OH; ++o) {
         if (i0 + o < np) {
-          const T* Bi = B + o * pst;
           T tx = T(0), ty = T(0);
-#pragma unroll
-          for (int j = 0; j < PH; ++j) {
-            if (j < np) {
-              const T b = __ldg(Bi + j);
-              tx = fma(b, v[j].x, tx);
-              ty = fma(b, v[j].y, ty);
-            }
-          }
+          brow_dot<PH>(B + o * pst, v, np, tx, ty);
           acc[o].x = fma(a, tx, acc[o].x);
           acc[o].y = fma(a, ty, acc[o].y);
         }
@@ -751,7 +779,7 @@ __global__ void __launch_bounds__(128)
     k_long_contract(typename C2<T>::t* __restrict__ A, int P, int Iy, int C,
                     const T* __restrict__ lbl, const typename C2<T>::t* __restrict__ lcl,
                     const typename C2<T>::t* __restrict__ lfx,
-                    const typename C2<T>::t* __restrict__ lfy, int nl, int ps, int pst) {
+                    const typename C2<T>::t* __restrict__ lfy, int nl, int ps, int pst, T xmax) {
   using T2 = typename C2<T>::t;
   const int mode = blockIdx.x * blockDim.x + threadIdx.x;
   if (mode >= Iy * C) return;
@@ -768,18 +796,24 @@ __global__ void __launch_bounds__(128)
     long_contract_parity<T, PH, PH>([&](int i) { return a[(2 * i + par) * pstr]; },
                                 [&](int i, T2 v) { a[(2 * i + par) * pstr] = v; },
                                 (P + 1 - par) / 2, par, ps, pst, nl, lbl, lcl, fx.x + fy.x,
-                                fx.y * fy.y);
+                                fx.y * fy.y, xmax);
 }
+
+// Outputs of one contraction work item in the fused y pass.
+constexpr int kYpassOut = 4;
 
 // Fused y pass of Algorithm 2 for one half-spectrum column c and one parity
 // par of the Chebyshev order (orders of different parity do not couple in the
 // contraction): the np planes n = 2 i + par of the column (transposed layout
 // [c][par][i][y], written by the x pass) are brought into shared memory by
-// bulk copies, the np forward y FFTs run in one pass of the engine, then the
-// contraction (a thread per mode y, four outputs at a time), the backward y
-// FFTs, and one bulk copy writes the block back in place.  A bulk copy that
-// does not complete within the bounded wait sets bit 2 of *status and the
-// CTA returns.
+// bulk copies, with this parity's B_l and (c1_l, c2_l) beside them; the np
+// forward y FFTs run in one pass of the engine; the contraction runs in
+// rounds, each over a range of modes y, one thread per (mode, chunk of
+// kYpassOut orders), threads of a warp sharing a chunk so that their B_l
+// reads are broadcasts; every round reads its modes' inputs, waits, then
+// writes the outputs in place; then the backward y FFTs, and one bulk copy
+// writes the block back.  A bulk copy that does not complete within the
+// bounded wait sets bit 2 of *status and the CTA returns.
 template <typename T, int PH>
 __global__ void __launch_bounds__(kYpassThreads, 1)
     k_long_ypass(typename C2<T>::t* __restrict__ data, FftLen fy,
@@ -787,7 +821,7 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
                  const T* __restrict__ lbl, const typename C2<T>::t* __restrict__ lcl,
                  const typename C2<T>::t* __restrict__ lfx,
                  const typename C2<T>::t* __restrict__ lfy, int nl, int ps, int pst,
-                 int* __restrict__ status) {
+                 T xmax, int* __restrict__ status) {
   using T2 = typename C2<T>::t;
   using T4 = typename C2<T>::tw;
   constexpr int CAP = FftCfg<T>::cap;
@@ -798,6 +832,8 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
   const int np0 = (P + 1) / 2, np = par ? P / 2 : np0;
   const int tot = np * Iy;
   T4* tw = reinterpret_cast<T4*>(buf + (size_t)np0 * Iy);
+  T* sB = reinterpret_cast<T*>(tw + Iy);                   // [l][i][j], row stride pst
+  T2* sC = reinterpret_cast<T2*>(sB + (size_t)nl * ps * pst);
   T2* blk = data + (size_t)c * P * Iy + (size_t)(par ? np0 : 0) * Iy;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
@@ -808,6 +844,12 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
                bytes - o < 32768u ? bytes - o : 32768u, &bar);
   }
   for (int i = threadIdx.x; i < Iy; i += blockDim.x) tw[i] = twg[fy.tw_off + i];
+  const int bsz = ps * pst;
+  for (int i = threadIdx.x; i < nl * bsz; i += blockDim.x) {
+    const int l = i / bsz;
+    sB[i] = lbl[((size_t)l * 2 + par) * bsz + (i - l * bsz)];
+  }
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) sC[l] = lcl[l];
   __syncthreads();
   if (!mbar_wait(&bar, 0)) {
     if (threadIdx.x == 0) atomicOr(status, 4);
@@ -818,18 +860,49 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
   const LineSet ls{Iy, np, Iy, 1, false};
   fft_lines<T2, CAP>(buf, ls, fy, tw, false);
   const T2 fx = lfx[c];
-  for (int y = threadIdx.x; y < Iy; y += blockDim.x) {
-    T2* a = buf + y;
-    if (c == 0 && y == 0) {
-      for (int i = 0; i < np; ++i) a[i * Iy] = T2{T(0), T(0)};
-      continue;
+  const int nsplit = (np + kYpassOut - 1) / kYpassOut;
+  const int mr = blockDim.x / nsplit;  // modes per round
+  const int ch = threadIdx.x / mr, yl = threadIdx.x - ch * mr;
+  for (int y0 = 0; y0 < Iy; y0 += mr) {
+    const int y = y0 + yl;
+    const bool act = ch < nsplit && y < Iy;
+    const int i0 = ch * kYpassOut;
+    T2 acc[kYpassOut];
+#pragma unroll
+    for (int o = 0; o < kYpassOut; ++o) acc[o] = T2{T(0), T(0)};
+    if (act && !(c == 0 && y == 0)) {
+      const T2* a = buf + y;
+      T2 v[PH];
+#pragma unroll
+      for (int i = 0; i < PH; ++i) v[i] = i < np ? a[i * Iy] : T2{T(0), T(0)};
+      const T2 fyv = lfy[y];
+      const T k2 = fx.x + fyv.x, fac = fx.y * fyv.y;
+#pragma unroll 1
+      for (int l = 0; l < nl; ++l) {
+        const T2 cl = sC[l];
+        const T xx = cl.y * k2;
+        if (xx > xmax) break;
+        const T al = fac * cl.x * dexp_(-xx);
+        const T* B = sB + (size_t)l * bsz + (size_t)i0 * pst;
+#pragma unroll
+        for (int o = 0; o < kYpassOut; ++o) {
+          if (i0 + o < np) {
+            T tx = T(0), ty = T(0);
+            brow_dot<PH>(B + o * pst, v, np, tx, ty);
+            acc[o].x = fma(al, tx, acc[o].x);
+            acc[o].y = fma(al, ty, acc[o].y);
+          }
+        }
+      }
     }
-    const T2 fyv = lfy[y];
-    long_contract_parity<T, PH, 4>([&](int i) { return a[i * Iy]; },
-                                   [&](int i, T2 v) { a[i * Iy] = v; }, np, par, ps, pst, nl, lbl,
-                                   lcl, fx.x + fyv.x, fx.y * fyv.y);
+    __syncthreads();  // every input of this round's modes has been read
+    if (act) {
+#pragma unroll
+      for (int o = 0; o < kYpassOut; ++o)
+        if (i0 + o < np) buf[(size_t)(i0 + o) * Iy + y] = acc[o];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   fft_lines<T2, CAP>(buf, ls, fy, tw, true);
   fence_async_smem();
   __syncthreads();
@@ -945,15 +1018,20 @@ cudaError_t fft_mid_forward_conv_inverse(const sog_plan* p, cudaStream_t s, int&
 template cudaError_t fft_mid_forward_conv_inverse<float>(const sog_plan*, cudaStream_t, int&);
 template cudaError_t fft_mid_forward_conv_inverse<double>(const sog_plan*, cudaStream_t, int&);
 
-// FP32 plans: one parity block of a column (ceil(P/2) Iy complex values) and
-// the y twiddles must fit the shared memory of one CTA, the block's lines one
-// pass of the engine, and the block the register budget (P <= 32).  FP64
-// plans use the separate passes.
-bool long_fused_fits(int P, const FftLen& fy, size_t es) {
+// Shared memory of the fused y pass: one parity block of a column, the y
+// twiddles, one parity's B_l for the nl Gaussians a mode can use, (c1, c2).
+size_t long_fused_smem(int P, const FftLen& fy, int nl, size_t es) {
+  const int np0 = (P + 1) / 2, ps = np0, pst = (ps + 3) / 4 * 4;
+  return (size_t)np0 * fy.n * 2 * es + (size_t)fy.n * (es == 4 ? sizeof(TwF) : sizeof(TwD)) +
+         (size_t)nl * ps * pst * es + (size_t)nl * 2 * es;
+}
+
+// FP32 plans: the fused y pass's shared memory must fit one CTA, the block's
+// lines one pass of the engine, and the block the register budget
+// (P <= 32).  FP64 plans use the separate passes.
+bool long_fused_fits(int P, const FftLen& fy, int nl, size_t es) {
   const int np0 = (P + 1) / 2;
-  return es == sizeof(float) && P <= 32 &&
-         (size_t)np0 * fy.n * sizeof(float2) + (size_t)fy.n * sizeof(TwF) + 64 <=
-             (size_t)kMaxDynSmem &&
+  return es == sizeof(float) && P <= 32 && long_fused_smem(P, fy, nl, es) + 64 <= (size_t)kMaxDynSmem &&
          max_lines(fy, FftCfg<float>::cap, kYpassThreads) >= np0;
 }
 
@@ -965,7 +1043,7 @@ static void launch_contract(const sog_plan* p, T* A, cudaStream_t s) {
   k_long_contract<T, PH><<<(modes + 127) / 128, 128, 0, s>>>(
       reinterpret_cast<T2*>(A), P, Iy, C, reinterpret_cast<const T*>(p->d_lbl),
       reinterpret_cast<const T2*>(p->d_lcl), reinterpret_cast<const T2*>(p->d_lfx),
-      reinterpret_cast<const T2*>(p->d_lfy), p->n_lg, p->lps, p->lpst);
+      reinterpret_cast<const T2*>(p->d_lfy), p->n_lg_used, p->lps, p->lpst, (T)p->lg_xmax);
 }
 
 template <typename T, int PH>
@@ -973,13 +1051,12 @@ static void launch_ypass(const sog_plan* p, typename C2<T>::t* col, cudaStream_t
   using T2 = typename C2<T>::t;
   using T4 = typename C2<T>::tw;
   const int P = p->prm.P_cheb, C = p->prm.I_long[0] / 2 + 1;
-  const int np0 = (P + 1) / 2;
-  const size_t sm = (size_t)np0 * p->fly.n * sizeof(T2) + (size_t)p->fly.n * sizeof(T4);
+  const size_t sm = long_fused_smem(P, p->fly, p->n_lg_used, sizeof(T));
   k_long_ypass<T, PH><<<2 * C, kYpassThreads, sm, s>>>(
       col, p->fly, reinterpret_cast<const T4*>(p->d_tw), P,
       reinterpret_cast<const T*>(p->d_lbl), reinterpret_cast<const T2*>(p->d_lcl),
-      reinterpret_cast<const T2*>(p->d_lfx), reinterpret_cast<const T2*>(p->d_lfy), p->n_lg,
-      p->lps, p->lpst, p->d_status);
+      reinterpret_cast<const T2*>(p->d_lfx), reinterpret_cast<const T2*>(p->d_lfy), p->n_lg_used,
+      p->lps, p->lpst, (T)p->lg_xmax, p->d_status);
 }
 
 // Algorithm 2 steps 2-4 on the proxy planes in d_lA.  Fused: x pass with the
@@ -996,7 +1073,9 @@ cudaError_t fft_long_solve(const sog_plan* p, cudaStream_t s, int& launches) {
   if constexpr (sizeof(T) == 4) if (p->long_fused) {
     T2* col = reinterpret_cast<T2*>(p->d_lB);
     if ((e = launch_rows<T>(A, p->flx, p->d_tw, Iy * P, false, s, col, Iy, ph))) return e;
-    if (ph <= 8) launch_ypass<T, 8>(p, col, s);
+    if (ph <= 4) launch_ypass<T, 4>(p, col, s);
+    else if (ph <= 8) launch_ypass<T, 8>(p, col, s);
+    else if (ph <= 12) launch_ypass<T, 12>(p, col, s);
     else launch_ypass<T, 16>(p, col, s);
     if ((e = cudaGetLastError())) return e;
     if ((e = launch_rows<T>(A, p->flx, p->d_tw, Iy * P, true, s, col, Iy, ph))) return e;
@@ -1004,7 +1083,9 @@ cudaError_t fft_long_solve(const sog_plan* p, cudaStream_t s, int& launches) {
     return cudaSuccess;
   }
   if ((e = fft_planes<T>(A, p->flx, p->fly, p->d_tw, P, false, s, launches))) return e;
-  if (ph <= 8) launch_contract<T, 8>(p, A, s);
+  if (ph <= 4) launch_contract<T, 4>(p, A, s);
+  else if (ph <= 8) launch_contract<T, 8>(p, A, s);
+  else if (ph <= 12) launch_contract<T, 12>(p, A, s);
   else if (ph <= 16) launch_contract<T, 16>(p, A, s);
   else launch_contract<T, 32>(p, A, s);
   if ((e = cudaGetLastError())) return e;
@@ -1049,7 +1130,9 @@ cudaError_t fft_prepare() {
                              kMaxDynSmem);
   if constexpr (sizeof(T) == 4) {
     // the y pass holds its mbarrier in static shared memory
+    if (e == cudaSuccess) e = allow_dyn_smem(k_long_ypass<T, 4>);
     if (e == cudaSuccess) e = allow_dyn_smem(k_long_ypass<T, 8>);
+    if (e == cudaSuccess) e = allow_dyn_smem(k_long_ypass<T, 12>);
     if (e == cudaSuccess) e = allow_dyn_smem(k_long_ypass<T, 16>);
   }
   return e;

@@ -174,6 +174,9 @@ struct sog_plan {
   void* d_lfx;         // (kx^2, hx^2 / What_x(kx)^2) per half-spectrum column, T pairs
   void* d_lfy;         // (ky^2, hy^2 / What_y(ky)^2) per row, T pairs
   int n_lg;            // long-range Gaussians M - m
+  int n_lg_used;       // those with c2_l k_min^2 <= lg_xmax for the smallest mode k != 0
+  double lg_xmax;      // terms with c2_l |k|^2 > lg_xmax are dropped: 80 in FP64,
+                       // 20 in FP32 (below 1e-8 of the mode's largest term)
   int lps;             // parity block edge ceil(P_cheb / 2)
   int lpst;            // row stride of a parity block (lps rounded up to 4)
   int long_fused;      // y pass, contraction and inverse y pass in one kernel
@@ -244,7 +247,8 @@ cudaError_t fft_prepare();
 bool fft_len_ok(int prec, const FftLen& f);
 // Whether the fused y pass (all P_cheb planes of one half-spectrum column in
 // one CTA's shared memory) fits, for element size es.
-bool long_fused_fits(int P, const FftLen& fy, size_t es);
+bool long_fused_fits(int P, const FftLen& fy, int nl, size_t es);
+size_t long_fused_smem(int P, const FftLen& fy, int nl, size_t es);
 
 // One-time kernel attributes for the plan's element type (sog_kernels.cu).
 cudaError_t prepare_kernels(int prec);

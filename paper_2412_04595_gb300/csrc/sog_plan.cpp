@@ -670,7 +670,6 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   if (p->has_long && !p->long_direct) {
     add_len(Ilx, p->flx);
     add_len(Ily, p->fly);
-    p->long_fused = sogk::long_fused_fits(P, p->fly, es) ? 1 : 0;
   }
   if (tw.empty()) tw.assign(4, 0.0);
   if ((p->has_mid && !(sogk::fft_len_ok(prec, p->fx) && sogk::fft_len_ok(prec, p->fy) &&
@@ -798,11 +797,21 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
               lbl[(((size_t)li * 2 + par) * ps + i) * pst + j] =
                   Bl[((size_t)li * P + 2 * i + par) * P + 2 * j + par];
       lcl.resize((size_t)2 * nl);
+      // the smallest mode k != 0 bounds the Gaussians any mode uses: s_l grows
+      // with l, and terms with c2_l k^2 > 80 are dropped
+      const double kmin = 2.0 * kPi / std::max(L[0], L[1]);
+      // a term with c2_l k^2 = x weighs about b^dl e^-x against the mode's
+      // largest (x of order 1; the weights w_l s_l^2 grow like b^l): x = 20
+      // leaves it below 1e-8 of that term, under FP32 rounding
+      p->lg_xmax = prec == SOG_PREC_FP64 ? 80.0 : 20.0;
+      p->n_lg_used = 0;
       for (int li = 0; li < nl; ++li) {
         const int l = prm.m + 1 + li;
         lcl[2 * li] = kPi / (L[0] * L[1]) * w[l] * s[l] * s[l];
         lcl[2 * li + 1] = 0.25 * s[l] * s[l];
+        if (lcl[2 * li + 1] * kmin * kmin <= p->lg_xmax) p->n_lg_used = li + 1;
       }
+      p->long_fused = sogk::long_fused_fits(P, p->fly, p->n_lg_used, es) ? 1 : 0;
       const double shp = eff_shape(prm.shape_long, prec), hw = eff_half(p->wl.half, prec);
       WinFT fx(prm.window, shp, hw * p->hl[0], prec);
       WinFT fy(prm.window, shp, hw * p->hl[1], prec);
