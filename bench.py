@@ -366,9 +366,47 @@ def run_ours(args, wl, rank, world):
                  "desc": "the same workload, inputs and parameters through an FP64 plan",
                  "phi": phi64.cpu().numpy(), "F": F64.cpu().numpy(), "E": float(E64.item())}
         p64.close()
+    md = None
+    if not args.no_md:
+        md = md_rate(B, plan, q, r, dev, stream, flush)
     plan.close()
     return dict(prm=prm, stage_ms=stage_ms, value=value, total_ms=total_ms, launches=launches,
+                md=md,
                 clocks=clk, e2e=e2e, E=E_h, F=F_h, phi=phi_h, q=q, r=r, plain=plain, es=es)
+
+
+def md_rate(B, plan, q, r, dev, stream, flush, steps=50, sort_every=10):
+    """Velocity-Verlet steps through sog_md_step on the workload (the plan
+    reused, particles re-sorted into cell order every sort_every steps):
+    steps per second, L2 flushed before each timed block of sort_every steps."""
+    import numpy as np
+    import torch
+    N = plan.N
+    rng = np.random.default_rng(11)
+    qt = torch.tensor(q, device=dev)
+    rt = torch.tensor(r, device=dev)
+    vt = torch.tensor(rng.normal(0.0, 0.05, (N, 3)).astype(q.dtype), device=dev)
+    F = torch.empty(N, 3, dtype=plan.dtype, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    order = torch.arange(N, dtype=torch.int32, device=dev)
+    plan.eval(qt, rt, None, E, F, stream=stream)
+    md = B.MD(plan)
+    md.step(qt, rt, vt, F, 1e-4, nsteps=2 * sort_every, E=E, sort_every=sort_every, order=order,
+            stream=stream)
+    torch.cuda.synchronize()
+    blocks = max(1, steps // sort_every)
+    ms = sum(timed_steps(lambda: md.step(qt, rt, vt, F, 1e-4, nsteps=sort_every, E=E,
+                                         sort_every=sort_every, order=order, stream=stream),
+                         blocks, stream, flush))
+    st = plan.check()
+    md.close()
+    if st != 0:
+        raise RuntimeError("MD steps reported status %d" % st)
+    n = blocks * sort_every
+    return {"steps_per_s": n / (ms * 1e-3), "particle_steps_per_s": N * n / (ms * 1e-3),
+            "ms_per_step": ms / n, "sort_every": sort_every, "steps": n,
+            "desc": "sog_md_step: velocity Verlet (kick, drift, evaluation, kick), plan reused, "
+                    "particles re-sorted into cell order every %d steps" % sort_every}
 
 
 def rel_errors(phi, F, ref_phi, ref_F):
@@ -666,6 +704,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-plain-fp64", action="store_true")
+    ap.add_argument("--no-md", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -720,6 +759,8 @@ def main():
             "peaks": {k: v for k, v in peaks.items()},
             "params": {k: prm[k] for k in ("rc", "M", "m", "I", "P_win", "I_long", "P_long",
                                            "P_cheb", "long_direct")}}
+    if res["md"] is not None:
+        line["md"] = res["md"]
     if res["plain"] is not None:
         line["plain_fp64"] = {k: v for k, v in res["plain"].items() if k not in ("phi", "F", "E")}
         line["speedup_vs_plain_fp64"] = res["value"] / (world * res["plain"]["value"])

@@ -322,6 +322,36 @@ sog_status sog_assemble_noalloc(int64_t N, int32_t precision, const sog_params* 
                                 const void* q, const double* phi_parts, const double* grad_parts,
                                 void* phi, double* E, void* F, void* stream);
 
+/*
+ * Molecular dynamics with repeated evaluations (the use the paper's C^1
+ * split of Sec. 2.2, Eq. 2.23-2.24, is built for).  A sog_md drives one plan
+ * through velocity-Verlet steps of length dt:
+ *   v += dt/2 F/m;  r += dt v (x, y wrapped by one period, z reflected at
+ *   the walls z = +-Lz/2 with v_z reversed);  F = forces at r (sog_eval, the
+ *   energy of the step to *E);  v += dt/2 F/m.
+ * The plan, its workspaces and its captured evaluation are reused by every
+ * step.  With sort_every > 0, after every sort_every-th step the arrays q,
+ * r, v, F, inv_mass and order are permuted in place into the near-field cell
+ * order of that step's evaluation, so that the next steps' binning sorts
+ * nearly sorted input; order[] (initialise it to 0..N-1) then tells the
+ * original index of each slot.
+ *   sog_md_create: allocates N x 3 elements of scratch; *md owned by the
+ *     caller, released by sog_md_destroy (before the plan).
+ *   sog_md_step: nsteps steps; q [N], r [N x 3], v [N x 3], F [N x 3] device
+ *     arrays of the plan's type, F holding the forces at r on entry (one
+ *     sog_eval before the first call) and on return; inv_mass [N] (plan
+ *     type) or NULL for unit masses; E device double or NULL; order [N]
+ *     int32 device, required when sort_every > 0.  Enqueued on `stream`.
+ *     Data errors (a z outside the box after a step cannot occur; charges
+ *     not neutral, non-finite values) are reported by sog_plan_check.
+ */
+typedef struct sog_md sog_md;
+sog_status sog_md_create(sog_md** md, sog_plan* plan);
+sog_status sog_md_step(sog_md* md, void* q, void* r, void* v, void* F, void* inv_mass, double dt,
+                       int32_t nsteps, int32_t sort_every, double* E, int32_t* order,
+                       void* stream);
+void sog_md_destroy(sog_md* md);
+
 /* Release the plan and its device memory (waits for its pending work). */
 void sog_plan_destroy(sog_plan* plan);
 

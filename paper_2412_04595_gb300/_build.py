@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsog.so")
 SOURCES = ["sog_plan.cpp", "sog_kernels.cu", "sog_fft.cu", "sog_noalloc.cu", "sog_batch.cpp", "sog_mlp.cu",
-           "sog_peak.cu"]
+           "sog_peak.cu", "sog_md.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

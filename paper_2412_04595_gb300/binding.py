@@ -94,6 +94,10 @@ def load(build_if_missing: bool = False):
     L.sog_plan_launches.argtypes = [vp]
     L.sog_plan_launches.restype = i64
     L.sog_measure_fma_peak.argtypes = [i32, ctypes.POINTER(d)]
+    L.sog_md_create.argtypes = [ctypes.POINTER(vp), vp]
+    L.sog_md_step.argtypes = [vp, vp, vp, vp, vp, vp, d, i32, i32, vp, vp, vp]
+    L.sog_md_destroy.argtypes = [vp]
+    L.sog_md_destroy.restype = None
     L.sog_status_str.argtypes = [ctypes.c_int]
     L.sog_status_str.restype = ctypes.c_char_p
     L.sog_assemble_noalloc.argtypes = [i64, i32, ctypes.POINTER(SogParams), vp, vp, vp, vp, vp,
@@ -491,6 +495,43 @@ class MLP:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.sog_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MD:
+    """Owns one ``sog_md``: velocity-Verlet steps with a plan's forces
+    (sog_md_step).  Tensors are contiguous CUDA tensors of the plan's dtype:
+    q [N], r, v, F [N, 3], inv_mass [N] or None; order int32 [N] or None."""
+
+    def __init__(self, plan):
+        self._lib = load()
+        self.plan = plan
+        h = ctypes.c_void_p()
+        _check(self._lib.sog_md_create(ctypes.byref(h), plan._h), "sog_md_create")
+        self._h = h
+
+    def step(self, q, r, v, F, dt, nsteps=1, inv_mass=None, E=None, sort_every=0, order=None,
+             stream=None):
+        import torch
+        N, dt_ = self.plan.N, self.plan.dtype
+        if sort_every > 0 and order is None:
+            raise ValueError("order is required when sort_every > 0")
+        _require((q, "q", dt_, N), (r, "r", dt_, 3 * N), (v, "v", dt_, 3 * N),
+                 (F, "F", dt_, 3 * N), (inv_mass, "inv_mass", dt_, N),
+                 (E, "E", torch.float64, 1, True), (order, "order", torch.int32, N))
+        _check(self._lib.sog_md_step(self._h, _ptr(q), _ptr(r), _ptr(v), _ptr(F), _ptr(inv_mass),
+                                     float(dt), int(nsteps), int(sort_every), _ptr(E),
+                                     _ptr(order), _stream_ptr(stream)), "sog_md_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sog_md_destroy(self._h)
             self._h = None
 
     def __del__(self):
