@@ -702,6 +702,100 @@ def long_range(prm, q, r, tgt=None):
     return phi, grad
 
 
+def taylor_coefficients(prm, k2, Q):
+    """A_p(k) of App. C for p < Q (without the window factor):
+        A_p(k) = ((-1)^p / p!) sum_{l>m} w_l s_l^2 (Lz / s_l)^{2p} e^{-s_l^2 |k|^2 / 4},
+    the factor of the p-th Taylor moment grid in the scaled spectrum.
+    READING (g2): the exponent uses |k|^2 (the printed e^{-s_l^2 k/4} drops
+    the square)."""
+    w, s = sog_weights(prm["b"], prm["sigma"], prm["omega"], prm["M"])
+    Lz = prm["L"][2]
+    A = np.zeros((Q,) + np.shape(k2))
+    for l in range(prm["m"] + 1, prm["M"] + 1):
+        e = w[l] * s[l] ** 2 * np.exp(-s[l] ** 2 * np.asarray(k2) / 4.0)
+        for p_ in range(Q):
+            A[p_] += (-1) ** p_ / math.factorial(p_) * (Lz / s[l]) ** (2 * p_) * e
+    return A
+
+
+def taylor_remainder_bound(prm, Q):
+    """Remainder of the Q-term Taylor expansion of every long-range Gaussian
+    e^{-d^2/s_l^2} (Lemma C.1).  READING (g4): the argument is a difference
+    d = z - z_j of two points in [-Lz/2, Lz/2], so |d| <= Lz and the bound is
+    1 / (Q! eta^{2Q}) with eta = s_{m+1} / Lz (the printed 1/(Q! (2 eta)^{2Q})
+    assumes |d| <= Lz/2)."""
+    _, s = sog_weights(prm["b"], prm["sigma"], prm["omega"], prm["M"])
+    eta = s[prm["m"] + 1] / prm["L"][2]
+    return 1.0 / (math.factorial(Q) * eta ** (2 * Q))
+
+
+def long_range_taylor(prm, q, r, Q, tgt=None):
+    """Long range without its k = 0 mode by the Taylor-moment variant of
+    Algorithm 2 (App. C): Q moment grids per Chebyshev proxy plane,
+        S^p(rho_g, z_c) = sum_j q_j W2(rho_g - rho_j) ((z_c - z_j) / Lz)^{2p},
+    2D FFTs divided by the window transform, the scaled spectrum
+        nu_c(k) = (pi/A) sum_p A_p(k) S^p_c(k)                   (k != 0)
+    and the gathering of Algorithm 2 (window in x, y; Lagrange interpolation
+    from the proxy points z_c to z_i).  The source's z enters exactly through
+    the Taylor polynomial; only the target side is interpolated."""
+    q = np.asarray(q, dtype=np.float64)
+    r = _wrap_xy(prm, r)
+    tgt, tr = _targets(r, tgt)
+    if prm["m"] >= prm["M"]:
+        return np.zeros(tgt.size), np.zeros((tgt.size, 3))
+    Lx, Ly, Lz = prm["L"]
+    Ilx, Ily = prm["I_long"]
+    hx, hy = Lx / Ilx, Ly / Ily
+    P = prm["P_cheb"]
+    zc = cheb_nodes(P, Lz)
+    win = make_window(prm["window"], prm["P_long"], prm["shape_long"])
+    gx, wx, _ = win.weights((r[:, 0] + Lx / 2) / hx)
+    gy, wy, _ = win.weights((r[:, 1] + Ly / 2) / hy)
+    gx %= Ilx
+    gy %= Ily
+    kx = 2 * PI * np.fft.fftfreq(Ilx, d=hx)
+    ky = 2 * PI * np.fft.fftfreq(Ily, d=hy)
+    W2 = win.ft(kx, win.half * hx)[:, None] * win.ft(ky, win.half * hy)[None, :]
+    k2 = kx[:, None] ** 2 + ky[None, :] ** 2
+    Acoef = taylor_coefficients(prm, k2, Q)
+    nu = np.zeros((P, Ilx, Ily), dtype=complex)
+    for c in range(P):
+        dz2 = ((zc[c] - r[:, 2]) / Lz) ** 2
+        for p_ in range(Q):
+            G = np.zeros(Ilx * Ily)
+            mom = q * dz2 ** p_
+            for dy in range(win.P):
+                idx = (gx * Ily + gy[:, dy:dy + 1]).ravel()
+                G += np.bincount(idx, weights=((mom * wy[:, dy])[:, None] * wx).ravel(),
+                                 minlength=Ilx * Ily)
+            Sk = np.fft.fft2(G.reshape(Ilx, Ily)) * (hx * hy) / W2
+            nu[c] += Acoef[p_] * Sk
+    nu[:, 0, 0] = 0.0
+    A = Lx * Ly
+    u = np.fft.ifft2(nu * (PI / A) * (hx * hy) / W2[None]).real * (Ilx * Ily)
+    Lt, dLt = lagrange(zc, tr[:, 2])
+    gx, wx, dwx = win.weights((tr[:, 0] + Lx / 2) / hx)
+    gy, wy, dwy = win.weights((tr[:, 1] + Ly / 2) / hy)
+    gx %= Ilx
+    gy %= Ily
+    phi = np.zeros(tgt.size)
+    grad = np.zeros((tgt.size, 3))
+    for c in range(P):
+        Sc = np.zeros(tgt.size)
+        Sx = np.zeros(tgt.size)
+        Sy = np.zeros(tgt.size)
+        for dy in range(win.P):
+            vals = u[c][gx, gy[:, dy:dy + 1]]
+            Sc += np.sum(vals * wx, axis=1) * wy[:, dy]
+            Sx += np.sum(vals * dwx, axis=1) * wy[:, dy]
+            Sy += np.sum(vals * wx, axis=1) * dwy[:, dy]
+        phi += Lt[:, c] * Sc
+        grad[:, 0] += Lt[:, c] * Sx / hx
+        grad[:, 1] += Lt[:, c] * Sy / hy
+        grad[:, 2] += dLt[:, c] * Sc
+    return phi, grad
+
+
 def long_range_direct(prm, q, r, tgt=None):
     """Long range without its k = 0 mode by Algorithm 3 (no FFT), in the same
     anterpolation reading: for the modes k = (2 pi n_x / Lx, 2 pi n_y / Ly),
