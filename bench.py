@@ -271,6 +271,13 @@ def run_ours(args, wl, rank, world):
     dt = plan.dtype
     qt = torch.tensor(q, device=dev)
     rt = torch.tensor(r, device=dev)
+    tune = None
+    if not args.no_autotune:
+        # tile edges and CTAs per tile timed on this workload (excluded from
+        # the timed region, like the plan's creation)
+        t0 = time.perf_counter()
+        tiles = plan.autotune(qt, rt, reps=3)
+        tune = dict(tiles, seconds=time.perf_counter() - t0)
     phi = torch.empty(N, dtype=dt, device=dev)
     F = torch.empty(N, 3, dtype=dt, device=dev)
     E = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -371,7 +378,7 @@ def run_ours(args, wl, rank, world):
         md = md_rate(B, plan, q, r, dev, stream, flush)
     plan.close()
     return dict(prm=prm, stage_ms=stage_ms, value=value, total_ms=total_ms, launches=launches,
-                md=md,
+                md=md, tune=tune,
                 clocks=clk, e2e=e2e, E=E_h, F=F_h, phi=phi_h, q=q, r=r, plain=plain, es=es)
 
 
@@ -705,6 +712,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-plain-fp64", action="store_true")
     ap.add_argument("--no-md", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -761,6 +769,8 @@ def main():
                                            "P_cheb", "long_direct")}}
     if res["md"] is not None:
         line["md"] = res["md"]
+    if res["tune"] is not None:
+        line["autotuned_tiles"] = res["tune"]
     if res["plain"] is not None:
         line["plain_fp64"] = {k: v for k, v in res["plain"].items() if k not in ("phi", "F", "E")}
         line["speedup_vs_plain_fp64"] = res["value"] / (world * res["plain"]["value"])

@@ -210,6 +210,24 @@ sog_status sog_plan_get_timing(sog_plan* plan, float* ms);
 int64_t sog_plan_launches(const sog_plan* plan);
 
 /*
+ * Autotuner of the gridding and gathering tiles (the paper selects no tiles;
+ * an implementation choice timed on this GPU).  Tries mid-range tile edges
+ * {8, 12, 16, 20, 23} (evened out over the grid, tile edge + window support
+ * <= 32) and 0.5, 1 and 2 times the default number of CTAs per tile, timing
+ * the mid gridding plus gathering stages of `reps` evaluations of (q, r)
+ * (device arrays as in sog_eval) each in isolation (timing mode 2), and
+ * keeps the fastest; then the same for the long-range tiles (gridded form
+ * with several tiles).  Results are unchanged up to rounding.  Synchronous;
+ * on return the plan's timing mode is restored and its captured evaluations
+ * are released.  reps in 1..100.
+ * sog_plan_tiles writes to host out[4]: mid tile edge, mid CTAs per tile,
+ * long tile edge, long CTAs per tile (0 where the part is absent).
+ */
+sog_status sog_plan_autotune(sog_plan* plan, const void* q, const void* r, int32_t reps,
+                             void* stream);
+sog_status sog_plan_tiles(const sog_plan* plan, int32_t* out);
+
+/*
  * Measured fused multiply-add rate of the current device (a measurement
  * utility; the paper has no counterpart): FP32 (precision SOG_PREC_MIXED) or
  * FP64 (SOG_PREC_FP64) FMAs in independent chains on every SM, timed with

@@ -94,6 +94,8 @@ def load(build_if_missing: bool = False):
     L.sog_plan_launches.argtypes = [vp]
     L.sog_plan_launches.restype = i64
     L.sog_measure_fma_peak.argtypes = [i32, ctypes.POINTER(d)]
+    L.sog_plan_autotune.argtypes = [vp, vp, vp, i32, vp]
+    L.sog_plan_tiles.argtypes = [vp, ctypes.POINTER(i32)]
     L.sog_md_create.argtypes = [ctypes.POINTER(vp), vp]
     L.sog_md_step.argtypes = [vp, vp, vp, vp, vp, vp, d, i32, i32, vp, vp, vp]
     L.sog_md_destroy.argtypes = [vp]
@@ -336,6 +338,19 @@ class Plan:
 
     def launches(self) -> int:
         return int(self._lib.sog_plan_launches(self._h))
+
+    def autotune(self, q, r, reps=3, stream=None):
+        """sog_plan_autotune on (q, r); returns the chosen tiles."""
+        self._check_io(q, r)
+        _check(self._lib.sog_plan_autotune(self._h, _ptr(q), _ptr(r), int(reps),
+                                           _stream_ptr(stream)), "sog_plan_autotune")
+        return self.tiles()
+
+    def tiles(self) -> dict:
+        out = (ctypes.c_int32 * 4)()
+        _check(self._lib.sog_plan_tiles(self._h, out), "sog_plan_tiles")
+        return {"mid_tile": out[0], "mid_ctas_per_tile": out[1], "long_tile": out[2],
+                "long_ctas_per_tile": out[3]}
 
     def check(self) -> int:
         return int(self._lib.sog_plan_check(self._h))

@@ -193,6 +193,9 @@ struct sog_plan {
   int* d_rank;         // 3 x N
   int* d_cnt;          // counts / starts of the three bin sets
   int cnt_off[4];
+  int cnt_cap;         // entries of d_cnt (sized for the smallest tiles the autotuner tries)
+  int mid_T, long_T;   // nominal tile edges of the current tiling
+  double mid_cscale, long_cscale;  // CTAs per tile relative to the default rule
   double* d_parts_phi;   // 4 x N
   double* d_parts_grad;  // 4 x N x 3
   double* d_red;         // reduction partials
@@ -249,6 +252,11 @@ bool fft_len_ok(int prec, const FftLen& f);
 // one CTA's shared memory) fits, for element size es.
 bool long_fused_fits(int P, const FftLen& fy, int nl, size_t es);
 size_t long_fused_smem(int P, const FftLen& fy, int nl, size_t es);
+
+// Dynamic shared memory of the mid / long gridding (gather = false) and
+// gathering kernels for the plan's current tiles (sog_kernels.cu).
+size_t mid_smem(const sog_plan* p, size_t es, bool gather);
+size_t long_smem(const sog_plan* p, size_t es, bool gather);
 
 // One-time kernel attributes for the plan's element type (sog_kernels.cu).
 cudaError_t prepare_kernels(int prec);

@@ -2134,7 +2134,7 @@ static cudaError_t allow_pw() {
   return e;
 }
 
-static size_t mid_smem(const sog_plan* p, size_t es, bool gather) {
+size_t mid_smem(const sog_plan* p, size_t es, bool gather) {
   const TileGeom& g = p->gm;
   const int P = p->wm.P;
   const int rp = gather_row_pitch(g.W[0]);
@@ -2144,7 +2144,7 @@ static size_t mid_smem(const sog_plan* p, size_t es, bool gather) {
   // fixed-point tile: int32 for FP32, int64 for FP64 (same size as T)
   return kTileHeader + ((size_t)kTileBatch * 3 * kMaxWin + tile) * es;
 }
-static size_t long_smem(const sog_plan* p, size_t es, bool gather) {
+size_t long_smem(const sog_plan* p, size_t es, bool gather) {
   const TileGeom& g = p->gl;
   const int P = p->prm.P_cheb;
   const int rp = gather_row_pitch(g.W[0]);

@@ -468,6 +468,62 @@ bool near_table(const std::vector<double>& w, const std::vector<double>& s, doub
 }
 
 
+// CTAs per tile of the gridding and gathering: enough CTAs in all (about
+// 600) while each keeps at least 32 charges; `scale` multiplies the rule.
+int tile_chunks(int64_t N, int ntiles, double scale) {
+  const double per_tile = (double)N / ntiles;
+  int ch = (int)ceil(scale * 600.0 / ntiles);
+  ch = std::max(1, std::min(ch, (int)(per_tile / 32.0)));
+  return std::max(1, ch);
+}
+
+// Mid-range tiling: as many tiles per dimension as edge T needs, their edge
+// evened out over the grid (120 = 8 x 15).
+void set_mid_tiles(sog_plan* p, int T, double scale) {
+  sogk::TileGeom& g = p->gm;
+  for (int d = 0; d < 3; ++d) {
+    g.I[d] = p->prm.I[d];
+    const int nt = (g.I[d] + T - 1) / T;
+    g.T[d] = (g.I[d] + nt - 1) / nt;
+    g.nt[d] = (g.I[d] + g.T[d] - 1) / g.T[d];
+    g.W[d] = g.T[d] + p->prm.P_win;
+  }
+  g.pad_lo = (int)floor(p->wm.half);
+  g.pitch = p->prm.I[0] + 2;
+  p->n_tiles_mid = g.nt[0] * g.nt[1] * g.nt[2];
+  g.chunks = tile_chunks(p->N, p->n_tiles_mid, scale);
+  p->mid_T = T;
+  p->mid_cscale = scale;
+}
+
+// Long-range tiling of the proxy planes (2D tiles of edge T).
+void set_long_tiles(sog_plan* p, int T, double scale) {
+  sogk::TileGeom& g = p->gl;
+  g.I[0] = p->prm.I_long[0];
+  g.I[1] = p->prm.I_long[1];
+  g.I[2] = 1;
+  for (int d = 0; d < 2; ++d) {
+    g.T[d] = std::min(T, g.I[d]);
+    g.nt[d] = (g.I[d] + g.T[d] - 1) / g.T[d];
+    g.W[d] = g.T[d] + p->prm.P_long;
+  }
+  g.T[2] = g.nt[2] = g.W[2] = 1;
+  g.pad_lo = (int)floor(p->wl.half);
+  g.pitch = p->prm.I_long[0] + 2;
+  p->n_tiles_long = g.nt[0] * g.nt[1];
+  g.chunks = tile_chunks(p->N, p->n_tiles_long, scale);
+  p->long_T = T;
+  p->long_cscale = scale;
+}
+
+// Offsets of the three bin-count arrays in d_cnt for the current tiles.
+void set_cnt_offsets(sog_plan* p) {
+  p->cnt_off[0] = 0;
+  p->cnt_off[1] = p->n_cells + 1;
+  p->cnt_off[2] = p->cnt_off[1] + (p->has_mid ? p->n_tiles_mid + 1 : 1);
+  p->cnt_off[3] = p->cnt_off[2] + (p->has_long ? p->n_tiles_long + 1 : 1);
+}
+
 template <typename T>
 void put(std::vector<unsigned char>& buf, size_t off, const std::vector<double>& v) {
   T* d = reinterpret_cast<T*>(buf.data() + off);
@@ -589,24 +645,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     int T = 16;
     if (prec == SOG_PREC_FP64 || (size_t)(16 + prm.P_win) * (16 + prm.P_win) * (16 + prm.P_win) * es > 72 * 1024)
       T = 8;
-    sogk::TileGeom& g = p->gm;
-    g.I[0] = Ix;
-    g.I[1] = Iy;
-    g.I[2] = Iz;
-    for (int d = 0; d < 3; ++d) {
-      // as many tiles as edge T needs, their edge evened out (120 = 8 x 15)
-      const int nt = (g.I[d] + T - 1) / T;
-      g.T[d] = (g.I[d] + nt - 1) / nt;
-      g.nt[d] = (g.I[d] + g.T[d] - 1) / g.T[d];
-      g.W[d] = g.T[d] + prm.P_win;
-    }
-    g.pad_lo = (int)floor(p->wm.half);
-    g.pitch = Ix + 2;
-    p->n_tiles_mid = g.nt[0] * g.nt[1] * g.nt[2];
-    const double per_tile = (double)N / p->n_tiles_mid;
-    int ch = (int)ceil(600.0 / p->n_tiles_mid);
-    ch = std::max(1, std::min(ch, (int)(per_tile / 32.0)));
-    g.chunks = std::max(1, ch);
+    set_mid_tiles(p, T, 1.0);
   }
   p->long_direct = p->has_long && prm.long_direct;
   if (p->long_direct) {
@@ -619,28 +658,12 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     p->wl = sogk::WinPar{prm.P_long, prm.window, 0.5 * (prm.P_long - 1), prm.shape_long};
     int T = 16;
     if ((size_t)P * ((16 + prm.P_long) * (16 + prm.P_long) + 1) * es > 96 * 1024) T = 8;
-    sogk::TileGeom& g = p->gl;
-    g.I[0] = Ilx;
-    g.I[1] = Ily;
-    g.I[2] = 1;
-    for (int d = 0; d < 2; ++d) {
-      g.T[d] = std::min(T, g.I[d]);
-      g.nt[d] = (g.I[d] + g.T[d] - 1) / g.T[d];
-      g.W[d] = g.T[d] + prm.P_long;
-    }
-    g.T[2] = g.nt[2] = g.W[2] = 1;
-    g.pad_lo = (int)floor(p->wl.half);
-    g.pitch = Ilx + 2;
-    p->n_tiles_long = g.nt[0] * g.nt[1];
+    set_long_tiles(p, T, 1.0);
     // one tile covering the grid and planes that fit shared memory: private
     // copies per CTA plus a reduction instead of atomics on a few addresses
-    p->long_small = (g.nt[0] == 1 && g.nt[1] == 1 &&
+    p->long_small = (p->gl.nt[0] == 1 && p->gl.nt[1] == 1 &&
                      (size_t)P * (Ilx * Ily + 1) * es <= 64 * 1024) ? 1 : 0;
     p->long_small_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(p->red_blocks, N / 128));
-    const double per_tile = (double)N / p->n_tiles_long;
-    int ch = (int)ceil(600.0 / p->n_tiles_long);
-    ch = std::max(1, std::min(ch, (int)(per_tile / 32.0)));
-    g.chunks = std::max(1, ch);
   }
 
   // FFT lengths and twiddles exp(-2 pi i t/n): FP64 (cos, sin); FP32
@@ -879,11 +902,20 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   const size_t o_perm = ar.take((size_t)3 * N * sizeof(int));
   const size_t o_key = ar.take((size_t)3 * N * sizeof(int));
   const size_t o_rank = ar.take((size_t)3 * N * sizeof(int));
-  p->cnt_off[0] = 0;
-  p->cnt_off[1] = p->n_cells + 1;
-  p->cnt_off[2] = p->cnt_off[1] + (p->has_mid ? p->n_tiles_mid + 1 : 1);
-  p->cnt_off[3] = p->cnt_off[2] + (p->has_long ? p->n_tiles_long + 1 : 1);
-  const size_t o_cnt = ar.take((size_t)p->cnt_off[3] * sizeof(int));
+  set_cnt_offsets(p);
+  // room for the smallest tiles the autotuner tries (edge 8)
+  {
+    auto ntiles = [](const int* I, int nd, int T) {
+      long n = 1;
+      for (int d = 0; d < nd; ++d) n *= (I[d] + T - 1) / T;
+      return n;
+    };
+    const long mid_max = p->has_mid ? ntiles(prm.I, 3, 8) : 0;
+    const long long_max = (p->has_long && !p->long_direct) ? ntiles(prm.I_long, 2, 8) : 0;
+    p->cnt_cap = (int)(p->n_cells + 1 + std::max<long>(mid_max, p->n_tiles_mid) + 1 +
+                       std::max<long>(long_max, p->n_tiles_long) + 1);
+  }
+  const size_t o_cnt = ar.take((size_t)p->cnt_cap * sizeof(int));
   const size_t o_pp = ar.take((size_t)4 * N * sizeof(double));
   const size_t o_pg = ar.take((size_t)12 * N * sizeof(double));
   const size_t o_red = ar.take((size_t)p->red_blocks * (3 + sogk::kMaxCheb) * sizeof(double));
@@ -1082,6 +1114,108 @@ sog_status sog_plan_get_timing(sog_plan* plan, float* ms) {
 }
 
 int64_t sog_plan_launches(const sog_plan* plan) { return plan ? plan->launches : 0; }
+
+sog_status sog_plan_tiles(const sog_plan* plan, int32_t* out) {
+  if (!plan || !out) return SOG_ERR_ARG;
+  out[0] = plan->has_mid ? plan->mid_T : 0;
+  out[1] = plan->has_mid ? plan->gm.chunks : 0;
+  out[2] = (plan->has_long && !plan->long_direct) ? plan->long_T : 0;
+  out[3] = (plan->has_long && !plan->long_direct) ? plan->gl.chunks : 0;
+  return SOG_OK;
+}
+
+sog_status sog_plan_autotune(sog_plan* plan, const void* q, const void* r, int32_t reps,
+                             void* stream) {
+  if (!plan || !q || !r || reps < 1 || reps > 100) return SOG_ERR_ARG;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int saved = plan->timing;
+  sog_status st = sog_plan_set_timing(plan, 2);
+  if (st != SOG_OK) return st;
+  const size_t es = plan->prec == SOG_PREC_FP64 ? sizeof(double) : sizeof(float);
+  // isolated time of stages a and b (gridding and gathering), median of reps
+  auto measure = [&](int a, int b, float* out) -> sog_status {
+    std::vector<float> v;
+    for (int i = 0; i <= reps; ++i) {
+      sog_status e = sogk::eval_device(plan, q, r, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+      if (e != SOG_OK) return e;
+      float ms[SOG_NSTAGES];
+      e = sog_plan_get_timing(plan, ms);
+      if (e != SOG_OK) return e;
+      if (i > 0) v.push_back(ms[a] + ms[b]);  // the first run captures the graph
+    }
+    std::sort(v.begin(), v.end());
+    *out = v[v.size() / 2];
+    return SOG_OK;
+  };
+  const int Ts[] = {8, 12, 16, 20, 23};
+  const double scales[] = {0.5, 1.0, 2.0};
+  const size_t smem_cap = (size_t)sogk::kMaxDynSmem - 4096;
+  // mid range: stages 2 (gridding) and 4 (gathering)
+  if (plan->has_mid && st == SOG_OK) {
+    int bT = plan->mid_T;
+    double bs = plan->mid_cscale;
+    float best = 0.0f;
+    st = measure(2, 4, &best);
+    for (int T : Ts) {
+      if (st != SOG_OK) break;
+      if (T + plan->prm.P_win > 32) continue;  // row tables of 32 entries
+      for (double sc : scales) {
+        if (T == bT && sc == bs) continue;
+        set_mid_tiles(plan, T, sc);
+        set_cnt_offsets(plan);
+        if (plan->cnt_off[3] > plan->cnt_cap || sogk::mid_smem(plan, es, false) > smem_cap ||
+            sogk::mid_smem(plan, es, true) > smem_cap)
+          continue;
+        sogk::release_graphs(plan);
+        float t = 0.0f;
+        st = measure(2, 4, &t);
+        if (st != SOG_OK) break;
+        if (t < best) {
+          best = t;
+          bT = T;
+          bs = sc;
+        }
+      }
+    }
+    set_mid_tiles(plan, bT, bs);
+    set_cnt_offsets(plan);
+  }
+  // long range (gridded form, several tiles): stages 5 and 7
+  if (plan->has_long && !plan->long_direct && !plan->long_small && st == SOG_OK) {
+    int bT = plan->long_T;
+    double bs = plan->long_cscale;
+    sogk::release_graphs(plan);
+    float best = 0.0f;
+    st = measure(5, 7, &best);
+    for (int T : Ts) {
+      if (st != SOG_OK) break;
+      if (T + plan->prm.P_long > 32) continue;
+      for (double sc : scales) {
+        if (T == bT && sc == bs) continue;
+        set_long_tiles(plan, T, sc);
+        set_cnt_offsets(plan);
+        if (plan->cnt_off[3] > plan->cnt_cap || plan->gl.nt[0] * plan->gl.nt[1] < 2 ||
+            sogk::long_smem(plan, es, false) > smem_cap ||
+            sogk::long_smem(plan, es, true) > smem_cap)
+          continue;
+        sogk::release_graphs(plan);
+        float t = 0.0f;
+        st = measure(5, 7, &t);
+        if (st != SOG_OK) break;
+        if (t < best) {
+          best = t;
+          bT = T;
+          bs = sc;
+        }
+      }
+    }
+    set_long_tiles(plan, bT, bs);
+    set_cnt_offsets(plan);
+  }
+  sogk::release_graphs(plan);
+  const sog_status st2 = sog_plan_set_timing(plan, saved);
+  return st != SOG_OK ? st : st2;
+}
 
 void sog_plan_destroy(sog_plan* plan) {
   if (!plan) return;
