@@ -827,6 +827,7 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
   constexpr int CAP = FftCfg<T>::cap;
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) unsigned long long bar;
+  __shared__ int ynext;
   T2* buf = reinterpret_cast<T2*>(smraw);
   const int c = blockIdx.x >> 1, par = blockIdx.x & 1, Iy = fy.n;
   const int np0 = (P + 1) / 2, np = par ? P / 2 : np0;
@@ -850,6 +851,7 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
     sB[i] = lbl[((size_t)l * 2 + par) * bsz + (i - l * bsz)];
   }
   for (int l = threadIdx.x; l < nl; l += blockDim.x) sC[l] = lcl[l];
+  if (threadIdx.x == 0) ynext = 0;
   __syncthreads();
   if (!mbar_wait(&bar, 0)) {
     if (threadIdx.x == 0) atomicOr(status, 4);
@@ -860,13 +862,24 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
   const LineSet ls{Iy, np, Iy, 1, false};
   fft_lines<T2, CAP>(buf, ls, fy, tw, false);
   const T2 fx = lfx[c];
+  // contraction: a warp takes a group of G modes at a time, its lanes over
+  // (mode, chunk of kYpassOut orders); all reads and writes of a mode stay
+  // inside one warp, so groups need no block-wide barrier.  Groups are
+  // handed out in the order 0, last, 1, last - 1, ... (the modes of small
+  // |k_y|, which keep the most Gaussians, first) from a shared counter.
   const int nsplit = (np + kYpassOut - 1) / kYpassOut;
-  const int mr = blockDim.x / nsplit;  // modes per round
-  const int ch = threadIdx.x / mr, yl = threadIdx.x - ch * mr;
-  for (int y0 = 0; y0 < Iy; y0 += mr) {
-    const int y = y0 + yl;
-    const bool act = ch < nsplit && y < Iy;
-    const int i0 = ch * kYpassOut;
+  const int G = 32 / nsplit;
+  const int lane = threadIdx.x & 31;
+  const int ml = lane / nsplit, ch = lane - ml * nsplit, i0 = ch * kYpassOut;
+  const int ngroups = (Iy + G - 1) / G;
+  for (;;) {
+    int gi = 0;
+    if (lane == 0) gi = atomicAdd(&ynext, 1);
+    gi = __shfl_sync(0xffffffffu, gi, 0);
+    if (gi >= ngroups) break;
+    const int grp = (gi & 1) ? ngroups - 1 - (gi >> 1) : (gi >> 1);
+    const int y = grp * G + ml;
+    const bool act = ml < G && y < Iy;
     T2 acc[kYpassOut];
 #pragma unroll
     for (int o = 0; o < kYpassOut; ++o) acc[o] = T2{T(0), T(0)};
@@ -895,14 +908,15 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
         }
       }
     }
-    __syncthreads();  // every input of this round's modes has been read
+    __syncwarp();  // every input of this group's modes has been read
     if (act) {
 #pragma unroll
       for (int o = 0; o < kYpassOut; ++o)
         if (i0 + o < np) buf[(size_t)(i0 + o) * Iy + y] = acc[o];
     }
-    __syncthreads();
+    __syncwarp();
   }
+  __syncthreads();
   fft_lines<T2, CAP>(buf, ls, fy, tw, true);
   fence_async_smem();
   __syncthreads();

@@ -1287,9 +1287,9 @@ __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T
   int* yoff = reinterpret_cast<int*>(zoff + kMaxCheb);             // [32]
   int* bofs = yoff + 32;                                           // [kTileBatch]
   T* red = reinterpret_cast<T*>(bofs + kTileBatch);                // [8]
-  T* wgt = reinterpret_cast<T*>(smraw + kLongSpreadHeader);        // [j][2][kMaxWin]
-  T* tnb = wgt + kTileBatch * 2 * kMaxWin;                         // [j][kMaxCheb]
-  A* st = reinterpret_cast<A*>(tnb + kTileBatch * kMaxCheb);
+  T* wgt = reinterpret_cast<T*>(smraw + kLongSpreadHeader);        // [j][2][Pw]
+  T* tnb = wgt + kTileBatch * 2 * Pw;                         // [j][P]
+  A* st = reinterpret_cast<A*>(tnb + kTileBatch * P);
   const int ty = tile / g.nt[0], tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
   {
@@ -1323,7 +1323,7 @@ __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T
       const T c = ax == 0 ? a.x : a.y;
       const int g0 = (int)dceil(c - w.half);
       const T v = win_val<T, PW == 0>(w, win_arg(((T)(g0 + k) - c), w));
-      wgt[(j * 2 + ax) * kMaxWin + k] = ax == 0 ? v * a.q : v;
+      wgt[(j * 2 + ax) * Pw + k] = ax == 0 ? v * a.q : v;
       if (r == 0) {
         const int gy0 = (int)dceil(a.y - w.half);
         bofs[j] = (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
@@ -1333,7 +1333,7 @@ __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T
       // T_n(x_j) by the three-term recurrence (|x_j| <= 1)
       const T x = rec[p0 + j].z;
       T t0 = T(1), t1 = x;
-      T* tj = tnb + j * kMaxCheb;
+      T* tj = tnb + j * P;
       for (int n = 0; n < P; ++n) {
         tj[n] = t0;
         const T t2 = T(2) * x * t1 - t0;
@@ -1343,8 +1343,8 @@ __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T
     }
     __syncthreads();
     for (int j = warp; j < nb; j += nw) {
-      const T* wj = wgt + j * 2 * kMaxWin;
-      const T* tj = tnb + j * kMaxCheb;
+      const T* wj = wgt + j * 2 * Pw;
+      const T* tj = tnb + j * P;
       T rwx[PR];
 #pragma unroll
       for (int dx = 0; dx < PR; ++dx) rwx[dx] = dx < Pw ? wj[dx] : T(0);
@@ -1353,7 +1353,7 @@ __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T
         const int s2 = lane + 32 * it;
         if (s2 < nrows) {
           const int n = s2 / Pw, dy = s2 - n * Pw;
-          const T c = wj[kMaxWin + dy] * tj[n] * S;
+          const T c = wj[Pw + dy] * tj[n] * S;
           A* rp = bj + n * PS + dy * RP;
 #pragma unroll
           for (int dx = 0; dx < PR; ++dx)
@@ -1529,9 +1529,9 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
   int* yoff = reinterpret_cast<int*>(zoff + kMaxCheb);    // [32]
   int* xoff = yoff + 32;                                  // [32]
   int* bofs = xoff + 32;                                  // [kTileBatch]
-  T* wgt = reinterpret_cast<T*>(smraw + kLongSpreadHeader);  // [j][4][kMaxWin]: w_x, w_x', w_y, w_y'
-  T* tnb = wgt + kTileBatch * 4 * kMaxWin;                   // [j][2][kMaxCheb]: T_n, T_n'
-  T* st = tnb + kTileBatch * 2 * kMaxCheb;
+  T* wgt = reinterpret_cast<T*>(smraw + kLongSpreadHeader);  // [j][4][Pw]: w_x, w_x', w_y, w_y'
+  T* tnb = wgt + kTileBatch * 4 * Pw;                   // [j][2][P]: T_n, T_n'
+  T* st = tnb + kTileBatch * 2 * P;
   const int ty = tile / g.nt[0], tx = tile % g.nt[0];
   const int ox = tx * g.T[0] - g.pad_lo, oy = ty * g.T[1] - g.pad_lo;
   tile_tables(g, oy, 0, P, true, yoff, zoff);
@@ -1554,9 +1554,9 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
       const int g0 = (int)dceil(c - w.half);
       T v, dv;
       win_eval<T, PW == 0>(w, win_arg(((T)(g0 + k) - c), w), v, dv);
-      T* wj = wgt + (j * 4 + 2 * ax) * kMaxWin;
+      T* wj = wgt + (j * 4 + 2 * ax) * Pw;
       wj[k] = v;
-      wj[kMaxWin + k] = -dv * w.inv_half;  // d/dt of phi((g - t)/half)
+      wj[Pw + k] = -dv * w.inv_half;  // d/dt of phi((g - t)/half)
       if (r == 0) {
         const int gy0 = (int)dceil(a.y - w.half);
         bofs[j] = (gy0 + g.pad_lo) * RP + g0 + g.pad_lo;
@@ -1565,11 +1565,11 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
       // T_n(x) and T_n'(x) by the three-term recurrences
       const T x = rec[p0 + j].z;
-      T* tj = tnb + j * 2 * kMaxCheb;
+      T* tj = tnb + j * 2 * P;
       T t0 = T(1), t1 = x, d0 = T(0), d1 = T(1);
       for (int n = 0; n < P; ++n) {
         tj[n] = t0;
-        tj[kMaxCheb + n] = d0;
+        tj[P + n] = d0;
         const T t2 = T(2) * x * t1 - t0, d2 = T(2) * t1 + T(2) * x * d1 - d0;
         t0 = t1;
         t1 = t2;
@@ -1579,13 +1579,13 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
     }
     __syncthreads();
     for (int j = warp; j < nb; j += nw) {
-      const T* wj = wgt + j * 4 * kMaxWin;
-      const T* tj = tnb + j * 2 * kMaxCheb;
+      const T* wj = wgt + j * 4 * Pw;
+      const T* tj = tnb + j * 2 * P;
       T rwx[PR], rdwx[PR];
 #pragma unroll
       for (int dx = 0; dx < PR; ++dx) {
         rwx[dx] = dx < Pw ? wj[dx] : T(0);
-        rdwx[dx] = dx < Pw ? wj[kMaxWin + dx] : T(0);
+        rdwx[dx] = dx < Pw ? wj[Pw + dx] : T(0);
       }
       const T* bj = st + bofs[j];
       T f = 0, fx = 0, fy = 0, fz = 0;
@@ -1603,8 +1603,8 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
               sd += u * rdwx[dx];
             }
           }
-          const T wy = wj[2 * kMaxWin + dy], dwy = wj[3 * kMaxWin + dy];
-          const T tn = tj[n], dtn = tj[kMaxCheb + n];
+          const T wy = wj[2 * Pw + dy], dwy = wj[3 * Pw + dy];
+          const T tn = tj[n], dtn = tj[P + n];
           const T tw = tn * wy;
           f += tw * sx;
           fx += tw * sd;
@@ -2149,12 +2149,14 @@ size_t long_smem(const sog_plan* p, size_t es, bool gather) {
   const int P = p->prm.P_cheb;
   const int rp = gather_row_pitch(g.W[0]);
   const size_t tile = (size_t)P * gather_plane_stride(rp, g.W[1], p->wl.P);
+  const size_t pw = (size_t)p->wl.P;
   // gathering: staged window values and derivatives, T_n and T_n', the tile
-  if (gather)
-    return kLongSpreadHeader + ((size_t)kTileBatch * (4 * kMaxWin + 2 * kMaxCheb) + tile) * es;
+  // (sized by the plan's support and P_cheb: the smaller footprint lets
+  // three CTAs share an SM)
+  if (gather) return kLongSpreadHeader + ((size_t)kTileBatch * (4 * pw + 2 * P) + tile) * es;
   // gridding: staged window values and T_n, then the fixed-point tile (int32
   // for FP32, int64 for FP64: the size of T)
-  return kLongSpreadHeader + ((size_t)kTileBatch * (2 * kMaxWin + kMaxCheb) + tile) * es;
+  return kLongSpreadHeader + ((size_t)kTileBatch * (2 * pw + P) + tile) * es;
 }
 
 #define SOG_CK(x)                      \
