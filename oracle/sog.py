@@ -133,10 +133,31 @@ class Window:
     kind: str
     P: int
     shape: float
+    nu: int = 0     # > 0: evaluated through polynomials of degree nu (Sec. 3.4, 5.1)
 
     @property
     def half(self) -> float:        # half-width in grid units
         return 0.5 * (self.P - 1)
+
+    def poly_coefficients(self):
+        """Polynomial approximation of the window by Chebyshev interpolation
+        (Sec. 3.4, 5.1; the paper gives the order nu, not the construction).
+        READING: a particle at grid coordinate t touches the points
+        g0 + d, d = 0..P-1, g0 = ceil(t - half), at offsets s - half + d with
+        s = g0 - t + half in [0, 1); the weight of point d, as a function of
+        s, is interpolated at the nu + 1 Chebyshev points of the first kind
+        in sigma = 2 s - 1.  Returns the Chebyshev coefficients, shape
+        (P, nu + 1), from the discrete orthogonality of T_j at those points."""
+        n = self.nu + 1
+        theta = (np.arange(n) + 0.5) * PI / n
+        sigma = np.cos(theta)
+        d = np.arange(self.P, dtype=np.float64)
+        v = (0.5 * (sigma[None, :] + 1.0) - self.half + d[:, None]) / self.half
+        vals = self.phi(v)                                   # (P, nu + 1)
+        Tm = np.cos(np.arange(n)[:, None] * theta[None, :])  # T_j(sigma_i)
+        c = (2.0 / n) * vals @ Tm.T
+        c[:, 0] *= 0.5
+        return c
 
     def phi(self, v):
         v = np.asarray(v, dtype=np.float64)
@@ -207,16 +228,25 @@ class Window:
 
     def weights(self, t):
         """Grid indices g = ceil(t - half) + d, d = 0..P-1, of a particle at
-        grid coordinate t, with weights phi((g - t)/half) and d/dt of them."""
+        grid coordinate t, with weights phi((g - t)/half) and d/dt of them
+        (nu > 0: the interpolating polynomials of poly_coefficients and their
+        derivatives, d sigma / dt = -2)."""
         t = np.asarray(t, dtype=np.float64)
         g0 = np.ceil(t - self.half)
         g = g0[:, None] + np.arange(self.P)[None, :]
+        if self.nu > 0:
+            c = self.poly_coefficients()                       # (P, nu + 1)
+            dc = np.polynomial.chebyshev.chebder(c, axis=1)    # (P, nu)
+            sigma = 2.0 * (g0 - t + self.half) - 1.0
+            val = np.polynomial.chebyshev.chebval(sigma, c.T).T          # (n, P)
+            der = np.polynomial.chebyshev.chebval(sigma, dc.T).T
+            return g.astype(np.int64), val, -2.0 * der
         v = (g - t[:, None]) / self.half
         # d/dt phi((g - t)/half) = -phi'(v)/half
         return g.astype(np.int64), self.phi(v), -self.dphi(v) / self.half
 
 
-def make_window(kind: str, P: int, shape: float | None = None) -> Window:
+def make_window(kind: str, P: int, shape: float | None = None, nu: int = 0) -> Window:
     """Default shape parameters: beta = 1.9 P for ES, 2.0 P for KB, S =
     0.35 pi P for the Gaussian.  READING: Sec. 5.1 uses beta = 2.5 P (ES, KB)
     and S = 0.455 pi P on oversampled grids; on the grids of Sec. 4.3, which
@@ -224,7 +254,7 @@ def make_window(kind: str, P: int, shape: float | None = None) -> Window:
     P (checked against the direct Fourier sum in the tests)."""
     if shape is None:
         shape = {"es": 1.9 * P, "kb": 2.0 * P}.get(kind, 0.35 * PI * P)
-    return Window(kind, int(P), float(shape))
+    return Window(kind, int(P), float(shape), int(nu))
 
 
 # ---------------------------------------------------------------------------
@@ -526,7 +556,7 @@ def mid_spread(prm, q, r):
     x and y, and periodic with the period Lz* of the padded box in z.  Grid
     point g sits at (-Lx/2 + g_x hx, -Ly/2 + g_y hy, -Lz*/2 + g_z hz)."""
     Lx, Ly, Lz, Ix, Iy, Izs, hx, hy, hz, Lzs = _mid_geometry(prm)
-    win = make_window(prm["window"], prm["P_win"], prm["shape"])
+    win = make_window(prm["window"], prm["P_win"], prm["shape"], prm.get("win_poly", 0))
     gx, wx, _ = win.weights((r[:, 0] + Lx / 2) / hx)
     gy, wy, _ = win.weights((r[:, 1] + Ly / 2) / hy)
     gz, wz, _ = win.weights((r[:, 2] + Lzs / 2) / hz)
@@ -550,7 +580,7 @@ def mid_scaling(prm):
     / hatW(k)^2, k_d = 2 pi n_d / L_d (Lz* in z), n_d in [-I_d/2, I_d/2).
     READING: the k = 0 mode is set to zero (charge neutrality, Eq. 2.4)."""
     Lx, Ly, Lz, Ix, Iy, Izs, hx, hy, hz, Lzs = _mid_geometry(prm)
-    win = make_window(prm["window"], prm["P_win"], prm["shape"])
+    win = make_window(prm["window"], prm["P_win"], prm["shape"], prm.get("win_poly", 0))
     kx = 2 * PI * np.fft.fftfreq(Ix, d=hx)
     ky = 2 * PI * np.fft.fftfreq(Iy, d=hy)
     kz = 2 * PI * np.fft.fftfreq(Izs, d=hz)
@@ -577,7 +607,7 @@ def mid_range(prm, q, r, tgt=None):
     Lx, Ly, Lz, Ix, Iy, Izs, hx, hy, hz, Lzs = _mid_geometry(prm)
     G = mid_spread(prm, q, r)
     u = np.fft.ifftn(np.fft.fftn(G) * mid_scaling(prm)).real * (Ix * Iy * Izs)
-    win = make_window(prm["window"], prm["P_win"], prm["shape"])
+    win = make_window(prm["window"], prm["P_win"], prm["shape"], prm.get("win_poly", 0))
     gx, wx, dwx = win.weights((tr[:, 0] + Lx / 2) / hx)
     gy, wy, dwy = win.weights((tr[:, 1] + Ly / 2) / hy)
     gz, wz, dwz = win.weights((tr[:, 2] + Lzs / 2) / hz)
@@ -632,7 +662,7 @@ def long_range(prm, q, r, tgt=None):
     hx, hy = Lx / Ilx, Ly / Ily
     P = prm["P_cheb"]
     zc = cheb_nodes(P, Lz)
-    win = make_window(prm["window"], prm["P_long"], prm["shape_long"])
+    win = make_window(prm["window"], prm["P_long"], prm["shape_long"], prm.get("win_poly", 0))
     # gridding with anterpolation weights q_j L_c(z_j)
     Ls, _ = lagrange(zc, r[:, 2], deriv=False)
     gx, wx, _ = win.weights((r[:, 0] + Lx / 2) / hx)
@@ -748,7 +778,7 @@ def long_range_taylor(prm, q, r, Q, tgt=None):
     hx, hy = Lx / Ilx, Ly / Ily
     P = prm["P_cheb"]
     zc = cheb_nodes(P, Lz)
-    win = make_window(prm["window"], prm["P_long"], prm["shape_long"])
+    win = make_window(prm["window"], prm["P_long"], prm["shape_long"], prm.get("win_poly", 0))
     gx, wx, _ = win.weights((r[:, 0] + Lx / 2) / hx)
     gy, wy, _ = win.weights((r[:, 1] + Ly / 2) / hy)
     gx %= Ilx

@@ -27,7 +27,8 @@ class SogParams(ctypes.Structure):
                 ("hz", ctypes.c_double), ("P_win", ctypes.c_int32), ("shape", ctypes.c_double),
                 ("I_long", ctypes.c_int32 * 2), ("P_long", ctypes.c_int32),
                 ("shape_long", ctypes.c_double), ("P_cheb", ctypes.c_int32),
-                ("window", ctypes.c_int32), ("long_direct", ctypes.c_int32)]
+                ("window", ctypes.c_int32), ("long_direct", ctypes.c_int32),
+                ("win_poly", ctypes.c_int32)]
 
     def to_dict(self):
         return dict(L=tuple(self.L), b=self.b, r0=self.r0, omega=self.omega, sigma=self.sigma,
@@ -35,7 +36,7 @@ class SogParams(ctypes.Structure):
                     P_win=self.P_win, shape=self.shape, I_long=tuple(self.I_long),
                     P_long=self.P_long, shape_long=self.shape_long, P_cheb=self.P_cheb,
                     window=_WIN_NAMES[self.window],
-                    long_direct=bool(self.long_direct))
+                    long_direct=bool(self.long_direct), win_poly=int(self.win_poly))
 
     @classmethod
     def from_dict(cls, d):
@@ -49,12 +50,14 @@ class SogParams(ctypes.Structure):
         p.I_long[:] = list(d["I_long"])
         p.window = {v: k for k, v in _WIN_NAMES.items()}[d.get("window", "es")]
         p.long_direct = 1 if d.get("long_direct", False) else 0
+        p.win_poly = int(d.get("win_poly", 0))
         return p
 
 
 class SogOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("window", ctypes.c_int32),
-                ("n_nb", ctypes.c_double), ("manual", ctypes.POINTER(SogParams))]
+                ("n_nb", ctypes.c_double), ("manual", ctypes.POINTER(SogParams)),
+                ("win_poly", ctypes.c_int32)]
 
 
 _lib = None
@@ -152,11 +155,12 @@ def _check(code, where):
         raise SogError(code, where)
 
 
-def _opts(precision, window, n_nb, manual):
+def _opts(precision, window, n_nb, manual, win_poly=0):
     o = SogOpts()
     o.precision = precision
     o.window = window
     o.n_nb = float(n_nb) if n_nb else 0.0
+    o.win_poly = int(win_poly)
     if manual is not None:
         mp = manual if isinstance(manual, SogParams) else SogParams.from_dict(manual)
         o._manual_ref = mp
@@ -164,9 +168,9 @@ def _opts(precision, window, n_nb, manual):
     return o
 
 
-def sog_select_params(N, Lx, Ly, Lz, tol, window=SOG_WIN_ES, n_nb=None) -> dict:
+def sog_select_params(N, Lx, Ly, Lz, tol, window=SOG_WIN_ES, n_nb=None, win_poly=0) -> dict:
     out = SogParams()
-    o = _opts(SOG_PREC_MIXED, window, n_nb, None)
+    o = _opts(SOG_PREC_MIXED, window, n_nb, None, win_poly)
     _check(load().sog_select_params(int(N), Lx, Ly, Lz, tol, ctypes.byref(o), ctypes.byref(out)),
            "sog_select_params")
     return out.to_dict()
@@ -247,11 +251,11 @@ class Plan:
     CUDA tensors of the plan's dtype (float64 for FP64, float32 for mixed)."""
 
     def __init__(self, N, L, tol, precision=SOG_PREC_MIXED, window=SOG_WIN_ES, n_nb=None,
-                 manual=None):
+                 manual=None, win_poly=0):
         L_ = tuple(map(float, L))
         self.N = int(N)
         self._lib = load()
-        self._opts = _opts(precision, window, n_nb, manual)
+        self._opts = _opts(precision, window, n_nb, manual, win_poly)
         h = ctypes.c_void_p()
         _check(self._lib.sog_plan_create(ctypes.byref(h), self.N, L_[0], L_[1], L_[2], float(tol),
                                          ctypes.byref(self._opts)), "sog_plan_create")

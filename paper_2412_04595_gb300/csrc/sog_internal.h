@@ -5,9 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <vector>
-
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "../../include/sog.h"
 
@@ -76,7 +76,52 @@ struct WinPar {
   int kind;          // SOG_WIN_ES, SOG_WIN_GAUSS or SOG_WIN_KB
   double half;
   double shape;
+  int nu = 0;        // > 0: evaluated through per-point polynomials of degree nu
 };
+
+// Largest degree of the polynomial windows.
+constexpr int kPolyMax = 12;
+
+// Window phi(v) in FP64 on the host (zero outside |v| <= 1).
+inline double win_phi_host(const WinPar& w, double v) {
+  if (!(v >= -1.0 && v <= 1.0)) return 0.0;
+  const double a = std::sqrt(std::max(0.0, (1.0 - v) * (1.0 + v)));
+  if (w.kind == SOG_WIN_ES) return std::exp(w.shape * (a - 1.0));
+  if (w.kind == SOG_WIN_KB) return std::cyl_bessel_i(0.0, w.shape * a) / std::cyl_bessel_i(0.0, w.shape);
+  return std::exp(-w.shape * v * v);
+}
+
+// Polynomial windows (Sec. 3.4, 5.1: Chebyshev interpolation of order nu).
+// A particle at grid coordinate t touches g0 + d, d = 0..P-1, g0 =
+// ceil(t - half); as a function of sigma = 2 (g0 - t + half) - 1 in [-1, 1)
+// the weight of point d is phi((s - half + d) / half), s = (sigma + 1) / 2.
+// Its interpolant at the nu + 1 Chebyshev points of the first kind is
+// written in monomials of sigma: a[d * (kPolyMax + 1) + j], j = 0..nu
+// (coefficients from the discrete orthogonality of T_j at those points,
+// then T_j expanded by T_{j+1} = 2 sigma T_j - T_{j-1}; all in FP64).
+inline void win_poly_coeffs(const WinPar& w, double* a) {
+  const int n = w.nu + 1;
+  const double pi = 3.14159265358979323846;
+  double T[kPolyMax + 1][kPolyMax + 1] = {};  // monomial coefficients of T_j
+  T[0][0] = 1.0;
+  if (w.nu >= 1) T[1][1] = 1.0;
+  for (int j = 1; j + 1 <= w.nu; ++j)
+    for (int i = 0; i <= j + 1; ++i)
+      T[j + 1][i] = (i > 0 ? 2.0 * T[j][i - 1] : 0.0) - T[j - 1][i];
+  for (int d = 0; d < w.P; ++d) {
+    double c[kPolyMax + 1] = {};
+    for (int i = 0; i < n; ++i) {
+      const double th = (i + 0.5) * pi / n, sg = std::cos(th);
+      const double f = win_phi_host(w, (0.5 * (sg + 1.0) - w.half + d) / w.half);
+      for (int j = 0; j < n; ++j) c[j] += f * std::cos(j * th);
+    }
+    for (int j = 0; j < n; ++j) c[j] *= (j == 0 ? 1.0 : 2.0) / n;
+    double* ad = a + d * (kPolyMax + 1);
+    for (int i = 0; i <= kPolyMax; ++i) ad[i] = 0.0;
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i <= j; ++i) ad[i] += c[j] * T[j][i];
+  }
+}
 
 // Tiling of a periodic grid for spreading / gathering.
 struct TileGeom {

@@ -95,6 +95,8 @@ struct WinT {
   T half, inv_half, shape;
   int kbn;           // KB: number of series terms
   T kbc[kKbTerms];   // KB: series coefficients for the rounded shape
+  int nu;            // > 0: polynomial windows of this degree
+  T pc[kMaxWin * (kPolyMax + 1)];  // their monomial coefficients [d][j] (win_poly_coeffs)
 };
 
 template <typename T>
@@ -108,6 +110,10 @@ __host__ WinT<T> wint(const WinPar& w) {
   o.kbn = 0;
   for (int k = 0; k < kKbTerms; ++k) o.kbc[k] = T(0);
   if (w.kind == SOG_WIN_KB) o.kbn = kb_series<T>((double)o.shape, o.kbc, kKbTerms);
+  o.nu = w.nu;
+  double a[kMaxWin * (kPolyMax + 1)] = {};
+  if (w.nu > 0) win_poly_coeffs(w, a);
+  for (int i = 0; i < kMaxWin * (kPolyMax + 1); ++i) o.pc[i] = (T)a[i];
   return o;
 }
 
@@ -189,6 +195,43 @@ __device__ __forceinline__ T win_val(const WinT<T>& w, T v) {
     return p;
   }
   return dexp(-w.shape * v * v);
+}
+
+// Window weight of support point k of a particle at grid coordinate c
+// (g0 = ceil(c - half)) and d phi / dv: directly at v = (g0 + k - c) / half,
+// or, for polynomial windows, by Horner in sigma = 2 (g0 - c) + P - 2 (the
+// same number as 2 (g0 - c + half) - 1, exact in both types) on point k's
+// coefficients; d phi / dv = 2 half d p / d sigma.
+template <typename T>
+__device__ __forceinline__ T win_sigma(int g0, T c, const WinT<T>& w) {
+  return T(2) * ((T)g0 - c) + (T)(w.P - 2);
+}
+template <typename T, bool KB>
+__device__ __forceinline__ void win_eval_pt(const WinT<T>& w, int g0, T c, int k, T& val, T& dval) {
+  if (w.nu > 0) {
+    const T sg = win_sigma(g0, c, w);
+    const T* a = w.pc + k * (kPolyMax + 1);
+    T p = a[w.nu], dp = T(0);
+    for (int j = w.nu - 1; j >= 0; --j) {
+      dp = dp * sg + p;
+      p = p * sg + a[j];
+    }
+    val = p;
+    dval = (T)(w.P - 1) * dp;
+    return;
+  }
+  win_eval<T, KB>(w, win_arg(((T)(g0 + k) - c), w), val, dval);
+}
+template <typename T, bool KB>
+__device__ __forceinline__ T win_val_pt(const WinT<T>& w, int g0, T c, int k) {
+  if (w.nu > 0) {
+    const T sg = win_sigma(g0, c, w);
+    const T* a = w.pc + k * (kPolyMax + 1);
+    T p = a[w.nu];
+    for (int j = w.nu - 1; j >= 0; --j) p = p * sg + a[j];
+    return p;
+  }
+  return win_val<T, KB>(w, win_arg(((T)(g0 + k) - c), w));
 }
 
 // ---------------------------------------------------------------------------
@@ -1025,7 +1068,7 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_spread(TileGeom g, WinT<T>
       const P4<T> a = rec[p0 + j];
       const T c = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
       const int g0 = (int)dceil(c - w.half);
-      const T v = win_val<T, PW == 0>(w, win_arg(((T)(g0 + k) - c), w));
+      const T v = win_val_pt<T, PW == 0>(w, g0, c, k);
       wgt[(j * 3 + ax) * kMaxWin + k] = ax == 0 ? v * a.q : v;
       if (r == 0) {
         const int gy0 = (int)dceil(a.y - w.half), gz0 = (int)dceil(a.z - w.half);
@@ -1197,13 +1240,13 @@ __global__ void __launch_bounds__(kTileThreads) k_mid_gather(TileGeom g, WinT<T>
       if (ax0 < 3) {
         const T c = ax0 == 0 ? a.x : (ax0 == 1 ? a.y : a.z);
         const int g0 = ax0 == 0 ? gx0 : (ax0 == 1 ? gy0 : gz0);
-        win_eval<T, PW == 0>(w, win_arg(((T)(g0 + k0) - c), w), v, dv);
+        win_eval_pt<T, PW == 0>(w, g0, c, k0, v, dv);
         wsm[ax0 * kMaxWin + k0] = Cx<T>{v, -dv * w.inv_half};
       }
       if (3 * P > 32 && ax1 < 3) {
         const T c = ax1 == 0 ? a.x : (ax1 == 1 ? a.y : a.z);
         const int g0 = ax1 == 0 ? gx0 : (ax1 == 1 ? gy0 : gz0);
-        win_eval<T, PW == 0>(w, win_arg(((T)(g0 + k1) - c), w), v, dv);
+        win_eval_pt<T, PW == 0>(w, g0, c, k1, v, dv);
         wsm[ax1 * kMaxWin + k1] = Cx<T>{v, -dv * w.inv_half};
       }
     }
@@ -1322,7 +1365,7 @@ __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T
       const P4<T> a = rec[p0 + j];
       const T c = ax == 0 ? a.x : a.y;
       const int g0 = (int)dceil(c - w.half);
-      const T v = win_val<T, PW == 0>(w, win_arg(((T)(g0 + k) - c), w));
+      const T v = win_val_pt<T, PW == 0>(w, g0, c, k);
       wgt[(j * 2 + ax) * Pw + k] = ax == 0 ? v * a.q : v;
       if (r == 0) {
         const int gy0 = (int)dceil(a.y - w.half);
@@ -1434,11 +1477,21 @@ __global__ void __launch_bounds__(256) k_long_spread_small(int I0, int I1, WinT<
         const int Id = ax ? I1 : I0;
         if (k < Id) {
           const P4<T> a = rec[p0 + j];
-          // nearest image of grid index k relative to the particle
-          T d = (T)k - (ax ? a.y : a.x);
-          d -= (T)Id * drint(d * (ax ? iI1 : iI0));
           T v, dv;
-          win_eval<T, true>(w, win_arg(d, w), v, dv);
+          if (w.nu > 0) {
+            // support point of grid index k, if any (the grid holds P + 4
+            // points at least, so one per index)
+            const T c = ax ? a.y : a.x;
+            const int g0 = (int)dceil(c - w.half);
+            const int kk = ((k - g0) % Id + Id) % Id;
+            v = T(0);
+            if (kk < w.P) win_eval_pt<T, true>(w, g0, c, kk, v, dv);
+          } else {
+            // nearest image of grid index k relative to the particle
+            T d = (T)k - (ax ? a.y : a.x);
+            d -= (T)Id * drint(d * (ax ? iI1 : iI0));
+            win_eval<T, true>(w, win_arg(d, w), v, dv);
+          }
           if (ax) wy[j][k] = v;
           else wx[j][k] = v * a.q;
         }
@@ -1553,7 +1606,7 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
       const T c = ax == 0 ? a.x : a.y;
       const int g0 = (int)dceil(c - w.half);
       T v, dv;
-      win_eval<T, PW == 0>(w, win_arg(((T)(g0 + k) - c), w), v, dv);
+      win_eval_pt<T, PW == 0>(w, g0, c, k, v, dv);
       T* wj = wgt + (j * 4 + 2 * ax) * Pw;
       wj[k] = v;
       wj[Pw + k] = -dv * w.inv_half;  // d/dt of phi((g - t)/half)

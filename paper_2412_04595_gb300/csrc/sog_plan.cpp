@@ -237,6 +237,7 @@ sog_status select_params(int64_t N, double Lx, double Ly, double Lz, double tol,
   out->P_cheb = bPc;
   out->window = window;
   out->long_direct = bdirect;
+  out->win_poly = 0;
   return SOG_OK;
 }
 
@@ -255,6 +256,7 @@ sog_status check_params(const sog_params& p) {
   if (p.M < 0 || p.M > 4000 || p.m < -1 || p.m > p.M) return SOG_ERR_PARAMS;
   if (p.window != SOG_WIN_ES && p.window != SOG_WIN_GAUSS && p.window != SOG_WIN_KB)
     return SOG_ERR_PARAMS;
+  if (p.win_poly != 0 && (p.win_poly < 2 || p.win_poly > sogk::kPolyMax)) return SOG_ERR_PARAMS;
   if (p.m >= 0) {
     for (int d = 0; d < 3; ++d)
       if (!smooth_even(p.I[d])) return SOG_ERR_PARAMS;
@@ -577,7 +579,11 @@ sog_status sog_select_params(int64_t N, double Lx, double Ly, double Lz, double 
   const int window = opts ? opts->window : SOG_WIN_ES;
   if (window != SOG_WIN_ES && window != SOG_WIN_GAUSS && window != SOG_WIN_KB) return SOG_ERR_ARG;
   const double nnb = (opts && opts->n_nb > 0.0) ? opts->n_nb : 120.0;
-  return select_params(N, Lx, Ly, Lz, tol, window, nnb, out);
+  const int nu = opts ? opts->win_poly : 0;
+  if (nu != 0 && (nu < 2 || nu > sogk::kPolyMax)) return SOG_ERR_ARG;
+  st = select_params(N, Lx, Ly, Lz, tol, window, nnb, out);
+  if (st == SOG_OK) out->win_poly = nu;
+  return st;
 }
 
 sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, double Lz, double tol,
@@ -641,7 +647,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     p->h[1] = L[1] / Iy;
     p->h[2] = prm.hz;
     p->Lzs = Iz * prm.hz;
-    p->wm = sogk::WinPar{prm.P_win, prm.window, 0.5 * (prm.P_win - 1), prm.shape};
+    p->wm = sogk::WinPar{prm.P_win, prm.window, 0.5 * (prm.P_win - 1), prm.shape, prm.win_poly};
     int T = 16;
     if (prec == SOG_PREC_FP64 || (size_t)(16 + prm.P_win) * (16 + prm.P_win) * (16 + prm.P_win) * es > 72 * 1024)
       T = 8;
@@ -655,7 +661,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   if (p->has_long && !p->long_direct) {
     p->hl[0] = L[0] / Ilx;
     p->hl[1] = L[1] / Ily;
-    p->wl = sogk::WinPar{prm.P_long, prm.window, 0.5 * (prm.P_long - 1), prm.shape_long};
+    p->wl = sogk::WinPar{prm.P_long, prm.window, 0.5 * (prm.P_long - 1), prm.shape_long, prm.win_poly};
     int T = 16;
     if ((size_t)P * ((16 + prm.P_long) * (16 + prm.P_long) + 1) * es > 96 * 1024) T = 8;
     set_long_tiles(p, T, 1.0);

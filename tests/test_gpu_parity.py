@@ -120,10 +120,11 @@ def test_mixed_matches_oracle_on_rounded_inputs(B, oracle_mod):
 
 
 def test_full_size_bench_workload(B, oracle_mod):
-    """The benchmark workload itself (N = 1e5 neutral +-1 charges in a
-    100^3 box, tol 1e-6, mixed precision, the launch configuration bench.py
-    times): energy and RMS force against the FP64 oracle on the same rounded
-    inputs and parameters, and phi element-wise on 2000 sampled particles."""
+    """The 1e5 cube workload (N = 1e5 neutral +-1 charges in a 100^3 box,
+    tol 1e-6, mixed precision, the launch configuration of
+    `bench.py --workload c2`): energy and RMS force against the FP64 oracle
+    on the same rounded inputs and parameters, and phi element-wise on 2000
+    sampled particles."""
     N, L, tol = 100000, (100.0, 100.0, 100.0), 1e-6
     from paper_2412_04595_gb300 import workloads
     q32, r32 = workloads.uniform_neutral(N, L, 1, dtype=np.float32)
@@ -333,3 +334,36 @@ def test_forces_are_the_gradient_of_the_energy(B, oracle_mod):
             Em = run_gpu(B, prm, q, rm, B.SOG_PREC_FP64)["E"]
             fd = -(Ep - Em) / (2 * h)
             assert abs(fd - base["F"][i, d]) < 1e-6 * Fmax, (i, d, fd, base["F"][i, d])
+
+
+@pytest.mark.parametrize("name", ["cube10", "slab"])
+@pytest.mark.parametrize("window", ["es", "kb"])
+def test_polynomial_windows_match_oracle(B, oracle_mod, name, window):
+    """Polynomial windows (win_poly = nu, Sec. 3.4, 5.1) on the mid grid, the
+    small one-tile long-range grid (cube10, Algorithm 2 variant) and the tiled
+    long-range grid (slab): FP64 parts against the oracle's evaluation of the
+    same polynomials to rounding; mixed precision within the FP32 tolerance;
+    and the energy within 1e-7 of the exact windows'."""
+    N, L, tol, nnb = CASES[name]
+    q, r = uniform_system(N, L, 21)
+    prm = oracle_mod.select_params(N, *L, tol, n_nb=nnb, window=window)
+    if name == "cube10":
+        prm = long_variants(oracle_mod, prm, tol)["grid"]
+    prm = dict(prm, win_poly=10)
+    ref = oracle_mod.sog_eval(prm, q, r)
+    out = run_gpu(B, prm, q, r, B.SOG_PREC_FP64, parts=True)
+    assert out["status"] == 0
+    for k, key in enumerate(("mid", "long")):
+        rp, rg = ref["parts"][key]
+        if np.max(np.abs(rp)) == 0.0:
+            continue
+        assert rel_max(out["pp"][k + 1], rp) < 1e-11, (window, key, rel_max(out["pp"][k + 1], rp))
+        assert rel_max(out["pg"][k + 1], rg) < 1e-10, (window, key, rel_max(out["pg"][k + 1], rg))
+    assert abs(out["E"] - ref["E"]) <= 1e-11 * abs(ref["E"])
+    exact = oracle_mod.sog_eval(dict(prm, win_poly=0), q, r)
+    assert abs(ref["E"] - exact["E"]) <= 1e-7 * abs(exact["E"])
+    q32, r32 = q.astype(np.float32), r.astype(np.float32)
+    outm = run_gpu(B, prm, q32, r32, B.SOG_PREC_MIXED)
+    assert outm["status"] == 0
+    relE, rmsF, linf = compare(outm, ref, q)
+    assert relE < 1e-5 and rmsF < 1e-4 and linf < 1e-4, (window, relE, rmsF, linf)
