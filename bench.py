@@ -64,7 +64,7 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "c3_slab"
 FLUSH_BYTES = 512 << 20          # larger than the 129 MB L2, written between steps
 N_ORACLE_TARGETS = 2000          # sampled targets compared with the FP64 oracle
-N_TRUTH_TARGETS = 16             # targets compared with Ewald2D
+N_TRUTH_TARGETS = 100            # targets compared with Ewald2D
 CPU_SAMPLE_SECONDS = 15.0        # oracle work of the CPU baseline's bounded sample
 # FP32 operations the near field must do (the per-unit counts of the method,
 # not of this implementation): 8 per candidate of the 27-cell neighbourhood
@@ -151,22 +151,67 @@ def make_system(wl, N=None, seed=None):
     return q, r, L
 
 
-def stage_work(prm, N, stage, es):
+def near_counts(prm, r, samples=20000, seed=0):
+    """Candidate tests and pairs of the near field on the actual positions:
+    candidates = sum over cells of (charges in the cell) x (charges in its
+    neighbour cells), the cells being the r_c-wide cells of the cell list
+    (Sec. 2.2); pairs = N x the mean number of neighbours within r_c of
+    `samples` random charges (k-d tree, minimum image in x, y).  None when
+    scipy is missing (the uniform-density estimate is used instead)."""
+    import numpy as np
+    try:
+        from scipy.spatial import cKDTree
+    except ImportError:
+        return None
+    L, rc = prm["L"], prm["rc"]
+    N = r.shape[0]
+    pts = r.astype(np.float64) + np.array([0.5 * L[0], 0.5 * L[1], 0.5 * L[2]])
+    pts[:, 0] %= L[0]
+    pts[:, 1] %= L[1]
+    pts[:, 2] = np.clip(pts[:, 2], 0.0, L[2])
+    nc = [max(1, int(math.floor(L[d] / rc))) for d in range(3)]
+    ci = [np.minimum((pts[:, d] * (nc[d] / L[d])).astype(np.int64), nc[d] - 1) for d in range(3)]
+    H = np.zeros((nc[2], nc[1], nc[0]))
+    np.add.at(H, (ci[2], ci[1], ci[0]), 1.0)
+    Hn = np.zeros_like(H)
+    for dz in ((-1, 0, 1) if nc[2] > 1 else (0,)):
+        for dy in ((-1, 0, 1) if nc[1] >= 3 else (0,)):
+            for dx in ((-1, 0, 1) if nc[0] >= 3 else (0,)):
+                sh = np.roll(np.roll(H, dy, axis=1), dx, axis=2)
+                if dz == 1:
+                    sh = np.concatenate([np.zeros_like(sh[:1]), sh[:-1]], 0)
+                elif dz == -1:
+                    sh = np.concatenate([sh[1:], np.zeros_like(sh[:1])], 0)
+                Hn += sh
+    cand = float((H * Hn).sum())
+    tree = cKDTree(pts, boxsize=[L[0], L[1], L[2] + 2.0 * rc + 1.0])
+    idx = np.random.default_rng(seed).choice(N, min(N, samples), replace=False)
+    nb = tree.query_ball_point(pts[idx], rc, return_length=True) - 1
+    return {"cand": cand, "pairs": float(nb.mean()) * N, "sampled": int(idx.size)}
+
+
+def stage_work(prm, N, stage, es, counts=None):
     """Algorithmic work of one launch of a stage and the resource bounding it:
     ("alu", FP32 operations), ("hbm", bytes) or (None, None), with its
-    description.  es: bytes per element of the plan's type."""
+    description.  es: bytes per element of the plan's type.  counts: the
+    near field's candidates and pairs on the actual positions (near_counts);
+    None: the uniform-density estimate."""
     Ix, Iy, Iz = prm["I"]
     P, Pc, Pl = prm["P_win"], prm["P_cheb"], prm["P_long"]
     L = prm["L"]
     rho = N / (L[0] * L[1] * L[2])
     if stage == "near":
-        pairs = N * 4.0 / 3.0 * math.pi * prm["rc"] ** 3 * rho
-        nc = [max(1, int(math.floor(L[d] / prm["rc"]))) for d in range(3)]
-        ext = [min(3, nc[d]) for d in range(3)]
-        cand = N * ext[0] * ext[1] * ext[2] * N / (nc[0] * nc[1] * nc[2])
+        if counts is not None:
+            cand, pairs, how = counts["cand"], counts["pairs"], "counted on the positions"
+        else:
+            pairs = N * 4.0 / 3.0 * math.pi * prm["rc"] ** 3 * rho
+            nc = [max(1, int(math.floor(L[d] / prm["rc"]))) for d in range(3)]
+            ext = [min(3, nc[d]) for d in range(3)]
+            cand = N * ext[0] * ext[1] * ext[2] * N / (nc[0] * nc[1] * nc[2])
+            how = "uniform-density estimate"
         return ("alu", cand * CAND_FLOP + pairs * PAIR_FLOP,
-                "FP32 flop: %.3g candidates x %d + %.3g pairs x %d"
-                % (cand, CAND_FLOP, pairs, PAIR_FLOP))
+                "FP32 flop: %.4g candidate tests (27-cell neighbourhoods) x %d + %.4g pairs "
+                "within r_c x %d (%s)" % (cand, CAND_FLOP, pairs, PAIR_FLOP, how))
     if stage == "binning":
         sets = 1 + (prm["m"] >= 0) + (prm["m"] < prm["M"] and not prm["long_direct"])
         return ("hbm", N * (4 * es + sets * 17 * es),
@@ -201,8 +246,8 @@ def stage_work(prm, N, stage, es):
     return None, None, None
 
 
-def roofline_entry(prm, N, stage, t_s, es, peaks):
-    bound, work, desc = stage_work(prm, N, stage, es)
+def roofline_entry(prm, N, stage, t_s, es, peaks, counts=None):
+    bound, work, desc = stage_work(prm, N, stage, es, counts)
     if bound == "alu":
         peak, src = peaks["fp32_tflops"] if es == 4 else peaks["fp64_tflops"], peaks["alu_src"]
         ach = work / t_s / 1e12
@@ -746,7 +791,8 @@ def main():
     prm = res["prm"]
     N = wl["N"]
     peaks = measured_peaks()
-    rooflines = [roofline_entry(prm, N, k, v * 1e-3, res["es"], peaks)
+    counts = near_counts(prm, res["r"]) if res.get("r") is not None else None
+    rooflines = [roofline_entry(prm, N, k, v * 1e-3, res["es"], peaks, counts)
                  for k, v in res["stage_ms"].items() if v > 0]
     rooflines = [x for x in rooflines if x is not None]
     # the dominant kernel: the stage with the longest isolated duration

@@ -349,7 +349,8 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
 
 // One in-place Stockham stage of radix R; L = product of earlier radices.
 template <typename T2, int CAP, int R, typename T4>
-__device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T4* tw, bool inv) {
+__device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T4* tw,
+                                      const T4* __restrict__ stw, bool inv) {
   constexpr int KB = CAP / R;
   const int nb = s.n / R, m = nb / L;
   const int tot = s.nl * nb;
@@ -376,7 +377,7 @@ __device__ __forceinline__ void stage(T2* buf, const LineSet s, int L, const T4*
 #pragma unroll
       for (int p = 0; p < R; ++p) x[k][p] = a[p * st];
 #pragma unroll
-      for (int p = 1; p < R; ++p) x[k][p] = cmul_tw(x[k][p], tw[j * p * m], inv);
+      for (int p = 1; p < R; ++p) x[k][p] = cmul_tw(x[k][p], stw[(p - 1) * L + j], inv);
       dft<T2, R>(x[k], inv, tw, s.n);
       wb[k] = line * s.ls + (kk * L * R + j) * s.es;
     }
@@ -405,17 +406,24 @@ template <typename T2, int CAP, typename T4>
 __device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T4* tw, bool inv) {
   const int n16 = f.n16, n15 = f.n15, n8 = f.n8, n4 = f.n4, n2 = f.n2, n3 = f.n3, n5 = f.n5,
             n7 = f.n7;
+  // the stage tables follow the length-n table: stage by stage, in this
+  // order, (R - 1) L entries [p - 1][j] = w_n^(j p n / (R L))
+  const T4* stw = tw + f.n;
   int L = 1;
   if constexpr (CAP >= 16)
-    for (int i = 0; i < n15; ++i, L *= 15) stage<T2, CAP, 15>(buf, s, L, tw, inv);
-  for (int i = 0; i < n3; ++i, L *= 3) stage<T2, CAP, 3>(buf, s, L, tw, inv);
-  for (int i = 0; i < n5; ++i, L *= 5) stage<T2, CAP, 5>(buf, s, L, tw, inv);
-  for (int i = 0; i < n7; ++i, L *= 7) stage<T2, CAP, 7>(buf, s, L, tw, inv);
+    for (int i = 0; i < n15; ++i, stw += 14 * L, L *= 15) stage<T2, CAP, 15>(buf, s, L, tw, stw, inv);
+  for (int i = 0; i < n3; ++i, stw += 2 * L, L *= 3) stage<T2, CAP, 3>(buf, s, L, tw, stw, inv);
+  for (int i = 0; i < n5; ++i, stw += 4 * L, L *= 5) stage<T2, CAP, 5>(buf, s, L, tw, stw, inv);
+  for (int i = 0; i < n7; ++i, stw += 6 * L, L *= 7) stage<T2, CAP, 7>(buf, s, L, tw, stw, inv);
   if constexpr (CAP >= 16)
-    for (int i = 0; i < n16; ++i, L *= 16) stage<T2, CAP, 16>(buf, s, L, tw, inv);
-  for (int i = 0; i < n8; ++i, L *= 8) stage<T2, CAP, 8>(buf, s, L, tw, inv);
-  if (n4) { stage<T2, CAP, 4>(buf, s, L, tw, inv); L *= 4; }
-  if (n2) { stage<T2, CAP, 2>(buf, s, L, tw, inv); L *= 2; }
+    for (int i = 0; i < n16; ++i, stw += 15 * L, L *= 16) stage<T2, CAP, 16>(buf, s, L, tw, stw, inv);
+  for (int i = 0; i < n8; ++i, stw += 7 * L, L *= 8) stage<T2, CAP, 8>(buf, s, L, tw, stw, inv);
+  if (n4) {
+    stage<T2, CAP, 4>(buf, s, L, tw, stw, inv);
+    stw += 3 * L;
+    L *= 4;
+  }
+  if (n2) stage<T2, CAP, 2>(buf, s, L, tw, stw, inv);
 }
 
 // Largest nl for which nl lines of length n fit the engine.
@@ -515,10 +523,10 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
   const int Ix = fx.n, Iy = fy.n, C = Ix / 2 + 1, pitch = Ix + 2;
   const int np = Iy / 2;
   T4* twx = reinterpret_cast<T4*>(smraw);
-  T4* twy = twx + Ix;
-  T2* buf = reinterpret_cast<T2*>(twy + Iy);
-  load_tw(twx, twg + fx.tw_off, Ix);
-  load_tw(twy, twg + fy.tw_off, Iy);
+  T4* twy = twx + kTwRegion * Ix;
+  T2* buf = reinterpret_cast<T2*>(twy + kTwRegion * Iy);
+  load_tw(twx, twg + fx.tw_off, kTwRegion * Ix);
+  load_tw(twy, twg + fy.tw_off, kTwRegion * Iy);
   T* pl = data + (size_t)blockIdx.x * Iy * pitch;
   T2* plc = reinterpret_cast<T2*>(pl);
   const LineSet xs{Ix, np, Ix, 1, false};
@@ -571,8 +579,8 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
   const int Ix = fx.n, C = Ix / 2 + 1, pitch = Ix + 2;
   using T4 = typename C2<T>::tw;
   T4* twx = reinterpret_cast<T4*>(smraw);
-  T2* buf = reinterpret_cast<T2*>(twx + Ix);
-  load_tw(twx, twg + fx.tw_off, Ix);
+  T2* buf = reinterpret_cast<T2*>(twx + kTwRegion * Ix);
+  load_tw(twx, twg + fx.tw_off, kTwRegion * Ix);
   const int p0 = blockIdx.x * B;
   const int nl = min(B, npairs - p0);
   T* base = data + (size_t)(2 * p0) * pitch;
@@ -647,8 +655,8 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
   const int n = f.n;
   using T4 = typename C2<T>::tw;
   T4* tw = reinterpret_cast<T4*>(smraw);
-  T2* buf = reinterpret_cast<T2*>(tw + n);
-  load_tw(tw, twg + f.tw_off, n);
+  T2* buf = reinterpret_cast<T2*>(tw + kTwRegion * n);
+  load_tw(tw, twg + f.tw_off, kTwRegion * n);
   const int gpo = (Cn + B - 1) / B;
   const int o = blockIdx.x / gpo;
   const int c0 = (blockIdx.x - o * gpo) * B;
@@ -833,7 +841,7 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
   const int np0 = (P + 1) / 2, np = par ? P / 2 : np0;
   const int tot = np * Iy;
   T4* tw = reinterpret_cast<T4*>(buf + (size_t)np0 * Iy);
-  T* sB = reinterpret_cast<T*>(tw + Iy);                   // [l][i][j], row stride pst
+  T* sB = reinterpret_cast<T*>(tw + kTwRegion * Iy);      // [l][i][j], row stride pst
   T2* sC = reinterpret_cast<T2*>(sB + (size_t)nl * ps * pst);
   T2* blk = data + (size_t)c * P * Iy + (size_t)(par ? np0 : 0) * Iy;
   if (threadIdx.x == 0) {
@@ -844,7 +852,7 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
       bulk_g2s(reinterpret_cast<char*>(buf) + o, reinterpret_cast<const char*>(blk) + o,
                bytes - o < 32768u ? bytes - o : 32768u, &bar);
   }
-  for (int i = threadIdx.x; i < Iy; i += blockDim.x) tw[i] = twg[fy.tw_off + i];
+  for (int i = threadIdx.x; i < kTwRegion * Iy; i += blockDim.x) tw[i] = twg[fy.tw_off + i];
   const int bsz = ps * pst;
   for (int i = threadIdx.x; i < nl * bsz; i += blockDim.x) {
     const int l = i / bsz;
@@ -929,7 +937,7 @@ template <typename T>
 static bool plane_fits(const FftLen& fx, const FftLen& fy, int nt = FftCfg<T>::threads) {
   constexpr int CAP = FftCfg<T>::cap;
   const int C = fx.n / 2 + 1;
-  const size_t smem = (size_t)(fx.n + fy.n) * sizeof(typename C2<T>::tw) +
+  const size_t smem = (size_t)kTwRegion * (fx.n + fy.n) * sizeof(typename C2<T>::tw) +
                       (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(typename C2<T>::t);
   return max_lines(fx, CAP, nt) >= fy.n / 2 && max_lines(fy, CAP, nt) >= C &&
          (fy.n / 2) * C <= nt * (CAP / 2) && smem <= (size_t)kMaxDynSmem;
@@ -950,7 +958,7 @@ static cudaError_t launch_plane(T* data, const FftLen& fx, const FftLen& fy, con
   using T2 = typename C2<T>::t;
   const int C = fx.n / 2 + 1;
   using T4 = typename C2<T>::tw;
-  const size_t sm = (size_t)(fx.n + fy.n) * sizeof(T4) +
+  const size_t sm = (size_t)kTwRegion * (fx.n + fy.n) * sizeof(T4) +
                     (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(T2);
   k_fft_plane<T><<<nplanes, plane_threads<T>(fx, fy), sm, s>>>(data, fx, fy,
                                                                 reinterpret_cast<const T4*>(tw),
@@ -970,7 +978,8 @@ static cudaError_t launch_rows(T* data, const FftLen& fx, const void* tw, int nr
   int B = std::min(max_lines(fx, CAP, NT), NT * (CAP / 2) / C);
   B = std::max(1, std::min(B, npairs));
   using T4 = typename C2<T>::tw;
-  const size_t sm = (size_t)fx.n * sizeof(T4) + (size_t)B * std::max(fx.n, 2 * C) * sizeof(T2);
+  const size_t sm =
+      (size_t)kTwRegion * fx.n * sizeof(T4) + (size_t)B * std::max(fx.n, 2 * C) * sizeof(T2);
   const int grid = (npairs + B - 1) / B;
   k_fft_rows<T><<<grid, NT, sm, s>>>(data, fx, reinterpret_cast<const T4*>(tw), npairs,
                                               B, inv, tdata, (long)nrows, Iy, np0);
@@ -988,7 +997,7 @@ static cudaError_t launch_cols(T* data, const FftLen& f, const void* tw, int Cn,
   const int groups = (Cn + B - 1) / B;
   B = (Cn + groups - 1) / groups;
   using T4 = typename C2<T>::tw;
-  const size_t sm = (size_t)f.n * sizeof(T4) + (size_t)B * f.n * sizeof(T2);
+  const size_t sm = (size_t)kTwRegion * f.n * sizeof(T4) + (size_t)B * f.n * sizeof(T2);
   const int grid = O * groups;
   k_fft_cols<T><<<grid, NT, sm, s>>>(reinterpret_cast<T2*>(data), f,
                                               reinterpret_cast<const T4*>(tw), Cn, O, os, es, B,
@@ -1036,7 +1045,8 @@ template cudaError_t fft_mid_forward_conv_inverse<double>(const sog_plan*, cudaS
 // twiddles, one parity's B_l for the nl Gaussians a mode can use, (c1, c2).
 size_t long_fused_smem(int P, const FftLen& fy, int nl, size_t es) {
   const int np0 = (P + 1) / 2, ps = np0, pst = (ps + 3) / 4 * 4;
-  return (size_t)np0 * fy.n * 2 * es + (size_t)fy.n * (es == 4 ? sizeof(TwF) : sizeof(TwD)) +
+  return (size_t)np0 * fy.n * 2 * es +
+         (size_t)kTwRegion * fy.n * (es == 4 ? sizeof(TwF) : sizeof(TwD)) +
          (size_t)nl * ps * pst * es + (size_t)nl * 2 * es;
 }
 
@@ -1117,7 +1127,7 @@ bool fft_len_ok(int prec, const FftLen& f) {
   const size_t elem = prec == SOG_PREC_FP64 ? sizeof(double2) : sizeof(float2);
   const size_t twe = prec == SOG_PREC_FP64 ? sizeof(TwD) : sizeof(TwF);
   return f.n >= 2 && max_lines(f, cap, nt) >= 1 && (f.n / 2 + 1) <= nt * (cap / 2) &&
-         (size_t)f.n * twe + (size_t)(f.n + 2) * elem <= (size_t)kMaxDynSmem;
+         (size_t)kTwRegion * f.n * twe + (size_t)(f.n + 2) * elem <= (size_t)kMaxDynSmem;
 }
 
 // The largest dynamic shared memory a kernel's static shared memory leaves.

@@ -36,6 +36,10 @@ __host__ __device__ inline void half_mode(int idx, int Ky, int& nx, int& ny) {
 
 // One FFT length: radix sequence of the Stockham stages and the offset of its
 // n roots of unity exp(-2 pi i t / n) in the twiddle table.
+// Twiddle entries per transform length in the plan's table: the length-n
+// table w_n^t, then the engine's per-stage tables (n entries reserved).
+constexpr int kTwRegion = 2;
+
 struct FftLen {
   int n;
   int nst;

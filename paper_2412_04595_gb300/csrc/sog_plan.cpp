@@ -678,18 +678,41 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   // biases the transform's gain.
   std::vector<double> tw;
   const int tw_vals = prec == SOG_PREC_MIXED ? 4 : 2;
+  // Per length: the n entries w_n^t, then the engine's per-stage tables
+  // (in the order the engine runs the radices: 15, 3, 5, 7, 16, 8, 4, 2;
+  // stage of radix R after a product L of earlier radices: entries
+  // [p - 1][j] = w_n^(j p n / (R L)), p < R, j < L, so that consecutive
+  // threads read consecutive entries), padded to n entries.
+  auto push_tw = [&](int t, int n) {
+    const double c = cos(2.0 * kPi * t / n), sn = -sin(2.0 * kPi * t / n);
+    if (prec == SOG_PREC_MIXED) {
+      const double ch = (double)(float)c, sh = (double)(float)sn;
+      tw.insert(tw.end(), {ch, sh, c - ch, sn - sh});
+    } else {
+      tw.insert(tw.end(), {c, sn});
+    }
+  };
   auto add_len = [&](int n, sogk::FftLen& f) {
     factorize(n, f, prec != SOG_PREC_FP64);
     f.tw_off = (int)(tw.size() / tw_vals);
-    for (int t = 0; t < n; ++t) {
-      const double c = cos(2.0 * kPi * t / n), sn = -sin(2.0 * kPi * t / n);
-      if (prec == SOG_PREC_MIXED) {
-        const double ch = (double)(float)c, sh = (double)(float)sn;
-        tw.insert(tw.end(), {ch, sh, c - ch, sn - sh});
-      } else {
-        tw.insert(tw.end(), {c, sn});
-      }
-    }
+    for (int t = 0; t < n; ++t) push_tw(t, n);
+    int L = 1, used = 0;
+    auto stage_tw = [&](int R) {
+      const int m = n / (R * L);
+      for (int pp = 1; pp < R; ++pp)
+        for (int j = 0; j < L; ++j) push_tw(j * pp * m, n);
+      used += (R - 1) * L;
+      L *= R;
+    };
+    for (int i = 0; i < f.n15; ++i) stage_tw(15);
+    for (int i = 0; i < f.n3; ++i) stage_tw(3);
+    for (int i = 0; i < f.n5; ++i) stage_tw(5);
+    for (int i = 0; i < f.n7; ++i) stage_tw(7);
+    for (int i = 0; i < f.n16; ++i) stage_tw(16);
+    for (int i = 0; i < f.n8; ++i) stage_tw(8);
+    for (int i = 0; i < f.n4; ++i) stage_tw(4);
+    for (int i = 0; i < f.n2; ++i) stage_tw(2);
+    for (; used < (sogk::kTwRegion - 1) * n; ++used) push_tw(0, n);
   };
   if (p->has_mid) {
     add_len(Ix, p->fx);
