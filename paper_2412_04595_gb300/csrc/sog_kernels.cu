@@ -1311,6 +1311,33 @@ __device__ __forceinline__ void cheb_all(T x, int P, T* t) {
 // charge with its lanes over the (n, dy) rows of the window, P_cheb x P rows
 // in all, 32 at a time; lane s writes word s x RP + dx (mod 32), so a step's
 // 32 rows fall in 32 banks.  The tile is then added to the planes.
+// A lane's rows (n, dy) of the P planes x Pw window rows, n Pw + dy = lane,
+// lane + 32, lane + 64, ...: the first one and the step between them (32
+// rows = dn planes and ddy rows; a row offset o = n PS + dy RP in the tile),
+// so that the row loops advance by additions instead of dividing.
+struct RowStep {
+  int n0, dy0, o0, dn, ddy, dO, wrapO;
+  __device__ RowStep(int lane, int Pw, int PS, int RP) {
+    n0 = lane / Pw;
+    dy0 = lane - n0 * Pw;
+    o0 = n0 * PS + dy0 * RP;
+    dn = 32 / Pw;
+    ddy = 32 - dn * Pw;
+    dO = dn * PS + ddy * RP;
+    wrapO = PS - Pw * RP;
+  }
+  __device__ __forceinline__ void next(int& n, int& dy, int& o, int Pw) const {
+    dy += ddy;
+    n += dn;
+    o += dO;
+    if (dy >= Pw) {
+      dy -= Pw;
+      ++n;
+      o += wrapO;
+    }
+  }
+};
+
 template <typename T, int PW>
 __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T> w, int P,
                                                               const P4<T>* __restrict__ rec,
@@ -1354,7 +1381,7 @@ __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T
   int ex = 0;
   frexp(qsum > T(0) ? qsum : T(1), &ex);  // qsum < 2^ex
   const T S = ldexp(T(1), FixAcc<T>::bits - ex), iS = ldexp(T(1), ex - FixAcc<T>::bits);
-  const int nrows = P * Pw, nit = (nrows + 31) >> 5;
+  const RowStep rs(lane, Pw, PS, RP);
   for (int p0 = b; p0 < e; p0 += kTileBatch) {
     const int nb = min(kTileBatch, e - p0);
     __syncthreads();
@@ -1392,16 +1419,15 @@ __global__ void __launch_bounds__(kTileThreads) k_long_spread(TileGeom g, WinT<T
 #pragma unroll
       for (int dx = 0; dx < PR; ++dx) rwx[dx] = dx < Pw ? wj[dx] : T(0);
       A* bj = st + bofs[j];
-      for (int it = 0; it < nit; ++it) {
-        const int s2 = lane + 32 * it;
-        if (s2 < nrows) {
-          const int n = s2 / Pw, dy = s2 - n * Pw;
-          const T c = wj[Pw + dy] * tj[n] * S;
-          A* rp = bj + n * PS + dy * RP;
+      // rows n Pw + dy = lane, lane + 32, ...: stepped, not divided
+      int n = rs.n0, dy = rs.dy0, o = rs.o0;
+      while (n < P) {
+        const T c = wj[Pw + dy] * tj[n] * S;
+        A* rp = bj + o;
 #pragma unroll
-          for (int dx = 0; dx < PR; ++dx)
-            if (dx < Pw) fix_add(rp + dx, FixAcc<T>::cvt(c * rwx[dx]));
-        }
+        for (int dx = 0; dx < PR; ++dx)
+          if (dx < Pw) fix_add(rp + dx, FixAcc<T>::cvt(c * rwx[dx]));
+        rs.next(n, dy, o, Pw);
       }
     }
   }
@@ -1593,7 +1619,7 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
   tile_load(planes, st, W0, W1, P, RP, PS, xoff, yoff, zoff);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const T sc_lane = (T)((lane >> 3) == 1 ? sc.x : ((lane >> 3) == 2 ? sc.y : sc.z));
-  const int nrows = P * Pw, nit = (nrows + 31) >> 5;
+  const RowStep rs(lane, Pw, PS, RP);
   OutSlots<T> out{T(0), 0, 0};
   for (int p0 = b; p0 < e; p0 += kTileBatch) {
     const int nb = min(kTileBatch, e - p0);
@@ -1642,28 +1668,27 @@ __global__ void __launch_bounds__(kTileThreads) k_long_gather(TileGeom g, WinT<T
       }
       const T* bj = st + bofs[j];
       T f = 0, fx = 0, fy = 0, fz = 0;
-      for (int it = 0; it < nit; ++it) {
-        const int s2 = lane + 32 * it;
-        if (s2 < nrows) {
-          const int n = s2 / Pw, dy = s2 - n * Pw;
-          const T* rp = bj + n * PS + dy * RP;
-          T sx = 0, sd = 0;
+      // rows n Pw + dy = lane, lane + 32, ...: stepped, not divided
+      int n = rs.n0, dy = rs.dy0, o = rs.o0;
+      while (n < P) {
+        const T* rp = bj + o;
+        T sx = 0, sd = 0;
 #pragma unroll
-          for (int dx = 0; dx < PR; ++dx) {
-            if (dx < Pw) {
-              const T u = rp[dx];
-              sx += u * rwx[dx];
-              sd += u * rdwx[dx];
-            }
+        for (int dx = 0; dx < PR; ++dx) {
+          if (dx < Pw) {
+            const T u = rp[dx];
+            sx += u * rwx[dx];
+            sd += u * rdwx[dx];
           }
-          const T wy = wj[2 * Pw + dy], dwy = wj[3 * Pw + dy];
-          const T tn = tj[n], dtn = tj[P + n];
-          const T tw = tn * wy;
-          f += tw * sx;
-          fx += tw * sd;
-          fy += tn * dwy * sx;
-          fz += dtn * wy * sx;
         }
+        const T wy = wj[2 * Pw + dy], dwy = wj[3 * Pw + dy];
+        const T tn = tj[n], dtn = tj[P + n];
+        const T tw = tn * wy;
+        f += tw * sx;
+        fx += tw * sd;
+        fy += tn * dwy * sx;
+        fz += dtn * wy * sx;
+        rs.next(n, dy, o, Pw);
       }
       const T tot = warp_sum4(f, fx, fy, fz);
       out.put(lane < 8 ? tot : tot * sc_lane, perm[p0 + j]);
