@@ -509,6 +509,10 @@ __global__ void k_bin_count(PrepGeom g, const T* __restrict__ q, const T* __rest
 // Exclusive scan of three count arrays (one CTA each): cnt[off + k] for
 // k < n becomes the start of bin k, cnt[off + n] the total.
 __global__ void k_scan3(int* __restrict__ cnt, int3 off, int3 nbins) {
+  // each thread takes kScanItems consecutive counts per round (their loads
+  // in flight together), scans them serially; the threads' totals are
+  // scanned across the block and carried from round to round
+  constexpr int kScanItems = 8;
   const int which = blockIdx.x;
   const int o = which == 0 ? off.x : (which == 1 ? off.y : off.z);
   const int n = which == 0 ? nbins.x : (which == 1 ? nbins.y : nbins.z);
@@ -519,10 +523,19 @@ __global__ void k_scan3(int* __restrict__ cnt, int3 off, int3 nbins) {
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int base = 0; base <= n; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const int v = (i < n) ? a[i] : 0;
-    int x = v;
+  for (int base = 0; base <= n; base += (int)blockDim.x * kScanItems) {
+    const int i0 = base + (int)threadIdx.x * kScanItems;
+    int v[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = (i0 + k < n) ? a[i0 + k] : 0;
+    int tsum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const int t = v[k];
+      v[k] = tsum;
+      tsum += t;
+    }
+    int x = tsum;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, d);
@@ -531,19 +544,21 @@ __global__ void k_scan3(int* __restrict__ cnt, int3 off, int3 nbins) {
     if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-      int s = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+      int sw = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, s, d);
-        if (lane >= d) s += y;
+        const int y = __shfl_up_sync(0xffffffffu, sw, d);
+        if (lane >= d) sw += y;
       }
-      wsum[lane] = s;
+      wsum[lane] = sw;
     }
     __syncthreads();
-    const int excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - v;
-    if (i <= n) a[i] = excl;
+    const int excl = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - tsum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+      if (i0 + k <= n) a[i0 + k] = excl + v[k];
     __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    if (threadIdx.x == blockDim.x - 1) carry = excl + tsum;
     __syncthreads();
   }
 }
