@@ -260,7 +260,7 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
       dft<T2, 4>(v, inv, tw, n);
 #pragma unroll
       for (int k1 = 0; k1 < 4; ++k1)
-        a[j2][k1] = (j2 == 0 || k1 == 0) ? v[k1] : cmul_tw(v[k1], tw[j2 * k1 * (n / 16)], inv);
+        a[j2][k1] = (j2 == 0 || k1 == 0) ? v[k1] : cmul_tw(v[k1], tw[j2 * k1], inv);
     }
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
@@ -279,7 +279,7 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
       dft<T2, 3>(v, inv, tw, n);
 #pragma unroll
       for (int k1 = 0; k1 < 3; ++k1)
-        a[j2][k1] = (j2 == 0 || k1 == 0) ? v[k1] : cmul_tw(v[k1], tw[j2 * k1 * (n / 15)], inv);
+        a[j2][k1] = (j2 == 0 || k1 == 0) ? v[k1] : cmul_tw(v[k1], tw[16 + j2 * k1], inv);
     }
 #pragma unroll
     for (int k1 = 0; k1 < 3; ++k1) {
@@ -329,21 +329,7 @@ __device__ __forceinline__ void dft(T2* x, bool inv, const T4* tw, int n) {
     x[3] = pm_i(a3, b3, inv);
     x[4] = pm_i(a3, b3, !inv);
   } else {
-    // other odd radix: y_q = sum_p x_p w^(qp), w = exp(-+2 pi i / R) from
-    // the length-n table (entry (qp mod R) n / R)
-    const int step = n / R;
-    T2 y[R];
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      T2 s = x[0];
-#pragma unroll
-      for (int p = 1; p < R; ++p) {
-        s = cadd(s, cmul_tw(x[p], tw[((q * p) % R) * step], inv));
-      }
-      y[q] = s;
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = y[q];
+    static_assert(R == 2, "radix without a butterfly");
   }
 }
 
@@ -408,7 +394,7 @@ __device__ void fft_lines(T2* buf, const LineSet s, const FftLen& f, const T4* t
             n7 = f.n7;
   // the stage tables follow the length-n table: stage by stage, in this
   // order, (R - 1) L entries [p - 1][j] = w_n^(j p n / (R L))
-  const T4* stw = tw + f.n;
+  const T4* stw = tw + kTwConst;
   int L = 1;
   if constexpr (CAP >= 16)
     for (int i = 0; i < n15; ++i, stw += 14 * L, L *= 15) stage<T2, CAP, 15>(buf, s, L, tw, stw, inv);
@@ -523,10 +509,10 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
   const int Ix = fx.n, Iy = fy.n, C = Ix / 2 + 1, pitch = Ix + 2;
   const int np = Iy / 2;
   T4* twx = reinterpret_cast<T4*>(smraw);
-  T4* twy = twx + kTwRegion * Ix;
-  T2* buf = reinterpret_cast<T2*>(twy + kTwRegion * Iy);
-  load_tw(twx, twg + fx.tw_off, kTwRegion * Ix);
-  load_tw(twy, twg + fy.tw_off, kTwRegion * Iy);
+  T4* twy = twx + tw_len(Ix);
+  T2* buf = reinterpret_cast<T2*>(twy + tw_len(Iy));
+  load_tw(twx, twg + fx.tw_off, tw_len(Ix));
+  load_tw(twy, twg + fy.tw_off, tw_len(Iy));
   T* pl = data + (size_t)blockIdx.x * Iy * pitch;
   T2* plc = reinterpret_cast<T2*>(pl);
   const LineSet xs{Ix, np, Ix, 1, false};
@@ -579,8 +565,8 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
   const int Ix = fx.n, C = Ix / 2 + 1, pitch = Ix + 2;
   using T4 = typename C2<T>::tw;
   T4* twx = reinterpret_cast<T4*>(smraw);
-  T2* buf = reinterpret_cast<T2*>(twx + kTwRegion * Ix);
-  load_tw(twx, twg + fx.tw_off, kTwRegion * Ix);
+  T2* buf = reinterpret_cast<T2*>(twx + tw_len(Ix));
+  load_tw(twx, twg + fx.tw_off, tw_len(Ix));
   const int p0 = blockIdx.x * B;
   const int nl = min(B, npairs - p0);
   T* base = data + (size_t)(2 * p0) * pitch;
@@ -655,8 +641,8 @@ __global__ void __launch_bounds__(FftCfg<T>::threads, FftCfg<T>::minb)
   const int n = f.n;
   using T4 = typename C2<T>::tw;
   T4* tw = reinterpret_cast<T4*>(smraw);
-  T2* buf = reinterpret_cast<T2*>(tw + kTwRegion * n);
-  load_tw(tw, twg + f.tw_off, kTwRegion * n);
+  T2* buf = reinterpret_cast<T2*>(tw + tw_len(n));
+  load_tw(tw, twg + f.tw_off, tw_len(n));
   const int gpo = (Cn + B - 1) / B;
   const int o = blockIdx.x / gpo;
   const int c0 = (blockIdx.x - o * gpo) * B;
@@ -841,7 +827,7 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
   const int np0 = (P + 1) / 2, np = par ? P / 2 : np0;
   const int tot = np * Iy;
   T4* tw = reinterpret_cast<T4*>(buf + (size_t)np0 * Iy);
-  T* sB = reinterpret_cast<T*>(tw + kTwRegion * Iy);      // [l][i][j], row stride pst
+  T* sB = reinterpret_cast<T*>(tw + tw_len(Iy));      // [l][i][j], row stride pst
   T2* sC = reinterpret_cast<T2*>(sB + (size_t)nl * ps * pst);
   T2* blk = data + (size_t)c * P * Iy + (size_t)(par ? np0 : 0) * Iy;
   if (threadIdx.x == 0) {
@@ -852,7 +838,7 @@ __global__ void __launch_bounds__(kYpassThreads, 1)
       bulk_g2s(reinterpret_cast<char*>(buf) + o, reinterpret_cast<const char*>(blk) + o,
                bytes - o < 32768u ? bytes - o : 32768u, &bar);
   }
-  for (int i = threadIdx.x; i < kTwRegion * Iy; i += blockDim.x) tw[i] = twg[fy.tw_off + i];
+  for (int i = threadIdx.x; i < tw_len(Iy); i += blockDim.x) tw[i] = twg[fy.tw_off + i];
   const int bsz = ps * pst;
   for (int i = threadIdx.x; i < nl * bsz; i += blockDim.x) {
     const int l = i / bsz;
@@ -937,7 +923,7 @@ template <typename T>
 static bool plane_fits(const FftLen& fx, const FftLen& fy, int nt = FftCfg<T>::threads) {
   constexpr int CAP = FftCfg<T>::cap;
   const int C = fx.n / 2 + 1;
-  const size_t smem = (size_t)kTwRegion * (fx.n + fy.n) * sizeof(typename C2<T>::tw) +
+  const size_t smem = (size_t)(tw_len(fx.n) + tw_len(fy.n)) * sizeof(typename C2<T>::tw) +
                       (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(typename C2<T>::t);
   return max_lines(fx, CAP, nt) >= fy.n / 2 && max_lines(fy, CAP, nt) >= C &&
          (fy.n / 2) * C <= nt * (CAP / 2) && smem <= (size_t)kMaxDynSmem;
@@ -958,7 +944,7 @@ static cudaError_t launch_plane(T* data, const FftLen& fx, const FftLen& fy, con
   using T2 = typename C2<T>::t;
   const int C = fx.n / 2 + 1;
   using T4 = typename C2<T>::tw;
-  const size_t sm = (size_t)kTwRegion * (fx.n + fy.n) * sizeof(T4) +
+  const size_t sm = (size_t)(tw_len(fx.n) + tw_len(fy.n)) * sizeof(T4) +
                     (size_t)std::max((fy.n / 2) * fx.n, fy.n * C) * sizeof(T2);
   k_fft_plane<T><<<nplanes, plane_threads<T>(fx, fy), sm, s>>>(data, fx, fy,
                                                                 reinterpret_cast<const T4*>(tw),
@@ -979,7 +965,7 @@ static cudaError_t launch_rows(T* data, const FftLen& fx, const void* tw, int nr
   B = std::max(1, std::min(B, npairs));
   using T4 = typename C2<T>::tw;
   const size_t sm =
-      (size_t)kTwRegion * fx.n * sizeof(T4) + (size_t)B * std::max(fx.n, 2 * C) * sizeof(T2);
+      (size_t)tw_len(fx.n) * sizeof(T4) + (size_t)B * std::max(fx.n, 2 * C) * sizeof(T2);
   const int grid = (npairs + B - 1) / B;
   k_fft_rows<T><<<grid, NT, sm, s>>>(data, fx, reinterpret_cast<const T4*>(tw), npairs,
                                               B, inv, tdata, (long)nrows, Iy, np0);
@@ -997,7 +983,7 @@ static cudaError_t launch_cols(T* data, const FftLen& f, const void* tw, int Cn,
   const int groups = (Cn + B - 1) / B;
   B = (Cn + groups - 1) / groups;
   using T4 = typename C2<T>::tw;
-  const size_t sm = (size_t)kTwRegion * f.n * sizeof(T4) + (size_t)B * f.n * sizeof(T2);
+  const size_t sm = (size_t)tw_len(f.n) * sizeof(T4) + (size_t)B * f.n * sizeof(T2);
   const int grid = O * groups;
   k_fft_cols<T><<<grid, NT, sm, s>>>(reinterpret_cast<T2*>(data), f,
                                               reinterpret_cast<const T4*>(tw), Cn, O, os, es, B,
@@ -1046,7 +1032,7 @@ template cudaError_t fft_mid_forward_conv_inverse<double>(const sog_plan*, cudaS
 size_t long_fused_smem(int P, const FftLen& fy, int nl, size_t es) {
   const int np0 = (P + 1) / 2, ps = np0, pst = (ps + 3) / 4 * 4;
   return (size_t)np0 * fy.n * 2 * es +
-         (size_t)kTwRegion * fy.n * (es == 4 ? sizeof(TwF) : sizeof(TwD)) +
+         (size_t)tw_len(fy.n) * (es == 4 ? sizeof(TwF) : sizeof(TwD)) +
          (size_t)nl * ps * pst * es + (size_t)nl * 2 * es;
 }
 
@@ -1127,7 +1113,7 @@ bool fft_len_ok(int prec, const FftLen& f) {
   const size_t elem = prec == SOG_PREC_FP64 ? sizeof(double2) : sizeof(float2);
   const size_t twe = prec == SOG_PREC_FP64 ? sizeof(TwD) : sizeof(TwF);
   return f.n >= 2 && max_lines(f, cap, nt) >= 1 && (f.n / 2 + 1) <= nt * (cap / 2) &&
-         (size_t)kTwRegion * f.n * twe + (size_t)(f.n + 2) * elem <= (size_t)kMaxDynSmem;
+         (size_t)tw_len(f.n) * twe + (size_t)(f.n + 2) * elem <= (size_t)kMaxDynSmem;
 }
 
 // The largest dynamic shared memory a kernel's static shared memory leaves.

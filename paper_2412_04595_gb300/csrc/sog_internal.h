@@ -36,9 +36,12 @@ __host__ __device__ inline void half_mode(int idx, int Ky, int& nx, int& ny) {
 
 // One FFT length: radix sequence of the Stockham stages and the offset of its
 // n roots of unity exp(-2 pi i t / n) in the twiddle table.
-// Twiddle entries per transform length in the plan's table: the length-n
-// table w_n^t, then the engine's per-stage tables (n entries reserved).
-constexpr int kTwRegion = 2;
+// Twiddle entries per transform length in the plan's table: the constants
+// of the radix-16 and radix-15 butterflies (w_16^t, t < 16, then w_15^t,
+// t < 15, and one unused entry), then the engine's per-stage tables (n
+// entries reserved, n - 1 used).
+constexpr int kTwConst = 32;
+inline __host__ __device__ int tw_len(int n) { return kTwConst + n; }
 
 struct FftLen {
   int n;

@@ -678,11 +678,12 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   // biases the transform's gain.
   std::vector<double> tw;
   const int tw_vals = prec == SOG_PREC_MIXED ? 4 : 2;
-  // Per length: the n entries w_n^t, then the engine's per-stage tables
-  // (in the order the engine runs the radices: 15, 3, 5, 7, 16, 8, 4, 2;
-  // stage of radix R after a product L of earlier radices: entries
-  // [p - 1][j] = w_n^(j p n / (R L)), p < R, j < L, so that consecutive
-  // threads read consecutive entries), padded to n entries.
+  // Per length: the radix-16 and radix-15 butterfly constants w_16^t and
+  // w_15^t (kTwConst entries), then the engine's per-stage tables (in the
+  // order the engine runs the radices: 15, 3, 5, 7, 16, 8, 4, 2; stage of
+  // radix R after a product L of earlier radices: entries [p - 1][j] =
+  // w_n^(j p n / (R L)), p < R, j < L, so that consecutive threads read
+  // consecutive entries), padded to n entries.
   auto push_tw = [&](int t, int n) {
     const double c = cos(2.0 * kPi * t / n), sn = -sin(2.0 * kPi * t / n);
     if (prec == SOG_PREC_MIXED) {
@@ -695,7 +696,8 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   auto add_len = [&](int n, sogk::FftLen& f) {
     factorize(n, f, prec != SOG_PREC_FP64);
     f.tw_off = (int)(tw.size() / tw_vals);
-    for (int t = 0; t < n; ++t) push_tw(t, n);
+    for (int t = 0; t < 16; ++t) push_tw(t, 16);
+    for (int t = 0; t < 16; ++t) push_tw(t % 15, 15);
     int L = 1, used = 0;
     auto stage_tw = [&](int R) {
       const int m = n / (R * L);
@@ -712,7 +714,7 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     for (int i = 0; i < f.n8; ++i) stage_tw(8);
     for (int i = 0; i < f.n4; ++i) stage_tw(4);
     for (int i = 0; i < f.n2; ++i) stage_tw(2);
-    for (; used < (sogk::kTwRegion - 1) * n; ++used) push_tw(0, n);
+    for (; used < n; ++used) push_tw(0, n);
   };
   if (p->has_mid) {
     add_len(Ix, p->fx);
