@@ -70,6 +70,8 @@ CPU_SAMPLE_SECONDS = 15.0        # oracle work of the CPU baseline's bounded sam
 # not of this implementation): 8 per candidate of the 27-cell neighbourhood
 # (3 differences, squared distance, comparison) and 30 per pair inside r_c
 # (distance, reciprocal, kernel value and derivative, potential and force).
+# neighbour counts whose analytic parameters sog_tune_cutoff times
+CUTOFF_CANDIDATES = (80.0, 100.0, 120.0, 140.0, 160.0, 200.0, 240.0, 300.0)
 CAND_FLOP = 8
 PAIR_FLOP = 30
 
@@ -312,10 +314,22 @@ def run_ours(args, wl, rank, world):
     q, r, _ = make_system(wl)
     q = q.astype(np.float64) if prec == B.SOG_PREC_FP64 else q
     r = r.astype(np.float64) if prec == B.SOG_PREC_FP64 else r
-    plan = B.Plan(N, L, tol, precision=prec, n_nb=args.n_nb)
-    dt = plan.dtype
     qt = torch.tensor(q, device=dev)
     rt = torch.tensor(r, device=dev)
+    cutoff = None
+    n_nb = args.n_nb
+    if not args.no_tune_cutoff:
+        # Sec. 4.3: the cutoff chosen by the run time of the evaluation (each
+        # candidate neighbour count through the analytic selection, timed on
+        # this workload; excluded from the timed region, like plan creation)
+        t0 = time.perf_counter()
+        n_nb, ms = B.sog_tune_cutoff(N, L, tol, qt, rt, CUTOFF_CANDIDATES, reps=3, precision=prec)
+        cutoff = {"n_nb": n_nb, "candidates_ms": {"%g" % k: round(v, 4) for k, v in ms.items()},
+                  "analytic_default_n_nb": args.n_nb, "seconds": time.perf_counter() - t0,
+                  "desc": "sog_tune_cutoff: median evaluation time of each candidate neighbour "
+                          "count's analytic parameters; the fastest is used"}
+    plan = B.Plan(N, L, tol, precision=prec, n_nb=n_nb)
+    dt = plan.dtype
     tune = None
     if not args.no_autotune:
         # tile edges and CTAs per tile timed on this workload (excluded from
@@ -423,7 +437,7 @@ def run_ours(args, wl, rank, world):
         md = md_rate(B, plan, q, r, dev, stream, flush)
     plan.close()
     return dict(prm=prm, stage_ms=stage_ms, value=value, total_ms=total_ms, launches=launches,
-                md=md, tune=tune,
+                md=md, tune=tune, cutoff=cutoff,
                 clocks=clk, e2e=e2e, E=E_h, F=F_h, phi=phi_h, q=q, r=r, plain=plain, es=es)
 
 
@@ -752,12 +766,14 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
-    ap.add_argument("--n-nb", dest="n_nb", type=float, default=120.0)
+    ap.add_argument("--n-nb", dest="n_nb", type=float, default=120.0,
+                    help="neighbour count of the analytic cutoff (used with --no-tune-cutoff)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-plain-fp64", action="store_true")
     ap.add_argument("--no-md", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-tune-cutoff", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -767,6 +783,9 @@ def main():
               "L": list(wl["L"]), "tol": wl["tol"], "precision": args.precision,
               "n_nb": args.n_nb, "l2": "flushed between steps (%d MiB write)" % (FLUSH_BYTES >> 20),
               "parallelism": "replicas x%d" % world}
+    if not args.no_tune_cutoff and "batch" not in wl:
+        config["n_nb"] = ("selected by run time among %s (Sec. 4.3; sog_tune_cutoff)"
+                          % ", ".join("%g" % c for c in CUTOFF_CANDIDATES))
 
     if args.impl == "reference":
         run_reference(args, wl, config, rank)
@@ -817,6 +836,8 @@ def main():
         line["md"] = res["md"]
     if res["tune"] is not None:
         line["autotuned_tiles"] = res["tune"]
+    if res["cutoff"] is not None:
+        line["cutoff_selection"] = res["cutoff"]
     if res["plain"] is not None:
         line["plain_fp64"] = {k: v for k, v in res["plain"].items() if k not in ("phi", "F", "E")}
         line["speedup_vs_plain_fp64"] = res["value"] / (world * res["plain"]["value"])

@@ -240,6 +240,30 @@ sog_status sog_plan_autotune(sog_plan* plan, const void* q, const void* r, int32
 sog_status sog_plan_tiles(const sog_plan* plan, int32_t* out);
 
 /*
+ * Cutoff selection by run time (Sec. 4.3: r_c is chosen to optimise the run
+ * time of the near field and the far field, ~ rho^(-1/3) as the rough
+ * estimate).  For each candidate neighbour count n_nb[c] (the analytic
+ * selection of sog_select_params with opts->n_nb = n_nb[c], every other
+ * parameter following from the tolerance as there), a plan is created,
+ * evaluated reps + 1 times on q, r (the first run captures its graph) and
+ * timed with CUDA events on `stream`, then destroyed; the fastest
+ * candidate's n_nb is written to host *best, the median times to host
+ * ms[c] (may be NULL; a candidate whose parameters are infeasible gets -1).
+ * Every candidate meets the tolerance by construction.  Synchronous;
+ * allocates and frees one plan at a time.
+ *   N, L, tol, opts   as for sog_plan_create (opts->manual must be NULL;
+ *                     opts->n_nb is ignored)
+ *   q, r              device, the plan type's element type, as in sog_eval
+ *   n_nb, ncand       host array of 1 <= ncand <= 32 candidates, each > 0
+ *   reps              1..100
+ * Errors: SOG_ERR_ARG for bad arguments; SOG_ERR_PARAMS when no candidate is
+ * feasible; the first CUDA or data error of an evaluation otherwise.
+ */
+sog_status sog_tune_cutoff(int64_t N, double Lx, double Ly, double Lz, double tol,
+                           const sog_opts* opts, const void* q, const void* r, const double* n_nb,
+                           int32_t ncand, int32_t reps, double* best, float* ms, void* stream);
+
+/*
  * Measured fused multiply-add rate of the current device (a measurement
  * utility; the paper has no counterpart): FP32 (precision SOG_PREC_MIXED) or
  * FP64 (SOG_PREC_FP64) FMAs in independent chains on every SM, timed with

@@ -99,6 +99,9 @@ def load(build_if_missing: bool = False):
     L.sog_measure_fma_peak.argtypes = [i32, ctypes.POINTER(d)]
     L.sog_plan_autotune.argtypes = [vp, vp, vp, i32, vp]
     L.sog_plan_tiles.argtypes = [vp, ctypes.POINTER(i32)]
+    L.sog_tune_cutoff.argtypes = [i64, d, d, d, d, ctypes.POINTER(SogOpts), vp, vp,
+                                  ctypes.POINTER(d), i32, i32, ctypes.POINTER(d),
+                                  ctypes.POINTER(ctypes.c_float), vp]
     L.sog_md_create.argtypes = [ctypes.POINTER(vp), vp]
     L.sog_md_step.argtypes = [vp, vp, vp, vp, vp, vp, d, i32, i32, vp, vp, vp]
     L.sog_md_destroy.argtypes = [vp]
@@ -200,6 +203,29 @@ def _require(*specs, cuda=True):
         for spec in specs:
             if spec[0] is not None and not spec[0].is_cuda:
                 raise ValueError("%s must be a CUDA tensor" % spec[1])
+
+
+def sog_tune_cutoff(N, L, tol, q, r, n_nb, reps=3, precision=SOG_PREC_MIXED, window=SOG_WIN_ES,
+                    win_poly=0, stream=None):
+    """sog_tune_cutoff: the candidate neighbour count (cutoff) of least
+    measured evaluation time on (q, r); returns (best n_nb, {n_nb: ms})
+    (ms -1: infeasible candidate)."""
+    import torch
+    N = int(N)
+    dt = torch.float64 if precision == SOG_PREC_FP64 else torch.float32
+    _require((q, "q", dt, N), (r, "r", dt, 3 * N))
+    cands = [float(x) for x in n_nb]
+    if not 1 <= len(cands) <= 32:
+        raise ValueError("1 to 32 candidates")
+    L_ = tuple(map(float, L))
+    o = _opts(precision, window, None, None, win_poly)
+    arr = (ctypes.c_double * len(cands))(*cands)
+    ms = (ctypes.c_float * len(cands))()
+    best = ctypes.c_double(0.0)
+    _check(load().sog_tune_cutoff(N, L_[0], L_[1], L_[2], float(tol), ctypes.byref(o), _ptr(q),
+                                  _ptr(r), arr, len(cands), int(reps), ctypes.byref(best), ms,
+                                  _stream_ptr(stream)), "sog_tune_cutoff")
+    return best.value, {c: float(m) for c, m in zip(cands, ms)}
 
 
 def sog_assemble_noalloc(params, q, phi_parts, grad_parts=None, phi=None, E=None, F=None,

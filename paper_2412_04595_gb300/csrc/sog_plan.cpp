@@ -1264,4 +1264,63 @@ void sog_plan_destroy(sog_plan* plan) {
   delete plan;
 }
 
+sog_status sog_tune_cutoff(int64_t N, double Lx, double Ly, double Lz, double tol,
+                           const sog_opts* opts, const void* q, const void* r, const double* n_nb,
+                           int32_t ncand, int32_t reps, double* best, float* ms, void* stream) {
+  if (!q || !r || !n_nb || !best || ncand < 1 || ncand > 32 || reps < 1 || reps > 100)
+    return SOG_ERR_ARG;
+  if (opts && opts->manual) return SOG_ERR_ARG;
+  for (int c = 0; c < ncand; ++c)
+    if (!(n_nb[c] > 0.0) || !std::isfinite(n_nb[c])) return SOG_ERR_ARG;
+  const cudaStream_t s = (cudaStream_t)stream;
+  sog_opts o = opts ? *opts : sog_opts{SOG_PREC_MIXED, SOG_WIN_ES, 0.0, nullptr, 0};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return SOG_ERR_CUDA;
+  }
+  float best_ms = -1.0f;
+  sog_status st = SOG_OK;
+  for (int c = 0; c < ncand && st == SOG_OK; ++c) {
+    if (ms) ms[c] = -1.0f;
+    o.n_nb = n_nb[c];
+    sog_plan* p = nullptr;
+    const sog_status cs = sog_plan_create(&p, N, Lx, Ly, Lz, tol, &o);
+    if (cs == SOG_ERR_PARAMS) continue;  // infeasible candidate
+    if (cs != SOG_OK) {
+      st = cs;
+      break;
+    }
+    std::vector<float> v;
+    for (int i = 0; i <= reps && st == SOG_OK; ++i) {
+      cudaEventRecord(e0, s);
+      st = sogk::eval_device(p, q, r, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (st != SOG_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        st = SOG_ERR_CUDA;
+        break;
+      }
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (i > 0) v.push_back(t);  // the first run captures the graph
+    }
+    if (st == SOG_OK) st = sog_plan_check(p);
+    sog_plan_destroy(p);
+    if (st != SOG_OK) break;
+    std::sort(v.begin(), v.end());
+    const float t = v[v.size() / 2];
+    if (ms) ms[c] = t;
+    if (best_ms < 0.0f || t < best_ms) {
+      best_ms = t;
+      *best = n_nb[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SOG_OK) return st;
+  return best_ms < 0.0f ? SOG_ERR_PARAMS : SOG_OK;
+}
+
 }  // extern "C"

@@ -58,6 +58,28 @@ def test_argument_errors_are_reported():
         binding.sog_select_params(100, 10.0, 10.0, 10.0, 0.0)
 
 
+def test_tune_cutoff_argument_errors_without_device_work():
+    """sog_tune_cutoff checks its arguments before any CUDA call: no
+    candidates, too many, a non-positive candidate, NULL inputs, bad reps."""
+    from paper_2412_04595_gb300 import _build, binding
+    lib = ctypes.CDLL(_build.build())
+    f = lib.sog_tune_cutoff
+    d, i32, vp = ctypes.c_double, ctypes.c_int32, ctypes.c_void_p
+    f.argtypes = [ctypes.c_int64, d, d, d, d, vp, vp, vp, ctypes.POINTER(d), i32, i32,
+                  ctypes.POINTER(d), ctypes.POINTER(ctypes.c_float), vp]
+    best = d(0.0)
+    dummy = vp(16)  # never dereferenced: every call below fails its argument checks
+    def call(cands, n, reps=3, q=dummy, r=dummy):
+        arr = (d * max(1, len(cands)))(*cands)
+        return f(1000, 10.0, 10.0, 10.0, 1e-6, None, q, r, arr, n, reps, ctypes.byref(best),
+                 None, None)
+    assert call([120.0], 0) == 1  # SOG_ERR_ARG
+    assert call([120.0] * 33, 33) == 1  # SOG_ERR_ARG
+    assert call([120.0, -1.0], 2) == 1  # SOG_ERR_ARG
+    assert call([120.0], 1, reps=0) == 1  # SOG_ERR_ARG
+    assert call([120.0], 1, q=None) == 1  # SOG_ERR_ARG
+
+
 def test_binding_fails_loudly_without_library(monkeypatch):
     from paper_2412_04595_gb300 import _build, binding
     monkeypatch.setattr(binding, "_lib", None)

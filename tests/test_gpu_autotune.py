@@ -91,3 +91,29 @@ def test_autotuned_stages_not_slower(B):
     print("default %.3f ms, tuned %.3f ms, tiles %s" % (t0, t1, tiles))
     assert t1 <= 1.1 * t0
     plan.close()
+
+
+def test_tune_cutoff_picks_the_fastest_feasible_candidate(B, oracle_mod):
+    """sog_tune_cutoff (Sec. 4.3: the cutoff chosen by run time): the chosen
+    neighbour count is a candidate with the least reported time, every
+    candidate was timed, and a plan with the chosen cutoff still matches the
+    oracle's evaluation with the same parameters (FP64 1e-10)."""
+    N, L = 20000, (141.4, 141.4, 10.0)
+    q, r = workloads.uniform_neutral(N, L, 23, dtype=np.float32)
+    dev = torch.device("cuda:0")
+    qt = torch.tensor(q, device=dev)
+    rt = torch.tensor(r, device=dev)
+    cands = (60.0, 120.0, 200.0)
+    best, ms = B.sog_tune_cutoff(N, L, 1e-6, qt, rt, cands, reps=3)
+    assert best in cands and all(ms[c] > 0 for c in cands)
+    assert ms[best] == min(ms.values())
+    q64, r64 = q.astype(np.float64), r.astype(np.float64)
+    prm = oracle_mod.select_params(N, *L, 1e-6, n_nb=best)
+    plan = B.Plan(N, L, 1e-6, precision=B.SOG_PREC_FP64, manual=prm)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    plan.eval(torch.tensor(q64, device=dev), torch.tensor(r64, device=dev), None, E, None)
+    torch.cuda.synchronize()
+    assert plan.check() == 0
+    plan.close()
+    ref = oracle_mod.sog_eval(prm, q64, r64)
+    assert abs(E.item() - ref["E"]) <= 1e-10 * abs(ref["E"])
