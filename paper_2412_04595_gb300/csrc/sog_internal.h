@@ -269,11 +269,11 @@ struct sog_plan {
   int ev_used[2 * SOG_NSTAGES];
   int64_t launches;
   // captured evaluations replayed with one cudaGraphLaunch; after the
-  // binning the near field (side_stream) and the long range (long_stream)
-  // run concurrently with the mid range
+  // binning the near field (side_stream), the long range (long_stream) and
+  // its k = 0 mode (k0_stream) run concurrently with the mid range
   cudaStream_t cap_stream;
-  cudaStream_t side_stream, long_stream;
-  cudaEvent_t ev_fork, ev_join, ev_join_long;
+  cudaStream_t side_stream, long_stream, k0_stream;
+  cudaEvent_t ev_fork, ev_join, ev_join_long, ev_join_k0;
   sogk::GraphEntry graphs[sogk::kMaxGraphs];
   int n_graphs;
   uint64_t use_clock;

@@ -2430,6 +2430,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   // part waits for)
   const cudaStream_t sl = serial ? s : p->long_stream;
   SOG_CK(cudaStreamWaitEvent(sl, p->ev_fork, 0));
+  bool k0_branch = false;
   if (p->has_long && p->long_direct) {
     const int P = m.P_cheb, Kx = (m.I_long[0] - 1) / 2, Ky = (m.I_long[1] - 1) / 2;
     const int nh = p->n_half;
@@ -2512,26 +2513,32 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     LAUNCH_CHECK();
     mark_end(p, 7, sl);
     }
+    // the k = 0 mode needs only the charges: its own branch (k0_stream),
+    // running beside the near field and the gridded long range
+    const cudaStream_t sk = serial ? s : p->k0_stream;
+    SOG_CK(cudaStreamWaitEvent(sk, p->ev_fork, 0));
     {
-    mark_begin(p, 8, sl);
+    mark_begin(p, 8, sk);
     const int P = m.P_cheb;
     double* mpart = p->d_red + 2 * p->red_blocks;
     const ModeGeom<T> mg0 = mode_geom<T>(m.L[0], m.L[1], m.L[2]);
     if (P <= 16)
-      k_k0_moments<T, 16><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+      k_k0_moments<T, 16><<<p->k0_blocks, kK0Threads, 0, sk>>>(q, r, N, P, mg0, mpart);
     else if (P <= 32)
-      k_k0_moments<T, 32><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+      k_k0_moments<T, 32><<<p->k0_blocks, kK0Threads, 0, sk>>>(q, r, N, P, mg0, mpart);
     else
-      k_k0_moments<T, 64><<<p->k0_blocks, kK0Threads, 0, sl>>>(q, r, N, P, mg0, mpart);
+      k_k0_moments<T, 64><<<p->k0_blocks, kK0Threads, 0, sk>>>(q, r, N, P, mg0, mpart);
     LAUNCH_CHECK();
     }
-    k_k0_finalize<<<1, 1024, 0, sl>>>(p->d_red + 2 * p->red_blocks, p->k0_blocks, P, p->d_k0mat,
+    k_k0_finalize<<<1, 1024, 0, sk>>>(p->d_red + 2 * p->red_blocks, p->k0_blocks, P, p->d_k0mat,
                                      p->d_k0nu, p->d_red, p->red_blocks, p->d_status);
     LAUNCH_CHECK();
-    k_k0_eval<T><<<(N + 255) / 256, 256, 0, sl>>>(r, N, P, 0.5 * m.L[2], float_pair(2.0 / m.L[2]),
+    k_k0_eval<T><<<(N + 255) / 256, 256, 0, sk>>>(r, N, P, 0.5 * m.L[2], float_pair(2.0 / m.L[2]),
                                                 p->d_k0nu, pp + 3 * (size_t)N, pg + 9 * (size_t)N);
     LAUNCH_CHECK();
-    mark_end(p, 8, sl);
+    mark_end(p, 8, sk);
+    SOG_CK(cudaEventRecord(p->ev_join_k0, sk));
+    k0_branch = true;
   } else {
     SOG_CK(cudaMemsetAsync(pp + 2 * (size_t)N, 0, sizeof(double) * 2 * N, sl));
     SOG_CK(cudaMemsetAsync(pg + 6 * (size_t)N, 0, sizeof(double) * 6 * N, sl));
@@ -2545,6 +2552,7 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
   // join the near field and the long range, then 6. assembly
   SOG_CK(cudaStreamWaitEvent(s, p->ev_join, 0));
   SOG_CK(cudaStreamWaitEvent(s, p->ev_join_long, 0));
+  if (k0_branch) SOG_CK(cudaStreamWaitEvent(s, p->ev_join_k0, 0));
   mark_begin(p, 9, s);
   if (phi || F || E) {
     double* epart = p->d_red + 2 * p->red_blocks + (size_t)p->red_blocks * kMaxCheb;

@@ -1032,9 +1032,11 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
   if (cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&p->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&p->long_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&p->k0_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&p->ev_join_long, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&p->ev_join_long, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_join_k0, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(base);
     delete p;
@@ -1257,9 +1259,11 @@ void sog_plan_destroy(sog_plan* plan) {
   cudaStreamDestroy(plan->cap_stream);
   cudaStreamDestroy(plan->side_stream);
   cudaStreamDestroy(plan->long_stream);
+  cudaStreamDestroy(plan->k0_stream);
   cudaEventDestroy(plan->ev_fork);
   cudaEventDestroy(plan->ev_join);
   cudaEventDestroy(plan->ev_join_long);
+  cudaEventDestroy(plan->ev_join_k0);
   cudaFree(plan->arena);
   delete plan;
 }
