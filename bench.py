@@ -71,7 +71,7 @@ CPU_SAMPLE_SECONDS = 15.0        # oracle work of the CPU baseline's bounded sam
 # (3 differences, squared distance, comparison) and 30 per pair inside r_c
 # (distance, reciprocal, kernel value and derivative, potential and force).
 # neighbour counts whose analytic parameters sog_tune_cutoff times
-CUTOFF_CANDIDATES = (80.0, 100.0, 120.0, 140.0, 160.0, 200.0, 240.0, 300.0)
+CUTOFF_CANDIDATES = (80.0, 100.0, 120.0, 140.0, 160.0, 200.0, 240.0, 280.0, 320.0)
 CAND_FLOP = 8
 PAIR_FLOP = 30
 
