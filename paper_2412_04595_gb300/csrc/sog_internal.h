@@ -17,6 +17,11 @@ constexpr int kMaxFftStages = 16;
 constexpr int kMaxCheb = 64;
 constexpr int kMaxWin = 16;
 constexpr int kNearD = 8;  // degree of the near-field table polynomials
+// Row stride of the near-field table in elements: the kNearD + 1
+// coefficients padded to whole 16-byte vectors (FP32: 12 floats = three
+// float4, FP64: 10 doubles = five double2), read with vector loads.
+template <typename T>
+__host__ __device__ constexpr int near_row() { return sizeof(T) == 4 ? 12 : 10; }
 constexpr int kMaxHalfModes = 256;  // long range by direct sums: half-plane modes
 constexpr int kModeBlocksPerSm = 4;  // CTAs of its moment sums per SM
 constexpr int kMaxHalfModeCoefs = 8192;  // half-plane modes x P_cheb (on-chip table)

@@ -675,12 +675,33 @@ __device__ __forceinline__ void near_pair(T r2, T q, T dx, T dy, T dz, const T* 
   kk = kk < K ? kk : K - 1;
   const T ihK2 = T(2) * ihK;
   const T u = (rr - (T)kk * hK) * ihK2 - T(1);
-  const T* cf = tab + kk * (kNearD + 1);
-  T p = cf[kNearD], dp = T(0);
+  // the interval's coefficients by 16-byte vector loads (rows padded to
+  // near_row<T>() elements)
+  T c[near_row<T>()];
+  if constexpr (sizeof(T) == 4) {
+    const float4* v = reinterpret_cast<const float4*>(tab + kk * near_row<T>());
+#pragma unroll
+    for (int i = 0; i < near_row<T>() / 4; ++i) {
+      const float4 t = v[i];
+      c[4 * i] = t.x;
+      c[4 * i + 1] = t.y;
+      c[4 * i + 2] = t.z;
+      c[4 * i + 3] = t.w;
+    }
+  } else {
+    const double2* v = reinterpret_cast<const double2*>(tab + kk * near_row<T>());
+#pragma unroll
+    for (int i = 0; i < near_row<T>() / 2; ++i) {
+      const double2 t = v[i];
+      c[2 * i] = t.x;
+      c[2 * i + 1] = t.y;
+    }
+  }
+  T p = c[kNearD], dp = T(0);
 #pragma unroll
   for (int jj = kNearD - 1; jj >= 0; --jj) {
     dp = dp * u + p;
-    p = p * u + cf[jj];
+    p = p * u + c[jj];
   }
   // g(r) = 1 - r F_M(r) = p; near kernel G = g/r; dG/dr = (g' - g/r)/r
   const T gp = dp * ihK2;
@@ -780,14 +801,14 @@ __global__ void __launch_bounds__(kNearThreads) k_near(NearGeom g, const P4<T>* 
   __shared__ P4<T> src[kNearSrc];                  // x - s, y - s, z, q
   __shared__ S2<T> shs[kNearSrc];                  // s (periodic shift) per source
   __shared__ unsigned short list[kNearThreads / 32][kNearList];  // accepted sources per warp
-  __shared__ T stab[kNearTab];
+  __shared__ __align__(16) T stab[kNearTab];
   __shared__ int cb[27], coff[28];
   __shared__ T csx[27], csy[27];
   __shared__ int ncell, any_shift;
   const int c = blockIdx.x;
   const int tb = cstart[c], te = cstart[c + 1];
   if (tb == te) return;
-  const int ntab = g.K * (kNearD + 1);
+  const int ntab = g.K * near_row<T>();
   const bool tab_sm = ntab <= kNearTab;
   if (tab_sm)
     for (int i = threadIdx.x; i < ntab; i += blockDim.x) stab[i] = tab[i];
@@ -2424,7 +2445,8 @@ static cudaError_t eval_t(sog_plan* p, const T* q, const T* r, T* phi, double* E
     SOG_CK(cudaMemsetAsync(pg + 3 * (size_t)N, 0, sizeof(double) * 3 * N, s));
   }
 
-  // 4-5. long range and its k = 0 mode, on long_stream, after the binning
+  // 4. long range on long_stream and 5. its k = 0 mode on k0_stream, after
+  // the binning
   // (the direct sums and the k = 0 moments could start with the evaluation,
   // but measured no faster: they compete with the binning that every other
   // part waits for)

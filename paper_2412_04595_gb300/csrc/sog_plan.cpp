@@ -741,6 +741,15 @@ sog_status sog_plan_create(sog_plan** plan, int64_t N, double Lx, double Ly, dou
     delete p;
     return SOG_ERR_PARAMS;
   }
+  {
+    // rows padded to the kernels' vector stride
+    const int D1 = p->near_D + 1, R = prec == SOG_PREC_FP64 ? sogk::near_row<double>()
+                                                           : sogk::near_row<float>();
+    std::vector<double> padded((size_t)p->near_K * R, 0.0);
+    for (int k = 0; k < p->near_K; ++k)
+      for (int c = 0; c < D1; ++c) padded[(size_t)k * R + c] = ntab[(size_t)k * D1 + c];
+    ntab.swap(padded);
+  }
 
   // mid scaling factors, Eq. (3.8) for unnormalised DFTs
   std::vector<double> mult;
