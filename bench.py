@@ -176,9 +176,12 @@ def near_counts(prm, r, samples=20000, seed=0):
     H = np.zeros((nc[2], nc[1], nc[0]))
     np.add.at(H, (ci[2], ci[1], ci[0]), 1.0)
     Hn = np.zeros_like(H)
+    # periodic x, y: the three neighbouring columns, or every column when
+    # there are fewer than three (the kernel's minimum-image case); z: the
+    # cells above and below, where they exist
     for dz in ((-1, 0, 1) if nc[2] > 1 else (0,)):
-        for dy in ((-1, 0, 1) if nc[1] >= 3 else (0,)):
-            for dx in ((-1, 0, 1) if nc[0] >= 3 else (0,)):
+        for dy in ((-1, 0, 1) if nc[1] >= 3 else range(nc[1])):
+            for dx in ((-1, 0, 1) if nc[0] >= 3 else range(nc[0])):
                 sh = np.roll(np.roll(H, dy, axis=1), dx, axis=2)
                 if dz == 1:
                     sh = np.concatenate([np.zeros_like(sh[:1]), sh[:-1]], 0)
